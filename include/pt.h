@@ -1,0 +1,158 @@
+/*
+ * pt.h — C ABI of the GB300 time-parallel inexact-Uzawa solver for parabolic problems.
+ *
+ * Problem (Neumüller & Smears, "Time-parallel iterative solvers for parabolic
+ * evolution equations", §2, eq. 2.1): implicit Euler for u_t - div(a grad u) = f on
+ * the unit box (0,1)^dim, homogeneous Dirichlet data, uniform steps tau = T/N_t,
+ * t_n = n tau,
+ *
+ *     (u_n - u_{n-1}) + tau A_n u_n = tau f_n,  n = 1..N_t,  u_0 = u0,
+ *
+ * with M = I and the conservative finite-difference operator
+ *     (A_n v)_i = sum_d h^-2 [a(x_i - h e_d/2, t_n)(v_i - v_{i-e_d}) + a(x_i + h e_d/2, t_n)(v_i - v_{i+e_d})].
+ * All N_t steps are solved at once: the time-global system B u = F (eq. 2.3-2.4) is
+ * rewritten as the symmetric saddle-point system of eq. 2.7 and solved by the inexact
+ * Uzawa iteration of §3, eq. 3.1, preconditioned by the DST-in-time Schur-complement
+ * preconditioner of §4, eq. 4.4-4.6, with geometric-multigrid V-cycles (or, in 1-D,
+ * exact tridiagonal solves) for the spatial blocks.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grids: `n[d]` interior points per axis with h = 1/(n+1); n + 1 must be a power of two
+ *   (multigrid coarsening n -> (n-1)/2); all axes equal for dim >= 2.
+ * - Arrays exchanged with the caller are packed FP64, layout [N_t][n_z][n_y][n_x], x
+ *   fastest, interior points only (n_s = prod n[d] values per step).
+ * - `*_on_device` = 1 means the pointer is CUDA device memory of the current device,
+ *   0 means host memory.  Inputs are copied; the caller keeps ownership of every
+ *   pointer it passes and may free it when the call returns.
+ * - Work is ordered on the stream given in pt_options.stream (NULL = legacy default
+ *   stream).  Calls that return results to host memory synchronise that stream.
+ * - Errors: every call returns a pt_status; PT_OK = 0.  On failure pt_last_error()
+ *   returns a thread-local message.  No exception crosses the ABI.  A pt_problem is
+ *   not thread-safe; distinct problems may be used from distinct threads.
+ */
+#ifndef PT_H_
+#define PT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PT_OK = 0,
+  PT_EINVAL = 1,     /* invalid argument (sizes, pointers, options) */
+  PT_ENOMEM = 2,     /* device allocation failed */
+  PT_ENOTCONV = 3,   /* max_it reached before tol; outputs are still written */
+  PT_EDIVERGED = 4,  /* residual became non-finite or grew past 1e30 */
+  PT_ECUDA = 5,      /* a CUDA runtime call failed */
+  PT_ETIMEOUT = 6,   /* a bounded wait expired */
+  PT_EBUSY = 7       /* resource busy (e.g. server queue full) */
+} pt_status;
+
+typedef struct {
+  int dim;  /* 1, 2 or 3 */
+  int n[3]; /* interior points per axis (entries beyond dim ignored) */
+} pt_grid;
+
+typedef enum { PT_TRIG_ONE = 0, PT_TRIG_SIN = 1, PT_TRIG_COS = 2 } pt_trig;
+
+/* Coefficient a(x,t) = a0 + c * prod_d g_d(pi*mx[d]*x_d) * g_t(pi*mt*t), g in {1, sin, cos};
+ * must stay positive on the grid (A_n symmetric positive definite, §2). */
+typedef struct {
+  double a0;
+  double c;
+  int fx[3];    /* pt_trig per axis */
+  double mx[3];
+  int ft;       /* pt_trig in time */
+  double mt;
+} pt_coeff;
+
+enum { PT_PREC_FP64 = 0, PT_PREC_MIXED = 1 };
+enum { PT_SOLVER_MG = 0, PT_SOLVER_EXACT_1D = 1 };
+
+typedef struct {
+  int precision;         /* PT_PREC_FP64: everything in FP64.  PT_PREC_MIXED: preconditioner
+                            (V-cycles, DSTs, block solves) in FP32; residuals, dot products
+                            and the updates of u and p in FP64 (iterative refinement). */
+  double omega;          /* Uzawa damping (§3, eq. 3.1); <= 0 selects 0.5 */
+  int spatial_solver;    /* PT_SOLVER_MG, or PT_SOLVER_EXACT_1D (dim == 1 only) */
+  int n_vcycles;         /* V-cycles per spatial solve; 0 selects 1 */
+  double jacobi_weight;  /* weighted-Jacobi smoothing weight; <= 0 selects 2/3, 4/5, 6/7 by dim */
+  void* stream;          /* cudaStream_t for all work of this problem; NULL = default stream */
+  int check_every;       /* iterations between host polls of the device convergence flag; 0 = auto */
+  int reserved[7];       /* must be zero */
+} pt_options;
+
+typedef struct pt_problem pt_problem; /* opaque, library-owned */
+
+/* Create a problem and upload its data.
+ *   grid, N_t >= 1, T > 0, coeff: the PDE and its discretisation (see above).
+ *   f  : [N_t][n_s] values f(x_i, t_n), n = 1..N_t (host or device, see f_on_device); required.
+ *   u0 : [n_s] initial datum u_I, or NULL for zero.
+ *   opts: may be NULL (all defaults).
+ * Forms F = [tau f_1 + u0, tau f_2, ..., tau f_N] on the device (§2, after eq. 2.4),
+ * allocates all device state, and returns the handle in *out.
+ * Errors: PT_EINVAL (bad sizes/options/pointers), PT_ENOMEM, PT_ECUDA. */
+pt_status pt_problem_create(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff,
+                            const double* f, int f_on_device, const double* u0, int u0_on_device,
+                            const pt_options* opts, pt_problem** out);
+
+/* Replace the source f (and u0) of an existing problem; same layouts as pt_problem_create. */
+pt_status pt_problem_set_rhs(pt_problem* p, const double* f, int f_on_device, const double* u0,
+                             int u0_on_device);
+
+/* Inexact Uzawa (§3, eq. 3.1) from u = p = 0 until ||F - B u_j|| / ||F|| <= tol or max_it updates.
+ *   u_out   : [N_t][n_s] solution u_1..u_N (host or device per u_out_on_device), or NULL.
+ *   res_hist: host array of max_it + 1 doubles receiving ||F - B u_j||/||F||, j = 0..iters
+ *             (res_hist[0] = 1); or NULL.
+ *   iters   : host int receiving the number of updates performed; or NULL.
+ * Returns PT_OK, PT_ENOTCONV (u_out still written) or PT_EDIVERGED, or an error. */
+pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_out_on_device,
+                   double* res_hist, int* iters);
+
+/* Copy the current iterates u_j and p_j (packed [N_t][n_s], FP64) of the problem's last solve.
+ * The pair (u_j, p_j) is the complete state of the stationary Uzawa iteration (a checkpoint).
+ * Either output may be NULL; on_device selects device (1) or host (0) memory for both. */
+pt_status pt_problem_get_state(pt_problem* p, double* u_out, double* p_out, int on_device);
+
+/* Release all device memory of the problem; NULL is ignored. */
+void pt_problem_destroy(pt_problem* p);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* pt_last_error(void);
+const char* pt_status_string(pt_status s);
+
+/* ---- Component entry points (device buffers, packed [N_t][n_s] FP64) ----------------
+ * They run one stage of the method on the problem's grid, coefficient and stream, with the
+ * problem's precision, and are what the per-kernel parity tests call.  in and out may not
+ * alias.  Errors: PT_EINVAL on NULL pointers, PT_ECUDA. */
+
+/* out = B u = (K (x) I) u + diag(tau A_n) u, u_0 := 0  (§2, eq. 2.3-2.4). */
+pt_status pt_apply_B(pt_problem* p, const double* u_dev, double* out_dev);
+
+/* out = Phi^-T r: out_k = sum_n r_n sin((2k-1) n pi / (2N)), k = 1..N (§4, eq. 4.3 transposed). */
+pt_status pt_dst_forward(pt_problem* p, const double* r_dev, double* out_dev);
+
+/* out = Phi^-1 y: out_n = sum_k y_k sin((2k-1) n pi / (2N)), n = 1..N (§4, eq. 4.3). */
+pt_status pt_dst_inverse(pt_problem* p, const double* y_dev, double* out_dev);
+
+/* out = A~^-1 r: slice n gets the spatial solver of tau A_n (one or more V-cycles, or the exact
+ * tridiagonal solve in 1-D) applied to r_n (§3, eq. 3.2). */
+pt_status pt_precond_A(pt_problem* p, const double* r_dev, double* out_dev);
+
+/* out = H~^-1 r = Phi^-1 Hhat~^-1 Phi^-T r with Hhat~_k^-1 = (2 tau/N) H~_k^-1 Abar H~_k^-1,
+ * H_k = mu_k I + tau Abar, mu_k = 2 sin((2k-1) pi/(4N))  (§4, eq. 4.4-4.6). */
+pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev);
+
+/* Number of kernel launches issued by this library since load (all problems); used to report
+ * how many GPU kernels a timed region launched. */
+unsigned long long pt_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H_ */

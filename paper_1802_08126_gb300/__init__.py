@@ -1,0 +1,175 @@
+"""GB300-native time-parallel inexact Uzawa solver for parabolic problems.
+
+Python binding of the C ABI in ``include/pt.h``: argument marshalling only, every step of the
+solver runs in the CUDA library ``_lib/libptuzawa.so`` (built by ``build.build()``).  PyTorch is
+used only to hold device memory and to name streams.
+
+Method (Neumüller & Smears, "Time-parallel iterative solvers for parabolic evolution
+equations"): implicit Euler over all N_t steps at once (§2, eq. 2.1-2.4), rewritten as the
+symmetric saddle-point system of eq. 2.7 and solved by the inexact Uzawa iteration of §3,
+eq. 3.1 with the DST-in-time Schur-complement preconditioner of §4, eq. 4.4-4.6.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import PT_EDIVERGED, PT_ENOTCONV, PT_OK  # noqa: F401
+
+__all__ = ["Problem", "PtError", "launch_count", "status_name"]
+
+
+class PtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (status_name(status), msg))
+        self.status = status
+
+
+def status_name(status: int) -> str:
+    return _lib.load().pt_status_string(int(status)).decode()
+
+
+def _check(status: int, allowed=(PT_OK,)):
+    if status not in allowed:
+        raise PtError(status, _lib.load().pt_last_error().decode())
+    return status
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library so far (all problems)."""
+    return int(_lib.load().pt_kernel_launch_count())
+
+
+def _ptr(a) -> tuple:
+    """(address, on_device) of a NumPy array or a torch tensor; None -> (None, 0)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    # torch tensor
+    if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    return a.data_ptr(), (1 if a.is_cuda else 0)
+
+
+def _coeff(c) -> _lib.Coeff:
+    k = _lib.Coeff()
+    k.a0 = float(c.a0)
+    k.c = float(c.c)
+    for d in range(3):
+        k.fx[d] = int(c.fx[d])
+        k.mx[d] = float(c.mx[d])
+    k.ft = int(c.ft)
+    k.mt = float(c.mt)
+    return k
+
+
+class Problem:
+    """One time-global problem resident on the GPU (wraps ``pt_problem``).
+
+    ``coeff`` is any object with attributes a0, c, fx[3], mx[3], ft, mt (see ``pt_coeff``).
+    ``f``: [N][n_s] source values, NumPy (host) or torch CUDA tensor (device), float64.
+    """
+
+    def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff, f, u0=None,
+                 precision: str = "fp64", omega: float = 0.0, solver: str = "mg",
+                 stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0):
+        L = _lib.load()
+        self._lib = L
+        self.dim, self.n, self.N, self.T = dim, list(n)[:dim], N, float(T)
+        self.ns = int(np.prod(self.n))
+        g = _lib.Grid()
+        g.dim = dim
+        for d in range(3):
+            g.n[d] = int(n[d]) if d < dim else 1
+        opts = _lib.Options()
+        opts.precision = {"fp64": _lib.PT_PREC_FP64, "mixed": _lib.PT_PREC_MIXED}[precision]
+        opts.omega = float(omega)
+        opts.spatial_solver = {"mg": _lib.PT_SOLVER_MG, "exact": _lib.PT_SOLVER_EXACT_1D}[solver]
+        opts.n_vcycles = 0
+        opts.jacobi_weight = float(jacobi_weight)
+        opts.stream = stream
+        opts.check_every = int(check_every)
+        self._opts = opts
+        fp, fdev = _ptr(f)
+        up, udev = _ptr(u0)
+        h = ctypes.c_void_p()
+        _check(L.pt_problem_create(ctypes.byref(g), int(N), float(T), ctypes.byref(_coeff(coeff)),
+                                   fp, fdev, up, udev, ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_rhs(self, f, u0=None):
+        fp, fdev = _ptr(f)
+        up, udev = _ptr(u0)
+        _check(self._lib.pt_problem_set_rhs(self._h, fp, fdev, up, udev))
+
+    def solve(self, tol: float, max_it: int, u_out=None, with_history: bool = True):
+        """Run the Uzawa iteration; returns (status, iters, history).
+
+        ``u_out`` (NumPy or torch, [N][n_s] float64) receives the solution if given.
+        ``status`` is PT_OK, PT_ENOTCONV or PT_EDIVERGED (other statuses raise)."""
+        up, udev = _ptr(u_out)
+        hist = np.zeros(max_it + 1) if with_history else None
+        it = ctypes.c_int(0)
+        hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None
+        st = _check(self._lib.pt_solve(self._h, float(tol), int(max_it), up, udev, hp, ctypes.byref(it)),
+                    allowed=(PT_OK, PT_ENOTCONV, PT_EDIVERGED))
+        return st, it.value, (hist[: it.value + 1] if hist is not None else None)
+
+    def get_state(self, u_out=None, p_out=None):
+        """Copy the current iterates (u_j, p_j) into the given arrays (both host or both device)."""
+        up, udev = _ptr(u_out)
+        pp, pdev = _ptr(p_out)
+        if u_out is not None and p_out is not None and udev != pdev:
+            raise ValueError("u_out and p_out must both be host or both be device arrays")
+        _check(self._lib.pt_problem_get_state(self._h, up, pp, udev or pdev))
+        return u_out, p_out
+
+    def _component(self, name: str, x, out):
+        xp, xdev = _ptr(x)
+        op, odev = _ptr(out)
+        if not (xdev and odev):
+            raise ValueError("component calls take device tensors")
+        _check(getattr(self._lib, name)(self._h, xp, op))
+        return out
+
+    def apply_B(self, u, out):
+        return self._component("pt_apply_B", u, out)
+
+    def dst_forward(self, r, out):
+        return self._component("pt_dst_forward", r, out)
+
+    def dst_inverse(self, y, out):
+        return self._component("pt_dst_inverse", y, out)
+
+    def precond_A(self, r, out):
+        return self._component("pt_precond_A", r, out)
+
+    def precond_H(self, r, out):
+        return self._component("pt_precond_H", r, out)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pt_problem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,716 @@
+// C ABI of the solver (include/pt.h): problem set-up, the inexact Uzawa loop of §3, eq. 3.1,
+// and the component entry points.  All arithmetic runs in the kernels of the other
+// translation units; this file owns device memory, tables and the launch sequence.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pt_internal.cuh"
+
+namespace {
+thread_local std::string g_err;
+std::atomic<unsigned long long> g_launches{0};
+
+pt_status fail(pt_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define PT_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA,                \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                                    \
+  } while (0)
+
+#define PT_CHECK_LAUNCH()                                                                \
+  do {                                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess) return fail(PT_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+double trig(int kind, double arg) {
+  if (kind == PT_TRIG_SIN) return std::sin(arg);
+  if (kind == PT_TRIG_COS) return std::cos(arg);
+  return 1.0;
+}
+}  // namespace
+
+namespace pt {
+void note_launch(int count) { g_launches.fetch_add((unsigned long long)count, std::memory_order_relaxed); }
+}  // namespace pt
+
+using namespace pt;
+
+struct pt_problem {
+  int dim = 0, n = 0, N = 0, logN = 0;
+  double T = 0.0, tau = 0.0;
+  pt_coeff coeff{};
+  pt_options opt{};
+  int mixed = 0;
+  int exact1d = 0;
+  double omega = 0.5;
+  double jacobi = 0.0;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  int nlev = 0, lc = 0;
+  Level lev[kMaxLevels];
+  long long ns = 0;   // interior points per slice
+  // device memory
+  std::vector<void*> allocs;
+  double *u = nullptr, *p = nullptr, *F = nullptr;
+  void *W1 = nullptr, *W2 = nullptr;            // preconditioner precision, fine level
+  void* mg_b[kMaxLevels] = {};
+  void* mg_x[kMaxLevels] = {};
+  void* mg_r[kMaxLevels] = {};
+  double* tab_d = nullptr;
+  float* tab_f = nullptr;
+  double* cth_d = nullptr;                      // [N] c * g_t(pi m_t t_n)
+  void* sigA = nullptr;                         // [N] zeros       (precond precision)
+  void* cthA = nullptr;                         // [N] c g_t(t_n)
+  void* sigH = nullptr;                         // [N] mu_k
+  void* cthH = nullptr;                         // [N] c * mean_n g_t(t_n)
+  double cthbar = 0.0;
+  void* dst_tw = nullptr;                       // [N/2] complex
+  void* dst_pre = nullptr;                      // [N] complex
+  void* tri_work = nullptr;
+  double* partials = nullptr;
+  SolveState* state = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  double* tmpA = nullptr;                       // FP64 padded scratch for component calls
+  double* tmpB = nullptr;
+  SolveState* host_state = nullptr;             // pinned
+  size_t bytes = 0;
+};
+
+namespace {
+
+// Zero elements in front of slot 0: the lowest index a kernel reads is the diagonal corner
+// (-1, -1, -1) of the prolongation, at -(P^(d-1) + ... + P + 1).
+long long padded_guard(const Level& L, int dim) {
+  long long g = 0, pk = 1;
+  for (int d = 0; d < dim; ++d) {
+    g += pk;
+    pk *= L.P;
+  }
+  return (g + 31) & ~31LL;
+}
+
+template <typename T>
+T* alloc_padded(pt_problem* p, const Level& L, int slots, pt_status* st) {
+  const long long guard = padded_guard(L, p->dim);
+  const size_t count = (size_t)(guard + L.S * (long long)slots + 64);
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *st = fail(PT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return nullptr;
+  }
+  p->allocs.push_back(ptr);
+  p->bytes += count * sizeof(T);
+  e = cudaMemsetAsync(ptr, 0, count * sizeof(T), p->st);
+  if (e != cudaSuccess) {
+    *st = fail(PT_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    return nullptr;
+  }
+  return (T*)ptr + guard;
+}
+
+void* alloc_bytes(pt_problem* p, size_t bytes, pt_status* st) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    *st = fail(PT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return nullptr;
+  }
+  p->allocs.push_back(ptr);
+  p->bytes += bytes;
+  return ptr;
+}
+
+template <typename T>
+pt_status upload(pt_problem* p, void* dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.begin(), src.end());
+  PT_CUDA(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, p->st));
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  return PT_OK;
+}
+
+template <typename T>
+StencilGeom<T> geom(const pt_problem* p, int l) {
+  StencilGeom<T> g;
+  g.dim = p->dim;
+  g.n = p->lev[l].n;
+  g.P = p->lev[l].P;
+  g.logP = p->lev[l].logP;
+  g.S = p->lev[l].S;
+  g.tab = (sizeof(T) == 8 ? (const T*)(const void*)p->tab_d : (const T*)(const void*)p->tab_f) + p->lev[l].tab;
+  g.a0 = (T)p->coeff.a0;
+  g.h2inv = (T)(1.0 / (p->lev[l].h * p->lev[l].h));
+  return g;
+}
+
+template <typename T>
+MGPlan<T> mg_plan(const pt_problem* p) {
+  MGPlan<T> m;
+  m.dim = p->dim;
+  m.nlev = p->nlev;
+  m.lc = p->lc;
+  for (int l = 0; l < p->nlev; ++l) {
+    m.lev[l] = p->lev[l];
+    m.buf[l].b = p->mg_b[l];
+    m.buf[l].x = p->mg_x[l];
+    m.buf[l].r = p->mg_r[l];
+  }
+  m.tab = sizeof(T) == 8 ? (const T*)(const void*)p->tab_d : (const T*)(const void*)p->tab_f;
+  m.a0 = (T)p->coeff.a0;
+  m.B = p->N;
+  return m;
+}
+
+template <typename T>
+OpBatch<T> op_A(const pt_problem* p) {
+  OpBatch<T> o;
+  o.sig = (const T*)p->sigA;
+  o.cth = (const T*)p->cthA;
+  o.s = (T)p->tau;
+  o.omega = (T)p->jacobi;
+  return o;
+}
+
+template <typename T>
+OpBatch<T> op_H(const pt_problem* p) {
+  OpBatch<T> o;
+  o.sig = (const T*)p->sigH;
+  o.cth = (const T*)p->cthH;
+  o.s = (T)p->tau;
+  o.omega = (T)p->jacobi;
+  return o;
+}
+
+template <typename T>
+DstPlan<T> dst_plan(const pt_problem* p) {
+  DstPlan<T> d;
+  d.N = p->N;
+  d.logN = p->logN;
+  d.tw = (const T*)p->dst_tw;
+  d.pre = (const T*)p->dst_pre;
+  return d;
+}
+
+// A~^-1 applied to rhs b (precision T, fine padded) -> out (mode 0 write T, mode 1 += into FP64)
+template <typename T>
+void apply_precond_A(pt_problem* p, const T* b, void* out, int mode, int out_fp64, const int* done) {
+  if (p->exact1d) {
+    launch_tridiag<T>(b, out, mode, out_fp64, geom<T>(p, 0), op_A<T>(p), p->N, (T*)p->tri_work, done,
+                      p->st);
+  } else {
+    vcycle<T>(mg_plan<T>(p), op_A<T>(p), b, out, mode, out_fp64, done, p->st);
+  }
+}
+
+// H_k solve (exact in 1-D if requested, else one V-cycle)
+template <typename T>
+void apply_Hk_solve(pt_problem* p, const T* b, T* out, const int* done) {
+  if (p->exact1d)
+    launch_tridiag<T>(b, out, 0, 0, geom<T>(p, 0), op_H<T>(p), p->N, (T*)p->tri_work, done, p->st);
+  else
+    vcycle<T>(mg_plan<T>(p), op_H<T>(p), b, out, 0, 0, done, p->st);
+}
+
+// W1 = rhat (in place transform done by caller) -> W2 = yhat = (2 tau/N) H~^-1 Abar H~^-1 rhat
+template <typename T>
+void block_solve(pt_problem* p, const int* done) {
+  T* W1 = (T*)p->W1;
+  T* W2 = (T*)p->W2;
+  apply_Hk_solve<T>(p, W1, W2, done);
+  launch_apply_A_scaled<T>(W2, W1, geom<T>(p, 0), (T)p->cthbar, (T)(2.0 * p->tau / p->N), p->N, done,
+                           p->st);
+  apply_Hk_solve<T>(p, W1, W2, done);
+}
+
+template <typename T>
+pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* res_hist) {
+  const long long total = p->lev[0].S * p->N;
+  const int* done = &p->state->done;
+  // fresh start: u = p = 0, ||F||^2
+  PT_CUDA(cudaMemsetAsync(p->u, 0, sizeof(double) * total, p->st));
+  PT_CUDA(cudaMemsetAsync(p->p, 0, sizeof(double) * total, p->st));
+  launch_norm2_partials(p->F, total, p->partials, p->st);
+  launch_finalize_fnorm(p->partials, p->state, p->st);
+  PT_CHECK_LAUNCH();
+  const StencilGeom<double> g = geom<double>(p, 0);
+  int check = p->opt.check_every;
+  if (check <= 0) check = total >= (1LL << 22) ? 1 : 8;
+  T* W1 = (T*)p->W1;
+  T* W2 = (T*)p->W2;
+  const DstPlan<T> dp = dst_plan<T>(p);
+  for (int j = 0; j <= max_it; ++j) {
+    launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, p->tau, p->N, done, p->st);
+    apply_precond_A<T>(p, W1, p->p, 1, 1, done);
+    launch_resid_u<T>(p->u, p->p, p->F, W1, p->partials, g, p->cth_d, p->tau, p->N, done, p->st);
+    launch_finalize_residual(p->partials, p->state, p->hist, j, tol, max_it, p->st);
+    if (j < max_it) {
+      launch_dst_forward<T>(W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
+      block_solve<T>(p, done);
+      launch_dst_inverse<T>(W2, p->u, 1, p->omega, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done,
+                            p->st);
+    }
+    PT_CHECK_LAUNCH();
+    if ((j + 1) % check == 0 || j == max_it) {
+      PT_CUDA(cudaMemcpyAsync(p->host_state, p->state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->st));
+      PT_CUDA(cudaStreamSynchronize(p->st));
+      if (p->host_state->done) break;
+    }
+  }
+  PT_CUDA(cudaMemcpyAsync(p->host_state, p->state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->st));
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  const SolveState hs = *p->host_state;
+  if (!hs.done) return fail(PT_ECUDA, "solver state not finalised");
+  if (iters_out) *iters_out = hs.iters;
+  if (res_hist) {
+    PT_CUDA(cudaMemcpyAsync(res_hist, p->hist, sizeof(double) * (hs.iters + 1), cudaMemcpyDeviceToHost, p->st));
+    PT_CUDA(cudaStreamSynchronize(p->st));
+  }
+  if (hs.status == PT_ENOTCONV) g_err = "max_it reached before tol";
+  if (hs.status == PT_EDIVERGED) g_err = "residual became non-finite";
+  return (pt_status)hs.status;
+}
+
+bool is_pow2(long long v) { return v >= 1 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+  int l = 0;
+  while ((1LL << l) < v) ++l;
+  return l;
+}
+
+pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff, const pt_options* o) {
+  if (!grid || !coeff) return fail(PT_EINVAL, "grid and coeff are required");
+  if (grid->dim < 1 || grid->dim > 3) return fail(PT_EINVAL, "dim must be 1, 2 or 3");
+  for (int d = 0; d < grid->dim; ++d) {
+    if (grid->n[d] != grid->n[0]) return fail(PT_EINVAL, "all axes must have the same n");
+    if (grid->n[d] < 1 || !is_pow2((long long)grid->n[d] + 1))
+      return fail(PT_EINVAL, "n + 1 must be a power of two >= 2");
+  }
+  if (grid->n[0] > 32767) return fail(PT_EINVAL, "n too large");
+  if (N_t < 1 || !is_pow2(N_t) || N_t > 8192) return fail(PT_EINVAL, "N_t must be a power of two in [1, 8192]");
+  if (!(T > 0.0) || !std::isfinite(T)) return fail(PT_EINVAL, "T must be positive");
+  if (!std::isfinite(coeff->a0) || !std::isfinite(coeff->c)) return fail(PT_EINVAL, "non-finite coefficient");
+  if (std::fabs(coeff->c) >= coeff->a0) return fail(PT_EINVAL, "need |c| < a0 so that a > 0");
+  for (int d = 0; d < 3; ++d)
+    if (coeff->fx[d] < 0 || coeff->fx[d] > 2) return fail(PT_EINVAL, "fx must be a pt_trig");
+  if (coeff->ft < 0 || coeff->ft > 2) return fail(PT_EINVAL, "ft must be a pt_trig");
+  if (o) {
+    if (o->precision != PT_PREC_FP64 && o->precision != PT_PREC_MIXED) return fail(PT_EINVAL, "bad precision");
+    if (o->spatial_solver != PT_SOLVER_MG && o->spatial_solver != PT_SOLVER_EXACT_1D)
+      return fail(PT_EINVAL, "bad spatial_solver");
+    if (o->spatial_solver == PT_SOLVER_EXACT_1D && grid->dim != 1)
+      return fail(PT_EINVAL, "exact spatial solves are available in 1-D only");
+    if (o->n_vcycles > 1) return fail(PT_EINVAL, "n_vcycles > 1 is not supported");
+    for (int i = 0; i < 7; ++i)
+      if (o->reserved[i] != 0) return fail(PT_EINVAL, "reserved options must be zero");
+  }
+  return PT_OK;
+}
+
+template <typename T>
+pt_status setup_precision(pt_problem* p) {
+  pt_status st = PT_OK;
+  const Level& L0 = p->lev[0];
+  p->W1 = alloc_padded<T>(p, L0, p->N, &st);
+  if (!p->W1) return st;
+  p->W2 = alloc_padded<T>(p, L0, p->N, &st);
+  if (!p->W2) return st;
+  if (!p->exact1d) {
+    for (int l = 0; l <= p->lc && l < p->nlev; ++l) {
+      if (l > 0) {
+        p->mg_b[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
+        if (!p->mg_b[l]) return st;
+      }
+      p->mg_x[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
+      if (!p->mg_x[l]) return st;
+      if (l < p->lc) {
+        p->mg_r[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
+        if (!p->mg_r[l]) return st;
+      }
+    }
+  } else {
+    p->tri_work = alloc_bytes(p, sizeof(T) * 2 * (size_t)L0.P * p->N, &st);
+    if (!p->tri_work) return st;
+  }
+  // per-slice operator parameters
+  std::vector<double> zeros(p->N, 0.0), cthA(p->N), mu(p->N), cthH(p->N, p->cthbar);
+  for (int i = 0; i < p->N; ++i) {
+    cthA[i] = p->coeff.c * trig(p->coeff.ft, M_PI * p->coeff.mt * (i + 1) * p->tau);
+    mu[i] = 2.0 * std::sin((2.0 * (i + 1) - 1.0) * M_PI / (4.0 * p->N));
+  }
+  const size_t nb = sizeof(T) * p->N;
+  if (!(p->sigA = alloc_bytes(p, nb, &st))) return st;
+  if (!(p->cthA = alloc_bytes(p, nb, &st))) return st;
+  if (!(p->sigH = alloc_bytes(p, nb, &st))) return st;
+  if (!(p->cthH = alloc_bytes(p, nb, &st))) return st;
+  if ((st = upload<T>(p, p->sigA, zeros)) != PT_OK) return st;
+  if ((st = upload<T>(p, p->cthA, cthA)) != PT_OK) return st;
+  if ((st = upload<T>(p, p->sigH, mu)) != PT_OK) return st;
+  if ((st = upload<T>(p, p->cthH, cthH)) != PT_OK) return st;
+  // DST tables: twiddles e^{2 pi i k/N}, k < N/2, and e^{i pi m/(2N)}, m < N
+  std::vector<double> tw(2 * std::max(1, p->N / 2)), pre(2 * p->N);
+  for (int k = 0; k < p->N / 2; ++k) {
+    tw[2 * k] = std::cos(2.0 * M_PI * k / p->N);
+    tw[2 * k + 1] = std::sin(2.0 * M_PI * k / p->N);
+  }
+  if (p->N == 1) {
+    tw[0] = 1.0;
+    tw[1] = 0.0;
+  }
+  for (int m = 0; m < p->N; ++m) {
+    pre[2 * m] = std::cos(M_PI * m / (2.0 * p->N));
+    pre[2 * m + 1] = std::sin(M_PI * m / (2.0 * p->N));
+  }
+  if (!(p->dst_tw = alloc_bytes(p, sizeof(T) * tw.size(), &st))) return st;
+  if (!(p->dst_pre = alloc_bytes(p, sizeof(T) * pre.size(), &st))) return st;
+  if ((st = upload<T>(p, p->dst_tw, tw)) != PT_OK) return st;
+  if ((st = upload<T>(p, p->dst_pre, pre)) != PT_OK) return st;
+  return PT_OK;
+}
+
+pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, int u0_dev) {
+  if (!f) return fail(PT_EINVAL, "f is required");
+  const size_t fbytes = sizeof(double) * (size_t)p->ns * p->N;
+  const double* fd = f;
+  const double* u0d = u0;
+  void* tf = nullptr;
+  void* tu = nullptr;
+  if (!f_dev) {
+    PT_CUDA(cudaMallocAsync(&tf, fbytes, p->st));
+    PT_CUDA(cudaMemcpyAsync(tf, f, fbytes, cudaMemcpyHostToDevice, p->st));
+    fd = (const double*)tf;
+  }
+  if (u0 && !u0_dev) {
+    PT_CUDA(cudaMallocAsync(&tu, sizeof(double) * p->ns, p->st));
+    PT_CUDA(cudaMemcpyAsync(tu, u0, sizeof(double) * p->ns, cudaMemcpyHostToDevice, p->st));
+    u0d = (const double*)tu;
+  }
+  const Level& L = p->lev[0];
+  launch_pack(fd, u0d, p->F, p->tau, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+  PT_CHECK_LAUNCH();
+  if (tf) PT_CUDA(cudaFreeAsync(tf, p->st));
+  if (tu) PT_CUDA(cudaFreeAsync(tu, p->st));
+  return PT_OK;
+}
+
+pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff, const double* f,
+                      int f_dev, const double* u0, int u0_dev, const pt_options* opts, pt_problem* p) {
+  pt_status st = PT_OK;
+  PT_CUDA(cudaGetDevice(&p->device));
+  p->dim = grid->dim;
+  p->n = grid->n[0];
+  p->N = N_t;
+  p->logN = ilog2(N_t);
+  p->T = T;
+  p->tau = T / N_t;
+  p->coeff = *coeff;
+  if (opts) p->opt = *opts;
+  p->mixed = p->opt.precision == PT_PREC_MIXED;
+  p->exact1d = p->opt.spatial_solver == PT_SOLVER_EXACT_1D;
+  p->omega = p->opt.omega > 0.0 ? p->opt.omega : 0.5;
+  p->jacobi = p->opt.jacobi_weight > 0.0 ? p->opt.jacobi_weight
+                                         : (p->dim == 1 ? 2.0 / 3.0 : (p->dim == 2 ? 0.8 : 6.0 / 7.0));
+  p->st = (cudaStream_t)p->opt.stream;
+  // levels
+  const int P0 = p->n + 1;
+  p->nlev = 0;
+  for (int P = P0; P >= 2; P >>= 1) {
+    Level& L = p->lev[p->nlev];
+    L.P = P;
+    L.n = P - 1;
+    L.logP = ilog2(P);
+    L.S = 1;
+    for (int d = 0; d < p->dim; ++d) L.S *= P;
+    L.h = 1.0 / P;
+    L.guard = padded_guard(L, p->dim);
+    ++p->nlev;
+  }
+  p->lc = p->nlev - 1;
+  for (int l = 0; l < p->nlev; ++l)
+    if (p->lev[l].S <= kCoarseMaxElems) {
+      p->lc = l;
+      break;
+    }
+  p->ns = 1;
+  for (int d = 0; d < p->dim; ++d) p->ns *= p->n;
+  // coefficient tables (node and face values of g_d per level)
+  std::vector<double> tab;
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& L = p->lev[l];
+    L.tab = (long long)tab.size();
+    for (int d = 0; d < p->dim; ++d) {
+      for (int i = 0; i < L.P; ++i)
+        tab.push_back(i < L.n ? trig(coeff->fx[d], M_PI * coeff->mx[d] * (i + 1) * L.h) : 0.0);
+      for (int j = 0; j < L.P; ++j) tab.push_back(trig(coeff->fx[d], M_PI * coeff->mx[d] * (j + 0.5) * L.h));
+    }
+  }
+  if (!(p->tab_d = (double*)alloc_bytes(p, sizeof(double) * tab.size(), &st))) return st;
+  if (!(p->tab_f = (float*)alloc_bytes(p, sizeof(float) * tab.size(), &st))) return st;
+  if ((st = upload<double>(p, p->tab_d, tab)) != PT_OK) return st;
+  if ((st = upload<float>(p, p->tab_f, tab)) != PT_OK) return st;
+  // time factors; reference coefficient = mean over the N steps (face-wise mean of the A_n)
+  std::vector<double> cth(p->N);
+  double mean = 0.0;
+  for (int i = 0; i < p->N; ++i) {
+    const double g = trig(coeff->ft, M_PI * coeff->mt * (i + 1) * p->tau);
+    cth[i] = coeff->c * g;
+    mean += g;
+  }
+  p->cthbar = coeff->c * (mean / p->N);
+  if (!(p->cth_d = (double*)alloc_bytes(p, sizeof(double) * p->N, &st))) return st;
+  if ((st = upload<double>(p, p->cth_d, cth)) != PT_OK) return st;
+  // state vectors
+  const Level& L0 = p->lev[0];
+  if (!(p->u = alloc_padded<double>(p, L0, p->N, &st))) return st;
+  if (!(p->p = alloc_padded<double>(p, L0, p->N, &st))) return st;
+  if (!(p->F = alloc_padded<double>(p, L0, p->N, &st))) return st;
+  st = p->mixed ? setup_precision<float>(p) : setup_precision<double>(p);
+  if (st != PT_OK) return st;
+  if (!(p->partials = (double*)alloc_bytes(p, sizeof(double) * kReduceBlocks, &st))) return st;
+  if (!(p->state = (SolveState*)alloc_bytes(p, sizeof(SolveState), &st))) return st;
+  PT_CUDA(cudaMemsetAsync(p->state, 0, sizeof(SolveState), p->st));
+  PT_CUDA(cudaMallocHost((void**)&p->host_state, sizeof(SolveState)));
+  return load_rhs(p, f, f_dev, u0, u0_dev);
+}
+
+template <typename T>
+pt_status pack_into(pt_problem* p, const double* src, T* dst) {
+  const Level& L = p->lev[0];
+  launch_pack_typed<T>(src, dst, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+  PT_CHECK_LAUNCH();
+  return PT_OK;
+}
+
+template <typename T>
+pt_status unpack_from(pt_problem* p, const T* src, double* dst) {
+  const Level& L = p->lev[0];
+  launch_unpack<T>(src, dst, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+  PT_CHECK_LAUNCH();
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  return PT_OK;
+}
+
+pt_status ensure_tmp(pt_problem* p) {
+  pt_status st = PT_OK;
+  if (!p->tmpA && !(p->tmpA = alloc_padded<double>(p, p->lev[0], p->N, &st))) return st;
+  if (!p->tmpB && !(p->tmpB = alloc_padded<double>(p, p->lev[0], p->N, &st))) return st;
+  return PT_OK;
+}
+
+template <typename T>
+pt_status comp_dst_forward(pt_problem* p, const double* r, double* out) {
+  pt_status st;
+  if ((st = pack_into<T>(p, r, (T*)p->W1)) != PT_OK) return st;
+  launch_dst_forward<T>((T*)p->W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dst_plan<T>(p), nullptr, p->st);
+  PT_CHECK_LAUNCH();
+  return unpack_from<T>(p, (const T*)p->W1, out);
+}
+
+template <typename T>
+pt_status comp_dst_inverse(pt_problem* p, const double* y, double* out) {
+  pt_status st;
+  if ((st = pack_into<T>(p, y, (T*)p->W1)) != PT_OK) return st;
+  launch_dst_inverse<T>((const T*)p->W1, p->W2, 0, 1.0, p->lev[0].S, p->dim, p->n, p->lev[0].logP,
+                        dst_plan<T>(p), nullptr, p->st);
+  PT_CHECK_LAUNCH();
+  return unpack_from<T>(p, (const T*)p->W2, out);
+}
+
+template <typename T>
+pt_status comp_precond_A(pt_problem* p, const double* r, double* out) {
+  pt_status st;
+  if ((st = pack_into<T>(p, r, (T*)p->W1)) != PT_OK) return st;
+  apply_precond_A<T>(p, (const T*)p->W1, p->W2, 0, 0, nullptr);
+  PT_CHECK_LAUNCH();
+  return unpack_from<T>(p, (const T*)p->W2, out);
+}
+
+template <typename T>
+pt_status comp_precond_H(pt_problem* p, const double* r, double* out) {
+  pt_status st;
+  if ((st = pack_into<T>(p, r, (T*)p->W1)) != PT_OK) return st;
+  launch_dst_forward<T>((T*)p->W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dst_plan<T>(p), nullptr, p->st);
+  block_solve<T>(p, nullptr);
+  launch_dst_inverse<T>((const T*)p->W2, p->W1, 0, 1.0, p->lev[0].S, p->dim, p->n, p->lev[0].logP,
+                        dst_plan<T>(p), nullptr, p->st);
+  PT_CHECK_LAUNCH();
+  return unpack_from<T>(p, (const T*)p->W1, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pt_last_error(void) { return g_err.c_str(); }
+
+const char* pt_status_string(pt_status s) {
+  switch (s) {
+    case PT_OK: return "PT_OK";
+    case PT_EINVAL: return "PT_EINVAL";
+    case PT_ENOMEM: return "PT_ENOMEM";
+    case PT_ENOTCONV: return "PT_ENOTCONV";
+    case PT_EDIVERGED: return "PT_EDIVERGED";
+    case PT_ECUDA: return "PT_ECUDA";
+    case PT_ETIMEOUT: return "PT_ETIMEOUT";
+    case PT_EBUSY: return "PT_EBUSY";
+  }
+  return "PT_UNKNOWN";
+}
+
+unsigned long long pt_kernel_launch_count(void) { return g_launches.load(); }
+
+pt_status pt_problem_create(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff,
+                            const double* f, int f_on_device, const double* u0, int u0_on_device,
+                            const pt_options* opts, pt_problem** out) {
+  g_err.clear();
+  if (!out) return fail(PT_EINVAL, "out is NULL");
+  *out = nullptr;
+  pt_status st = validate(grid, N_t, T, coeff, opts);
+  if (st != PT_OK) return st;
+  pt_problem* p = new pt_problem();
+  st = create_impl(grid, N_t, T, coeff, f, f_on_device, u0, u0_on_device, opts, p);
+  if (st == PT_OK) {
+    cudaError_t e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) st = fail(PT_ECUDA, cudaGetErrorString(e));
+  }
+  if (st != PT_OK) {
+    pt_problem_destroy(p);
+    return st;
+  }
+  *out = p;
+  return PT_OK;
+}
+
+pt_status pt_problem_set_rhs(pt_problem* p, const double* f, int f_on_device, const double* u0,
+                             int u0_on_device) {
+  g_err.clear();
+  if (!p) return fail(PT_EINVAL, "problem is NULL");
+  PT_CUDA(cudaSetDevice(p->device));
+  return load_rhs(p, f, f_on_device, u0, u0_on_device);
+}
+
+pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_out_on_device,
+                   double* res_hist, int* iters) {
+  g_err.clear();
+  if (!p) return fail(PT_EINVAL, "problem is NULL");
+  if (max_it < 0 || !(tol >= 0.0)) return fail(PT_EINVAL, "need max_it >= 0 and tol >= 0");
+  PT_CUDA(cudaSetDevice(p->device));
+  if (max_it + 1 > p->hist_cap) {
+    pt_status st = PT_OK;
+    if (!(p->hist = (double*)alloc_bytes(p, sizeof(double) * (max_it + 1), &st))) return st;
+    p->hist_cap = max_it + 1;
+  }
+  pt_status st = p->mixed ? uzawa<float>(p, tol, max_it, iters, res_hist)
+                          : uzawa<double>(p, tol, max_it, iters, res_hist);
+  if (st != PT_OK && st != PT_ENOTCONV && st != PT_EDIVERGED) return st;
+  if (u_out) {
+    const Level& L = p->lev[0];
+    const size_t bytes = sizeof(double) * (size_t)p->ns * p->N;
+    double* dst = u_out;
+    void* tmp = nullptr;
+    if (!u_out_on_device) {
+      PT_CUDA(cudaMallocAsync(&tmp, bytes, p->st));
+      dst = (double*)tmp;
+    }
+    launch_unpack<double>(p->u, dst, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+    PT_CHECK_LAUNCH();
+    if (tmp) {
+      PT_CUDA(cudaMemcpyAsync(u_out, tmp, bytes, cudaMemcpyDeviceToHost, p->st));
+      PT_CUDA(cudaFreeAsync(tmp, p->st));
+    }
+    PT_CUDA(cudaStreamSynchronize(p->st));
+  }
+  return st;
+}
+
+pt_status pt_problem_get_state(pt_problem* p, double* u_out, double* p_out, int on_device) {
+  g_err.clear();
+  if (!p) return fail(PT_EINVAL, "problem is NULL");
+  PT_CUDA(cudaSetDevice(p->device));
+  const Level& L = p->lev[0];
+  const size_t bytes = sizeof(double) * (size_t)p->ns * p->N;
+  double* srcs[2] = {p->u, p->p};
+  double* dsts[2] = {u_out, p_out};
+  for (int k = 0; k < 2; ++k) {
+    if (!dsts[k]) continue;
+    double* dst = dsts[k];
+    void* tmp = nullptr;
+    if (!on_device) {
+      PT_CUDA(cudaMallocAsync(&tmp, bytes, p->st));
+      dst = (double*)tmp;
+    }
+    launch_unpack<double>(srcs[k], dst, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+    PT_CHECK_LAUNCH();
+    if (tmp) {
+      PT_CUDA(cudaMemcpyAsync(dsts[k], tmp, bytes, cudaMemcpyDeviceToHost, p->st));
+      PT_CUDA(cudaFreeAsync(tmp, p->st));
+    }
+  }
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  return PT_OK;
+}
+
+void pt_problem_destroy(pt_problem* p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  cudaStreamSynchronize(p->st);
+  for (void* a : p->allocs) cudaFree(a);
+  if (p->host_state) cudaFreeHost(p->host_state);
+  delete p;
+}
+
+pt_status pt_apply_B(pt_problem* p, const double* u_dev, double* out_dev) {
+  g_err.clear();
+  if (!p || !u_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
+  PT_CUDA(cudaSetDevice(p->device));
+  pt_status st = ensure_tmp(p);
+  if (st != PT_OK) return st;
+  if ((st = pack_into<double>(p, u_dev, p->tmpA)) != PT_OK) return st;
+  launch_apply_B(p->tmpA, p->tmpB, geom<double>(p, 0), p->cth_d, p->tau, p->N, p->st);
+  PT_CHECK_LAUNCH();
+  return unpack_from<double>(p, p->tmpB, out_dev);
+}
+
+pt_status pt_dst_forward(pt_problem* p, const double* r_dev, double* out_dev) {
+  g_err.clear();
+  if (!p || !r_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
+  PT_CUDA(cudaSetDevice(p->device));
+  return p->mixed ? comp_dst_forward<float>(p, r_dev, out_dev) : comp_dst_forward<double>(p, r_dev, out_dev);
+}
+
+pt_status pt_dst_inverse(pt_problem* p, const double* y_dev, double* out_dev) {
+  g_err.clear();
+  if (!p || !y_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
+  PT_CUDA(cudaSetDevice(p->device));
+  return p->mixed ? comp_dst_inverse<float>(p, y_dev, out_dev) : comp_dst_inverse<double>(p, y_dev, out_dev);
+}
+
+pt_status pt_precond_A(pt_problem* p, const double* r_dev, double* out_dev) {
+  g_err.clear();
+  if (!p || !r_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
+  PT_CUDA(cudaSetDevice(p->device));
+  return p->mixed ? comp_precond_A<float>(p, r_dev, out_dev) : comp_precond_A<double>(p, r_dev, out_dev);
+}
+
+pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev) {
+  g_err.clear();
+  if (!p || !r_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
+  PT_CUDA(cudaSetDevice(p->device));
+  return p->mixed ? comp_precond_H<float>(p, r_dev, out_dev) : comp_precond_H<double>(p, r_dev, out_dev);
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// Temporal change of basis of the preconditioner (§4, eq. 4.2-4.4): for every spatial point,
+//   forward  (Phi^-T):  rhat_k = sum_{n=1}^N r_n sin((2k-1) n pi / (2N)),   k = 1..N,
+//   inverse  (Phi^-1):  u_n    = sum_{k=1}^N y_k sin((2k-1) n pi / (2N)),   n = 1..N,
+// computed with an N-point complex FFT (the fast splitting §5 refers to), not as sums.
+//
+// Both are reduced to cosine transforms by reflecting the time index (n' = N - n):
+//   inverse: u_{N-m} = sum_j z_j cos(pi (2j+1) m / (2N)) with z_j = (-1)^j y_{j+1}   (DCT-II of z)
+//   forward: rhat_{j+1} = (-1)^j sum_m w_m cos(pi (2j+1) m / (2N)), w_m = r_{N-m}     (DCT-III of w)
+// and the cosine transforms are computed through one complex FFT of length N (Makhoul, IEEE
+// Trans. ASSP 28, 1980): the DCT-II permutes v_j = z_{2j}, v_{N-1-j} = z_{2j+1}, transforms,
+// and takes Re(e^{-i pi m/(2N)} V_m); the DCT-III runs those steps backwards.  Two real columns
+// share one complex FFT (real and imaginary parts).  The FFT is a radix-2 decimation-in-
+// frequency transform in shared memory (natural order in, bit-reversed order out).
+//
+// A CTA owns W = 2C consecutive padded spatial columns for all N time slots, so the transform
+// is done in place with no inter-CTA dependency.  N must be a power of two.
+#include <cmath>
+
+#include "stencil_common.cuh"
+
+namespace pt {
+
+namespace {
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+// Geometry of the padded columns: a column whose spatial coordinates include the ghost index n
+// must stay exactly zero.  (Two real columns share one complex FFT; rounding would otherwise
+// leak a few ulps of the interior partner into a ghost column.)
+struct ColGeom {
+  int dim, n, logP;
+};
+
+__device__ __forceinline__ bool ghost_col(ColGeom g, long long col) {
+  const int P = 1 << g.logP;
+  const int x = (int)(col & (P - 1));
+  const int y = g.dim >= 2 ? (int)((col >> g.logP) & (P - 1)) : 0;
+  const int z = g.dim >= 3 ? (int)((col >> (2 * g.logP)) & (P - 1)) : 0;
+  return x == g.n || y == g.n || z == g.n;
+}
+
+__device__ __forceinline__ int bitrev(int v, int logN) {
+  return logN == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - logN));
+}
+
+// radix-2 DIF stages over C columns of length N (row stride N+1); sgn = +1 inverse, -1 forward
+template <typename T, typename T2>
+__device__ __forceinline__ void dif_fft(T2* buf, int C, int N, int logN, const T2* __restrict__ tw,
+                                        T sgn) {
+  const int half = N >> 1;
+  for (int s = 0; s < logN; ++s) {
+    const int h = half >> s;  // span
+    const int tstep = 1 << s; // twiddle index stride: N / (2h)
+    for (int idx = threadIdx.x; idx < C * half; idx += blockDim.x) {
+      const int c = idx / half;
+      const int b = idx - c * half;
+      const int j = b & (h - 1);
+      const int i = ((b >> (logN - 1 - s)) << (logN - s)) + j;  // (b / h) * 2h + j
+      T2* col = buf + (size_t)c * (N + 1);
+      const T2 a = col[i];
+      const T2 bb = col[i + h];
+      const T2 w = tw[j * tstep];
+      const T dr = a.x - bb.x, di = a.y - bb.y;
+      const T wr = w.x, wi = sgn * w.y;
+      col[i].x = a.x + bb.x;
+      col[i].y = a.y + bb.y;
+      col[i + h].x = dr * wr - di * wi;
+      col[i + h].y = dr * wi + di * wr;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_dst_forward(T* x, long long S, ColGeom cg, int N, int logN, int C,
+                              const typename Vec2<T>::type* __restrict__ tw,
+                              const typename Vec2<T>::type* __restrict__ pre, const int* done) {
+  using T2 = typename Vec2<T>::type;
+  if (stop_requested(done)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* buf = (T2*)smem_raw;
+  const long long c0 = (long long)blockIdx.x * 2 * C;
+  // load: slot m = N-1-t holds (w_a, w_b); the m = 0 entry is doubled
+  for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+    const int c = idx % C;
+    const int t = idx / C;
+    T2 v = *(const T2*)(x + (long long)t * S + c0 + 2 * c);
+    const int m = N - 1 - t;
+    if (m == 0) {
+      v.x *= (T)2;
+      v.y *= (T)2;
+    }
+    buf[(size_t)c * (N + 1) + m] = v;
+  }
+  __syncthreads();
+  // pre-twiddle in pairs (m, N-m):  V[m] = e^{i pi m/(2N)} (w_m - i w_{N-m});  Z = V_a + i V_b
+  const int halfp = (N >> 1) + 1;
+  for (int idx = threadIdx.x; idx < C * halfp; idx += blockDim.x) {
+    const int c = idx / halfp;
+    const int m = idx - c * halfp;
+    if (m == 0 || N == 1) continue;
+    const int q = N - m;
+    T2* col = buf + (size_t)c * (N + 1);
+    const T2 A = col[m], Bq = col[q];
+    const T2 em = pre[m], eq = pre[q];
+    // column a: w_a = A.x (at m), Bq.x (at q); column b: A.y, Bq.y
+    const T vam_r = A.x * em.x + Bq.x * em.y, vam_i = A.x * em.y - Bq.x * em.x;
+    const T vbm_r = A.y * em.x + Bq.y * em.y, vbm_i = A.y * em.y - Bq.y * em.x;
+    T2 zm;
+    zm.x = vam_r - vbm_i;
+    zm.y = vam_i + vbm_r;
+    if (q != m) {
+      const T vaq_r = Bq.x * eq.x + A.x * eq.y, vaq_i = Bq.x * eq.y - A.x * eq.x;
+      const T vbq_r = Bq.y * eq.x + A.y * eq.y, vbq_i = Bq.y * eq.y - A.y * eq.x;
+      T2 zq;
+      zq.x = vaq_r - vbq_i;
+      zq.y = vaq_i + vbq_r;
+      col[q] = zq;
+    }
+    col[m] = zm;
+  }
+  __syncthreads();
+  dif_fft<T, T2>(buf, C, N, logN, tw, (T)1);
+  // output: rhat_{j+1} = (-1)^j C3_j / 2, C3_{2i} = v_i, C3_{2i+1} = v_{N-1-i}; v_i at slot bitrev(i)
+  for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+    const int c = idx % C;
+    const int j = idx / C;
+    const int vi = (j & 1) ? (N - 1 - (j >> 1)) : (j >> 1);
+    T2 v = buf[(size_t)c * (N + 1) + bitrev(vi, logN)];
+    const T sc = (j & 1) ? (T)-0.5 : (T)0.5;
+    v.x = ghost_col(cg, c0 + 2 * c) ? (T)0 : v.x * sc;
+    v.y = ghost_col(cg, c0 + 2 * c + 1) ? (T)0 : v.y * sc;
+    *(T2*)(x + (long long)j * S + c0 + 2 * c) = v;
+  }
+}
+
+template <typename T>
+__global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, double omega, long long S,
+                              ColGeom cg, int N, int logN, int C, const typename Vec2<T>::type* __restrict__ tw,
+                              const typename Vec2<T>::type* __restrict__ pre, const int* done) {
+  using T2 = typename Vec2<T>::type;
+  if (stop_requested(done)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* buf = (T2*)smem_raw;
+  const long long c0 = (long long)blockIdx.x * 2 * C;
+  // load: z_j = (-1)^j y_{j+1};  v_{j/2} = z_j (j even), v_{N-1-(j-1)/2} = z_j (j odd)
+  for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+    const int c = idx % C;
+    const int j = idx / C;
+    T2 v = *(const T2*)(y + (long long)j * S + c0 + 2 * c);
+    int s;
+    if (j & 1) {
+      s = N - 1 - (j >> 1);
+      v.x = -v.x;
+      v.y = -v.y;
+    } else {
+      s = j >> 1;
+    }
+    buf[(size_t)c * (N + 1) + s] = v;
+  }
+  __syncthreads();
+  dif_fft<T, T2>(buf, C, N, logN, tw, (T)-1);
+  // post: V_a[m] = (C_m + conj C_{N-m})/2, V_b[m] = (C_m - conj C_{N-m})/(2i);
+  //       X[m] = Re(e^{-i pi m/(2N)} V[m]);  u_{N-m} = X[m]  (time slot N-1-m)
+  const int halfp = (N >> 1) + 1;
+  for (int idx = threadIdx.x; idx < C * halfp; idx += blockDim.x) {
+    const int c = idx % C;
+    const int m = idx / C;
+    if (N == 1 && m > 0) continue;
+    const bool ga = ghost_col(cg, c0 + 2 * c), gb = ghost_col(cg, c0 + 2 * c + 1);
+    const int q = (N - m) & (N - 1);
+    const T2* col = buf + (size_t)c * (N + 1);
+    const T2 Cm = col[bitrev(m, logN)];
+    const T2 Cq = col[bitrev(q, logN)];
+    // V_a[m] = ((Cm.x + Cq.x)/2, (Cm.y - Cq.y)/2); V_b[m] = ((Cm.y + Cq.y)/2, (Cq.x - Cm.x)/2)
+    const T2 em = pre[m];
+    const T var = (T)0.5 * (Cm.x + Cq.x), vai = (T)0.5 * (Cm.y - Cq.y);
+    const T vbr = (T)0.5 * (Cm.y + Cq.y), vbi = (T)0.5 * (Cq.x - Cm.x);
+    const T Xa = ga ? (T)0 : var * em.x + vai * em.y;
+    const T Xb = gb ? (T)0 : vbr * em.x + vbi * em.y;
+    const long long o1 = (long long)(N - 1 - m) * S + c0 + 2 * c;
+    if (mode == 1) {
+      double2* u = (double2*)((double*)out + o1);
+      double2 cur = *u;
+      cur.x += omega * (double)Xa;
+      cur.y += omega * (double)Xb;
+      *u = cur;
+    } else {
+      T2 v;
+      v.x = Xa;
+      v.y = Xb;
+      *(T2*)((T*)out + o1) = v;
+    }
+    if (m != 0 && q != m) {
+      // X[q] with the roles of m and q exchanged -> time slot N-1-q = m-1
+      const T2 eq = pre[q];
+      const T var2 = (T)0.5 * (Cq.x + Cm.x), vai2 = (T)0.5 * (Cq.y - Cm.y);
+      const T vbr2 = (T)0.5 * (Cq.y + Cm.y), vbi2 = (T)0.5 * (Cm.x - Cq.x);
+      const T Xa2 = ga ? (T)0 : var2 * eq.x + vai2 * eq.y;
+      const T Xb2 = gb ? (T)0 : vbr2 * eq.x + vbi2 * eq.y;
+      const long long o2 = (long long)(m - 1) * S + c0 + 2 * c;
+      if (mode == 1) {
+        double2* u = (double2*)((double*)out + o2);
+        double2 cur = *u;
+        cur.x += omega * (double)Xa2;
+        cur.y += omega * (double)Xb2;
+        *u = cur;
+      } else {
+        T2 v;
+        v.x = Xa2;
+        v.y = Xb2;
+        *(T2*)((T*)out + o2) = v;
+      }
+    }
+  }
+}
+
+template <typename T>
+int dst_cols(int N, long long S) {
+  // complex columns per CTA: a power of two, <= 16, using at most ~100 KB of shared memory
+  const long long bytes = (long long)(N + 1) * 2 * sizeof(T);
+  long long C = (100 * 1024) / bytes;
+  if (C < 1) C = 1;
+  if (C > 16) C = 16;
+  long long pw = 1;
+  while (pw * 2 <= C) pw *= 2;
+  C = pw;
+  while (C > 1 && (S % (2 * C)) != 0) C >>= 1;
+  if (2 * C > S) C = S / 2 > 0 ? S / 2 : 1;
+  return (int)C;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> plan, const int* done,
+                        cudaStream_t st) {
+  using T2 = typename Vec2<T>::type;
+  const int C = dst_cols<T>(plan.N, S);
+  const size_t smem = (size_t)C * (plan.N + 1) * sizeof(T2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_dst_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const int blocks = (int)(S / (2 * C));
+  const ColGeom cg{dim, n, logP};
+  k_dst_forward<T><<<blocks, kThreads, smem, st>>>(x, S, cg, plan.N, plan.logN, C, (const T2*)plan.tw,
+                                                   (const T2*)plan.pre, done);
+  note_launch();
+}
+
+template <typename T>
+void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
+                        int logP, DstPlan<T> plan, const int* done, cudaStream_t st) {
+  using T2 = typename Vec2<T>::type;
+  const int C = dst_cols<T>(plan.N, S);
+  const size_t smem = (size_t)C * (plan.N + 1) * sizeof(T2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_dst_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const int blocks = (int)(S / (2 * C));
+  const ColGeom cg{dim, n, logP};
+  k_dst_inverse<T><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan.N, plan.logN, C,
+                                                   (const T2*)plan.tw, (const T2*)plan.pre, done);
+  note_launch();
+}
+
+template void launch_dst_forward<float>(float*, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);
+template void launch_dst_forward<double>(double*, long long, int, int, int, DstPlan<double>, const int*, cudaStream_t);
+template void launch_dst_inverse<float>(const float*, void*, int, double, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);
+template void launch_dst_inverse<double>(const double*, void*, int, double, long long, int, int, int, DstPlan<double>, const int*, cudaStream_t);
+
+}  // namespace pt

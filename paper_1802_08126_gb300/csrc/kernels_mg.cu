@@ -1,0 +1,500 @@
+// Batched geometric multigrid for the spatial solves of the Uzawa preconditioners
+// (A~_n^-1 of §3, eq. 3.2-3.3 and H~_k^-1 of §4, eq. 4.6-4.7).
+//
+// The paper only asks for "MG V-cycles with Jacobi smoothers" (§8.2).  Reading used here:
+// symmetric V(1,1) with zero initial guess, weighted Jacobi before and after the coarse-grid
+// correction, full-weighting restriction R = P^T / 2^d, d-linear prolongation P, level
+// operators rediscretised from the same coefficient at the level's face midpoints, exact
+// solve on the one-point grid.  Every launch covers all B slices of the batch (all time
+// steps, or all DST frequencies) at once.  Levels whose slices have at most kCoarseMaxElems
+// padded points are finished by one CTA per slice in shared memory.
+//
+// Also here: the exact batched tridiagonal solve used for 1-D problems.
+#include <cmath>
+
+#include "stencil_common.cuh"
+
+namespace pt {
+
+namespace {
+
+template <int DIM, typename T>
+__device__ __forceinline__ T diag_at(StencilGeom<T> g, T sig, T s, T cth, int x, int y, int z,
+                                     T* am, T* ap) {
+  face_coefs<DIM, T>(g.tab, g.P, x, y, z, cth, g.a0, am, ap);
+  return sig + s * g.h2inv * face_sum<DIM, T>(am, ap);
+}
+
+// x = w D^-1 b   (pre-smoothing from a zero iterate)
+template <int DIM, typename T>
+__global__ void k_jacobi0(const T* __restrict__ b, T* __restrict__ x, StencilGeom<T> g,
+                          OpBatch<T> op, long long total, const int* done) {
+  if (stop_requested(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int xx, y, z;
+    T v = (T)0;
+    if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
+      T am[3], ap[3];
+      const T D = diag_at<DIM, T>(g, op.sig[t], op.s, op.cth[t], xx, y, z, am, ap);
+      v = op.omega * b[i] / D;
+    }
+    x[i] = v;
+  }
+}
+
+// r = b - L x
+template <int DIM, typename T>
+__global__ void k_residual(const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r,
+                           StencilGeom<T> g, OpBatch<T> op, long long total, const int* done) {
+  if (stop_requested(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int xx, y, z;
+    T v = (T)0;
+    if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
+      T am[3], ap[3];
+      face_coefs<DIM, T>(g.tab, g.P, xx, y, z, op.cth[t], g.a0, am, ap);
+      const T xc = x[i];
+      v = b[i] - (op.sig[t] * xc + op.s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
+    }
+    r[i] = v;
+  }
+}
+
+// out (mode) x + w D^-1 r
+template <int DIM, typename T>
+__global__ void k_jacobi_update(const T* x, const T* __restrict__ r, void* out, int mode,
+                                int out_fp64, StencilGeom<T> g, OpBatch<T> op, long long total,
+                                const int* done) {
+  if (stop_requested(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int xx, y, z;
+    if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
+      T am[3], ap[3];
+      const T D = diag_at<DIM, T>(g, op.sig[t], op.s, op.cth[t], xx, y, z, am, ap);
+      store_out<T>(out, i, mode, out_fp64, x[i] + op.omega * r[i] / D);
+    } else if (mode == 0) {
+      store_out<T>(out, i, 0, out_fp64, (T)0);
+    }
+  }
+}
+
+// offset (within a slice) of the fine point 2I+1 that coincides with coarse point I
+template <int DIM>
+__device__ __forceinline__ long long fine_center(int x, int y, int z, int Pf) {
+  if (DIM == 1) return 2 * x + 1;
+  if (DIM == 2) return (long long)(2 * y + 1) * Pf + (2 * x + 1);
+  return ((long long)(2 * z + 1) * Pf + (2 * y + 1)) * Pf + (2 * x + 1);
+}
+
+// full weighting: bc[I] = sum_{o in {-1,0,1}^d} prod_d w(o_d) r[2I+1+o],  w(0)=1/2, w(+-1)=1/4
+template <int DIM, typename T>
+__global__ void k_restrict(const T* __restrict__ r, T* __restrict__ bc, int nf_logP, long long Sf,
+                           int nc, int nc_logP, long long total_c, const int* done) {
+  if (stop_requested(done)) return;
+  const int Pf = 1 << nf_logP;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total_c;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    T v = (T)0;
+    if (decode<DIM>(i, nc_logP, nc, t, x, y, z)) {
+      const long long fc = t * Sf + fine_center<DIM>(x, y, z, Pf);
+      if (DIM == 1) {
+        v = (T)0.25 * r[fc - 1] + (T)0.5 * r[fc] + (T)0.25 * r[fc + 1];
+      } else if (DIM == 2) {
+        T rows[3];
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy) {
+          const long long c = fc + (long long)oy * Pf;
+          rows[oy + 1] = (T)0.25 * r[c - 1] + (T)0.5 * r[c] + (T)0.25 * r[c + 1];
+        }
+        v = (T)0.25 * rows[0] + (T)0.5 * rows[1] + (T)0.25 * rows[2];
+      } else {
+        const long long Pf2 = (long long)Pf * Pf;
+        T planes[3];
+#pragma unroll
+        for (int oz = -1; oz <= 1; ++oz) {
+          T rows[3];
+#pragma unroll
+          for (int oy = -1; oy <= 1; ++oy) {
+            const long long c = fc + (long long)oz * Pf2 + (long long)oy * Pf;
+            rows[oy + 1] = (T)0.25 * r[c - 1] + (T)0.5 * r[c] + (T)0.25 * r[c + 1];
+          }
+          planes[oz + 1] = (T)0.25 * rows[0] + (T)0.5 * rows[1] + (T)0.25 * rows[2];
+        }
+        v = (T)0.25 * planes[0] + (T)0.5 * planes[1] + (T)0.25 * planes[2];
+      }
+    }
+    bc[i] = v;
+  }
+}
+
+// d-linear interpolation weights along one axis for fine index f: coarse c0,c1 with w0,w1
+__device__ __forceinline__ void interp_axis(int f, int& c0, int& c1, bool& two) {
+  if (f & 1) {
+    c0 = f >> 1;
+    c1 = c0;
+    two = false;
+  } else {
+    c0 = (f >> 1) - 1;
+    c1 = f >> 1;
+    two = true;
+  }
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ T prolong_at(const T* __restrict__ ec, long long slot_off, int Pc, int x,
+                                        int y, int z) {
+  int x0, x1, y0 = 0, y1 = 0, z0 = 0, z1 = 0;
+  bool tx, ty = false, tz = false;
+  interp_axis(x, x0, x1, tx);
+  if (DIM >= 2) interp_axis(y, y0, y1, ty);
+  if (DIM >= 3) interp_axis(z, z0, z1, tz);
+  auto row = [&](int zz, int yy) -> T {
+    const long long base = slot_off + ((long long)zz * Pc + yy) * Pc;
+    return tx ? (T)0.5 * (ec[base + x0] + ec[base + x1]) : ec[base + x0];
+  };
+  auto plane = [&](int zz) -> T {
+    if (DIM == 1) return row(0, 0);
+    return ty ? (T)0.5 * (row(zz, y0) + row(zz, y1)) : row(zz, y0);
+  };
+  if (DIM <= 2) return plane(0);
+  return tz ? (T)0.5 * (plane(z0) + plane(z1)) : plane(z0);
+}
+
+// x += P ec
+template <int DIM, typename T>
+__global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ ec, StencilGeom<T> g,
+                              int Pc_logP, long long Sc, long long total, const int* done) {
+  if (stop_requested(done)) return;
+  const int Pc = 1 << Pc_logP;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int xx, y, z;
+    if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) x[i] += prolong_at<DIM, T>(ec, t * Sc, Pc, xx, y, z);
+  }
+}
+
+// ---- one-CTA-per-slice coarse V-cycle ------------------------------------------------------
+struct CoarseLevel {
+  int n, logP;
+  int S;       // slice elements
+  int guard;   // zero elements in front
+  int off;     // offset (elements) of this level's b array in shared memory; x, r follow
+  long long tab;
+  float h2inv;
+  double h2inv_d;
+};
+
+struct CoarsePlan {
+  int nl;                       // number of levels handled (lc..L)
+  CoarseLevel lv[kMaxLevels];
+};
+
+template <int DIM, typename T>
+__global__ void k_coarse_vcycle(const T* __restrict__ bglob, long long Sg, void* out, int mode,
+                                int out_fp64, const T* __restrict__ tab_all, T a0, OpBatch<T> op,
+                                CoarsePlan cp, const int* done) {
+  if (stop_requested(done)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = (T*)smem_raw;
+  const int slice = blockIdx.x;
+  const T sig = op.sig[slice], cth = op.cth[slice], s = op.s, w = op.omega;
+  // zero everything (ghosts and guards must read as zero)
+  const int total_sm = cp.lv[cp.nl - 1].off + 3 * (cp.lv[cp.nl - 1].guard + cp.lv[cp.nl - 1].S);
+  for (int i = threadIdx.x; i < total_sm; i += blockDim.x) sm[i] = (T)0;
+  __syncthreads();
+  auto B = [&](int l) { return sm + cp.lv[l].off + cp.lv[l].guard; };
+  auto X = [&](int l) { return sm + cp.lv[l].off + (cp.lv[l].guard + cp.lv[l].S) + cp.lv[l].guard; };
+  auto R = [&](int l) { return sm + cp.lv[l].off + 2 * (cp.lv[l].guard + cp.lv[l].S) + cp.lv[l].guard; };
+  // load this slice's rhs
+  {
+    const CoarseLevel& L0 = cp.lv[0];
+    T* b = B(0);
+    for (int i = threadIdx.x; i < L0.S; i += blockDim.x) b[i] = bglob[(long long)slice * Sg + i];
+  }
+  __syncthreads();
+  auto geom = [&](int l) {
+    StencilGeom<T> g;
+    g.dim = DIM;
+    g.n = cp.lv[l].n;
+    g.logP = cp.lv[l].logP;
+    g.P = 1 << g.logP;
+    g.S = cp.lv[l].S;
+    g.tab = tab_all + cp.lv[l].tab;
+    g.a0 = a0;
+    g.h2inv = sizeof(T) == 8 ? (T)cp.lv[l].h2inv_d : (T)cp.lv[l].h2inv;
+    return g;
+  };
+  // downward sweep
+  for (int l = 0; l + 1 < cp.nl; ++l) {
+    const StencilGeom<T> g = geom(l);
+    T* b = B(l);
+    T* x = X(l);
+    T* r = R(l);
+    for (int i = threadIdx.x; i < g.S; i += blockDim.x) {
+      long long t;
+      int xx, y, z;
+      if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
+        T am[3], ap[3];
+        const T D = diag_at<DIM, T>(g, sig, s, cth, xx, y, z, am, ap);
+        x[i] = w * b[i] / D;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.S; i += blockDim.x) {
+      long long t;
+      int xx, y, z;
+      if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
+        T am[3], ap[3];
+        face_coefs<DIM, T>(g.tab, g.P, xx, y, z, cth, g.a0, am, ap);
+        const T xc = x[i];
+        r[i] = b[i] - (sig * xc + s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
+      }
+    }
+    __syncthreads();
+    const CoarseLevel& C = cp.lv[l + 1];
+    T* bc = B(l + 1);
+    const int Pf = g.P;
+    for (int i = threadIdx.x; i < C.S; i += blockDim.x) {
+      long long t;
+      int x0, y0, z0;
+      if (decode<DIM>(i, C.logP, C.n, t, x0, y0, z0)) {
+        const long long fc = fine_center<DIM>(x0, y0, z0, Pf);
+        T v;
+        if (DIM == 1) {
+          v = (T)0.25 * r[fc - 1] + (T)0.5 * r[fc] + (T)0.25 * r[fc + 1];
+        } else if (DIM == 2) {
+          T rows[3];
+          for (int oy = -1; oy <= 1; ++oy) {
+            const long long c = fc + (long long)oy * Pf;
+            rows[oy + 1] = (T)0.25 * r[c - 1] + (T)0.5 * r[c] + (T)0.25 * r[c + 1];
+          }
+          v = (T)0.25 * rows[0] + (T)0.5 * rows[1] + (T)0.25 * rows[2];
+        } else {
+          T planes[3];
+          for (int oz = -1; oz <= 1; ++oz) {
+            T rows[3];
+            for (int oy = -1; oy <= 1; ++oy) {
+              const long long c = fc + (long long)oz * Pf * Pf + (long long)oy * Pf;
+              rows[oy + 1] = (T)0.25 * r[c - 1] + (T)0.5 * r[c] + (T)0.25 * r[c + 1];
+            }
+            planes[oz + 1] = (T)0.25 * rows[0] + (T)0.5 * rows[1] + (T)0.25 * rows[2];
+          }
+          v = (T)0.25 * planes[0] + (T)0.5 * planes[1] + (T)0.25 * planes[2];
+        }
+        bc[i] = v;
+      }
+    }
+    __syncthreads();
+  }
+  // coarsest level: one point, exact
+  {
+    const int l = cp.nl - 1;
+    const StencilGeom<T> g = geom(l);
+    if (threadIdx.x == 0) {
+      T am[3], ap[3];
+      const T D = diag_at<DIM, T>(g, sig, s, cth, 0, 0, 0, am, ap);
+      X(l)[0] = B(l)[0] / D;
+    }
+    __syncthreads();
+  }
+  // upward sweep
+  for (int l = cp.nl - 2; l >= 0; --l) {
+    const StencilGeom<T> g = geom(l);
+    T* b = B(l);
+    T* x = X(l);
+    T* r = R(l);
+    const T* ec = X(l + 1);
+    const int Pc = 1 << cp.lv[l + 1].logP;
+    for (int i = threadIdx.x; i < g.S; i += blockDim.x) {
+      long long t;
+      int xx, y, z;
+      if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) x[i] += prolong_at<DIM, T>(ec, 0, Pc, xx, y, z);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.S; i += blockDim.x) {
+      long long t;
+      int xx, y, z;
+      if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
+        T am[3], ap[3];
+        face_coefs<DIM, T>(g.tab, g.P, xx, y, z, cth, g.a0, am, ap);
+        const T xc = x[i];
+        r[i] = b[i] - (sig * xc + s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.S; i += blockDim.x) {
+      long long t;
+      int xx, y, z;
+      if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
+        T am[3], ap[3];
+        const T D = diag_at<DIM, T>(g, sig, s, cth, xx, y, z, am, ap);
+        x[i] = x[i] + w * r[i] / D;
+      }
+    }
+    __syncthreads();
+  }
+  // write the level-lc result of this slice
+  {
+    const CoarseLevel& L0 = cp.lv[0];
+    const T* x = X(0);
+    for (int i = threadIdx.x; i < L0.S; i += blockDim.x) {
+      long long t;
+      int xx, y, z;
+      const bool inner = decode<DIM>(i, L0.logP, L0.n, t, xx, y, z);
+      const long long gi = (long long)slice * Sg + i;
+      if (inner)
+        store_out<T>(out, gi, mode, out_fp64, x[i]);
+      else if (mode == 0)
+        store_out<T>(out, gi, 0, out_fp64, (T)0);
+    }
+  }
+}
+
+// ---- exact tridiagonal solve (1-D), one thread per slice -----------------------------------
+template <typename T>
+__global__ void k_tridiag(const T* __restrict__ r, void* out, int mode, int out_fp64,
+                          StencilGeom<T> g, OpBatch<T> op, int B, T* __restrict__ work,
+                          const int* done) {
+  if (stop_requested(done)) return;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int n = g.n;
+  const long long base = (long long)b * g.S;
+  T* cp = work + (long long)b * 2 * g.P;
+  T* dp = cp + g.P;
+  const T sig = op.sig[b], cth = op.cth[b], sh = op.s * g.h2inv;
+  T prev_c = (T)0, prev_d = (T)0;
+  for (int i = 0; i < n; ++i) {
+    T am[1], ap[1];
+    face_coefs<1, T>(g.tab, g.P, i, 0, 0, cth, g.a0, am, ap);
+    const T lo = i > 0 ? -sh * am[0] : (T)0;
+    const T up = i < n - 1 ? -sh * ap[0] : (T)0;
+    const T di = sig + sh * (am[0] + ap[0]);
+    const T denom = di - lo * prev_c;
+    prev_c = up / denom;
+    prev_d = (r[base + i] - lo * prev_d) / denom;
+    cp[i] = prev_c;
+    dp[i] = prev_d;
+  }
+  T xn = (T)0;
+  for (int i = n - 1; i >= 0; --i) {
+    xn = dp[i] - cp[i] * xn;
+    store_out<T>(out, base + i, mode, out_fp64, xn);
+  }
+  if (mode == 0) store_out<T>(out, base + n, 0, out_fp64, (T)0);  // ghost
+}
+
+template <int DIM, typename T>
+void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode,
+                int out_fp64, const int* done, cudaStream_t st) {
+  const int B = plan.B;
+  auto geom = [&](int l) {
+    StencilGeom<T> g;
+    g.dim = DIM;
+    g.n = plan.lev[l].n;
+    g.P = plan.lev[l].P;
+    g.logP = plan.lev[l].logP;
+    g.S = plan.lev[l].S;
+    g.tab = plan.tab + plan.lev[l].tab;
+    g.a0 = plan.a0;
+    g.h2inv = (T)(1.0 / (plan.lev[l].h * plan.lev[l].h));
+    return g;
+  };
+  const T* bl = b0;
+  for (int l = 0; l < plan.lc; ++l) {
+    const StencilGeom<T> g = geom(l);
+    const long long total = g.S * B;
+    T* x = (T*)plan.buf[l].x;
+    T* r = (T*)plan.buf[l].r;
+    k_jacobi0<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, g, op, total, done);
+    k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, r, g, op, total, done);
+    const Level& C = plan.lev[l + 1];
+    const long long total_c = C.S * B;
+    k_restrict<DIM, T><<<grid_for(total_c), kThreads, 0, st>>>(r, (T*)plan.buf[l + 1].b, g.logP, g.S,
+                                                               C.n, C.logP, total_c, done);
+    note_launch(3);
+    bl = (const T*)plan.buf[l + 1].b;
+  }
+  // coarse part: levels lc..nlev-1 in one CTA per slice
+  {
+    CoarsePlan cp;
+    cp.nl = plan.nlev - plan.lc;
+    int off = 0;
+    for (int k = 0; k < cp.nl; ++k) {
+      const Level& L = plan.lev[plan.lc + k];
+      CoarseLevel& c = cp.lv[k];
+      c.n = L.n;
+      c.logP = L.logP;
+      c.S = (int)L.S;
+      c.guard = 0;
+      for (int d = 0, pk = 1; d < DIM; ++d, pk *= L.P) c.guard += pk;  // (-1,-1,-1) corner
+      c.guard = (c.guard + 3) & ~3;
+      c.off = off;
+      c.tab = L.tab;
+      c.h2inv_d = 1.0 / (L.h * L.h);
+      c.h2inv = (float)c.h2inv_d;
+      off += 3 * (c.guard + c.S);
+    }
+    const size_t smem = (size_t)off * sizeof(T);
+    void* dst = plan.lc == 0 ? out : plan.buf[plan.lc].x;
+    const int dmode = plan.lc == 0 ? mode : 0;
+    const int dfp64 = plan.lc == 0 ? out_fp64 : 0;
+    const int threads = plan.lev[plan.lc].S >= 256 ? 256 : 128;
+    k_coarse_vcycle<DIM, T><<<B, threads, smem, st>>>(bl, plan.lev[plan.lc].S, dst, dmode, dfp64,
+                                                      plan.tab, plan.a0, op, cp, done);
+    note_launch();
+  }
+  // upward sweep over the global levels
+  for (int l = plan.lc - 1; l >= 0; --l) {
+    const StencilGeom<T> g = geom(l);
+    const long long total = g.S * B;
+    const T* b = l == 0 ? b0 : (const T*)plan.buf[l].b;
+    T* x = (T*)plan.buf[l].x;
+    T* r = (T*)plan.buf[l].r;
+    const Level& C = plan.lev[l + 1];
+    k_prolong_add<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, (const T*)plan.buf[l + 1].x, g,
+                                                                C.logP, C.S, total, done);
+    k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, g, op, total, done);
+    if (l == 0)
+      k_jacobi_update<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, r, out, mode, out_fp64, g, op,
+                                                                    total, done);
+    else
+      k_jacobi_update<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, r, x, 0, 0, g, op, total, done);
+    note_launch(3);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void vcycle(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode, int out_fp64,
+            const int* done, cudaStream_t st) {
+  switch (plan.dim) {
+    case 1: vcycle_dim<1, T>(plan, op, b0, out, mode, out_fp64, done, st); break;
+    case 2: vcycle_dim<2, T>(plan, op, b0, out, mode, out_fp64, done, st); break;
+    default: vcycle_dim<3, T>(plan, op, b0, out, mode, out_fp64, done, st); break;
+  }
+}
+
+template <typename T>
+void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T> g, OpBatch<T> op,
+                    int B, T* work, const int* done, cudaStream_t st) {
+  k_tridiag<T><<<(B + 63) / 64, 64, 0, st>>>(r, out, mode, out_fp64, g, op, B, work, done);
+  note_launch();
+}
+
+template void vcycle<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, const int*, cudaStream_t);
+template void vcycle<double>(const MGPlan<double>&, OpBatch<double>, const double*, void*, int, int, const int*, cudaStream_t);
+template void launch_tridiag<float>(const float*, void*, int, int, StencilGeom<float>, OpBatch<float>, int, float*, const int*, cudaStream_t);
+template void launch_tridiag<double>(const double*, void*, int, int, StencilGeom<double>, OpBatch<double>, int, double*, const int*, cudaStream_t);
+
+}  // namespace pt

@@ -1,0 +1,327 @@
+// Space-time stencil kernels: layout conversion, the two Uzawa residuals (§3, eq. 3.1), the
+// time-global operator B (§2, eq. 2.3-2.4), the Abar apply of the block solve (§4, eq. 4.4)
+// and the deterministic FP64 reductions.
+#include <cmath>
+
+#include "stencil_common.cuh"
+
+namespace pt {
+
+namespace {
+
+template <int DIM>
+__global__ void k_pack(const double* __restrict__ src, const double* __restrict__ u0,
+                       double* __restrict__ dst, double scale, int n, int logP, long long total) {
+  const long long ns = DIM == 1 ? n : (DIM == 2 ? (long long)n * n : (long long)n * n * n);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    double v = 0.0;
+    if (decode<DIM>(i, logP, n, t, x, y, z)) {
+      const long long q = ((long long)z * n + y) * n + x;
+      v = scale * src[t * ns + q];
+      if (u0 != nullptr && t == 0) v += u0[q];
+    }
+    dst[i] = v;
+  }
+}
+
+template <int DIM, typename T>
+__global__ void k_pack_typed(const double* __restrict__ src, T* __restrict__ dst, int n, int logP,
+                             long long total) {
+  const long long ns = DIM == 1 ? n : (DIM == 2 ? (long long)n * n : (long long)n * n * n);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    T v = (T)0;
+    if (decode<DIM>(i, logP, n, t, x, y, z)) v = (T)src[t * ns + ((long long)z * n + y) * n + x];
+    dst[i] = v;
+  }
+}
+
+template <int DIM, typename T>
+__global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, int n, int logP,
+                         long long S, long long total_packed) {
+  const long long ns = DIM == 1 ? n : (DIM == 2 ? (long long)n * n : (long long)n * n * n);
+  const int P = 1 << logP;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total_packed;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long t = q / ns;
+    long long r = q - t * ns;
+    const int x = (int)(r % n);
+    r /= n;
+    const int y = DIM >= 2 ? (int)(r % n) : 0;
+    const int z = DIM >= 3 ? (int)(r / n) : 0;
+    dst[q] = (double)src[t * S + ((long long)z * P + y) * P + x];
+  }
+}
+
+template <int DIM>
+__global__ void k_apply_B(const double* __restrict__ u, double* __restrict__ out,
+                          StencilGeom<double> g, const double* __restrict__ cth, double tau,
+                          long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    double v = 0.0;
+    if (decode<DIM>(i, g.logP, g.n, t, x, y, z)) {
+      double am[3], ap[3];
+      face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
+      const double uc = u[i];
+      const double um = t > 0 ? u[i - g.S] : 0.0;
+      const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
+      v = (uc - um) + tau * Au;
+    }
+    out[i] = v;
+  }
+}
+
+// r_p = K u - tau A_t p - F  (first line of eq. 3.1)
+template <int DIM, typename Tp>
+__global__ void k_resid_p(const double* __restrict__ u, const double* __restrict__ p,
+                          const double* __restrict__ F, Tp* __restrict__ rp, StencilGeom<double> g,
+                          const double* __restrict__ cth, double tau, long long total,
+                          const int* done) {
+  if (stop_requested(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    double v = 0.0;
+    if (decode<DIM>(i, g.logP, g.n, t, x, y, z)) {
+      double am[3], ap[3];
+      face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
+      const double pc = p[i];
+      const double Ap = stencil_sum<DIM, double>(p, i, pc, am, ap, g.P) * g.h2inv;
+      const double um = t > 0 ? u[i - g.S] : 0.0;
+      v = (u[i] - um) - tau * Ap - F[i];
+    }
+    rp[i] = (Tp)v;
+  }
+}
+
+// r_u = F - K^T p - (K + K^T + A) u = (F - B u) - K^T (p + u)  (second line of eq. 3.1),
+// plus per-block partial sums of ||F - B u||^2.
+template <int DIM, typename Tp>
+__global__ void k_resid_u(const double* __restrict__ u, const double* __restrict__ p,
+                          const double* __restrict__ F, Tp* __restrict__ ru,
+                          double* __restrict__ partials, StencilGeom<double> g,
+                          const double* __restrict__ cth, double tau, int N, long long total,
+                          const int* done) {
+  if (stop_requested(done)) return;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    double v = 0.0;
+    if (decode<DIM>(i, g.logP, g.n, t, x, y, z)) {
+      double am[3], ap[3];
+      face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
+      const double uc = u[i];
+      const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
+      const double um = t > 0 ? u[i - g.S] : 0.0;
+      const double bres = F[i] - (uc - um) - tau * Au;
+      const double next = t + 1 < N ? p[i + g.S] + u[i + g.S] : 0.0;
+      v = bres - (p[i] + uc) + next;
+      acc += bres * bres;
+    }
+    ru[i] = (Tp)v;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+template <int DIM, typename T>
+__global__ void k_apply_A_scaled(const T* __restrict__ z, T* __restrict__ out, StencilGeom<T> g,
+                                 T cth, T scale, long long total, const int* done) {
+  if (stop_requested(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, zz;
+    T v = (T)0;
+    if (decode<DIM>(i, g.logP, g.n, t, x, y, zz)) {
+      T am[3], ap[3];
+      face_coefs<DIM, T>(g.tab, g.P, x, y, zz, cth, g.a0, am, ap);
+      const T zc = z[i];
+      v = scale * g.h2inv * stencil_sum<DIM, T>(z, i, zc, am, ap, g.P);
+    }
+    out[i] = v;
+  }
+}
+
+__global__ void k_norm2_partials(const double* __restrict__ v, long long count,
+                                 double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    acc += v[i] * v[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// One block of kReduceBlocks threads sums the partials in a fixed order.
+__global__ void k_finalize_residual(const double* __restrict__ partials, SolveState* state,
+                                    double* __restrict__ hist, int j, double tol, int max_it) {
+  if (state->done) return;
+  double v = partials[threadIdx.x];
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    const double res = sqrt(v / state->fnorm2);
+    hist[j] = res;
+    state->last_res = res;
+    if (!(res <= 1e30)) {  // NaN or overflow
+      state->status = PT_EDIVERGED;
+      state->done = 1;
+      state->iters = j;
+    } else if (res <= tol) {
+      state->status = PT_OK;
+      state->done = 1;
+      state->iters = j;
+    } else if (j >= max_it) {
+      state->status = PT_ENOTCONV;
+      state->done = 1;
+      state->iters = j;
+    }
+  }
+}
+
+__global__ void k_finalize_fnorm(const double* __restrict__ partials, SolveState* state) {
+  double v = partials[threadIdx.x];
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    state->fnorm2 = v > 0.0 ? v : 1.0;
+    state->done = 0;
+    state->status = PT_ENOTCONV;
+    state->iters = 0;
+    state->last_res = 1.0;
+  }
+}
+
+template <typename Tp>
+__global__ void k_axpy(double* __restrict__ y, const Tp* __restrict__ x, double a, long long count,
+                       const int* done) {
+  if (stop_requested(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * (double)x[i];
+}
+
+}  // namespace
+
+#define PT_DISPATCH_DIM(dim, ...)                 \
+  switch (dim) {                                  \
+    case 1: {                                     \
+      constexpr int D = 1;                        \
+      __VA_ARGS__;                                \
+    } break;                                      \
+    case 2: {                                     \
+      constexpr int D = 2;                        \
+      __VA_ARGS__;                                \
+    } break;                                      \
+    default: {                                    \
+      constexpr int D = 3;                        \
+      __VA_ARGS__;                                \
+    } break;                                      \
+  }
+
+void launch_pack(const double* src, const double* u0, double* dst, double scale, int dim, int n,
+                 int P, int logP, long long S, int N, cudaStream_t st) {
+  (void)P;
+  const long long total = S * N;
+  PT_DISPATCH_DIM(dim, k_pack<D><<<grid_for(total), kThreads, 0, st>>>(src, u0, dst, scale, n, logP, total));
+  note_launch();
+}
+
+template <typename T>
+void launch_pack_typed(const double* src, T* dst, int dim, int n, int P, int logP, long long S,
+                       int N, cudaStream_t st) {
+  (void)P;
+  const long long total = S * N;
+  PT_DISPATCH_DIM(dim, k_pack_typed<D, T><<<grid_for(total), kThreads, 0, st>>>(src, dst, n, logP, total));
+  note_launch();
+}
+
+template <typename T>
+void launch_unpack(const T* src, double* dst, int dim, int n, int P, int logP, long long S, int N,
+                   cudaStream_t st) {
+  (void)P;
+  long long ns = n;
+  for (int d = 1; d < dim; ++d) ns *= n;
+  const long long total = ns * N;
+  PT_DISPATCH_DIM(dim, k_unpack<D, T><<<grid_for(total), kThreads, 0, st>>>(src, dst, n, logP, S, total));
+  note_launch();
+}
+
+void launch_apply_B(const double* u, double* out, StencilGeom<double> g, const double* cth, double tau,
+                    int N, cudaStream_t st) {
+  const long long total = g.S * N;
+  PT_DISPATCH_DIM(g.dim, k_apply_B<D><<<grid_for(total), kThreads, 0, st>>>(u, out, g, cth, tau, total));
+  note_launch();
+}
+
+template <typename Tp>
+void launch_resid_p(const double* u, const double* p, const double* F, Tp* rp, StencilGeom<double> g,
+                    const double* cth, double tau, int N, const int* done, cudaStream_t st) {
+  const long long total = g.S * N;
+  PT_DISPATCH_DIM(g.dim, k_resid_p<D, Tp><<<grid_for(total), kThreads, 0, st>>>(u, p, F, rp, g, cth, tau, total, done));
+  note_launch();
+}
+
+template <typename Tp>
+void launch_resid_u(const double* u, const double* p, const double* F, Tp* ru, double* partials,
+                    StencilGeom<double> g, const double* cth, double tau, int N, const int* done,
+                    cudaStream_t st) {
+  const long long total = g.S * N;
+  PT_DISPATCH_DIM(g.dim, k_resid_u<D, Tp><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, ru, partials, g, cth, tau, N, total, done));
+  note_launch();
+}
+
+template <typename T>
+void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale, int N,
+                           const int* done, cudaStream_t st) {
+  const long long total = g.S * N;
+  PT_DISPATCH_DIM(g.dim, k_apply_A_scaled<D, T><<<grid_for(total), kThreads, 0, st>>>(z, out, g, cth, scale, total, done));
+  note_launch();
+}
+
+void launch_norm2_partials(const double* v, long long count, double* partials, cudaStream_t st) {
+  k_norm2_partials<<<kReduceBlocks, kThreads, 0, st>>>(v, count, partials);
+  note_launch();
+}
+
+void launch_finalize_residual(const double* partials, SolveState* state, double* hist, int j,
+                              double tol, int max_it, cudaStream_t st) {
+  k_finalize_residual<<<1, kReduceBlocks, 0, st>>>(partials, state, hist, j, tol, max_it);
+  note_launch();
+}
+
+void launch_finalize_fnorm(const double* partials, SolveState* state, cudaStream_t st) {
+  k_finalize_fnorm<<<1, kReduceBlocks, 0, st>>>(partials, state);
+  note_launch();
+}
+
+template <typename Tp>
+void launch_axpy(double* y, const Tp* x, double a, long long count, const int* done, cudaStream_t st) {
+  k_axpy<Tp><<<grid_for(count), kThreads, 0, st>>>(y, x, a, count, done);
+  note_launch();
+}
+
+template void launch_pack_typed<float>(const double*, float*, int, int, int, int, long long, int, cudaStream_t);
+template void launch_pack_typed<double>(const double*, double*, int, int, int, int, long long, int, cudaStream_t);
+template void launch_unpack<float>(const float*, double*, int, int, int, int, long long, int, cudaStream_t);
+template void launch_unpack<double>(const double*, double*, int, int, int, int, long long, int, cudaStream_t);
+template void launch_resid_p<float>(const double*, const double*, const double*, float*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
+template void launch_resid_p<double>(const double*, const double*, const double*, double*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
+template void launch_resid_u<float>(const double*, const double*, const double*, float*, double*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
+template void launch_resid_u<double>(const double*, const double*, const double*, double*, double*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
+template void launch_apply_A_scaled<float>(const float*, float*, StencilGeom<float>, float, float, int, const int*, cudaStream_t);
+template void launch_apply_A_scaled<double>(const double*, double*, StencilGeom<double>, double, double, int, const int*, cudaStream_t);
+template void launch_axpy<float>(double*, const float*, double, long long, const int*, cudaStream_t);
+template void launch_axpy<double>(double*, const double*, double, long long, const int*, cudaStream_t);
+
+}  // namespace pt

@@ -1,0 +1,160 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+//
+// Device layout of every space-time vector ("padded layout"): for a grid with n interior
+// points per axis, pitch P = n + 1 (a power of two) and slice stride S = P^dim, the value at
+// time slot t and interior coordinates (x, y, z) lives at  base[t*S + (z*P + y)*P + x].
+// Positions with any coordinate equal to n are "ghosts" and always hold zero; so do the
+// `guard` elements in front of slot 0.  The ghost at x = n of one row is the left neighbour
+// of the next row, the ghost row y = n of one plane is the lower neighbour of the next
+// plane, and so on, so a stencil reads its Dirichlet zeros without branches.  Every kernel
+// writes zero (or nothing) at ghost positions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/pt.h"
+
+namespace pt {
+
+constexpr int kMaxLevels = 16;
+constexpr int kReduceBlocks = 1024;  // fixed grid of the residual reduction (deterministic)
+constexpr int kCoarseMaxElems = 1024; // levels with P^dim <= this run inside one CTA per slice
+
+// Counts every kernel launch of the library (reported by pt_kernel_launch_count).
+void note_launch(int count = 1);
+
+struct Level {
+  int n;             // interior points per axis
+  int P;             // pitch n + 1
+  int logP;          // log2(P)
+  long long S;       // slice stride P^dim
+  long long guard;   // zero elements in front of slot 0 (>= P^(dim-1) + ... + P + 1, rounded)
+  double h;          // 1 / (n + 1)
+  long long tab;     // offset of this level's coefficient tables (2*dim arrays of P entries)
+};
+
+// Coefficient of one batch of slices at one level:
+//   a(face) = a0 + cth[b] * g_face(axis d) * prod_{e != d} g_node(axis e)
+// cth[b] = c * g_t(pi m_t t_b) for the slice's time (or c * mean over steps for Abar).
+template <typename T>
+struct StencilGeom {
+  int dim, n, P, logP;
+  long long S;
+  const T* tab;   // level tables: node_x, face_x, node_y, face_y, node_z, face_z (P each)
+  T a0;
+  T h2inv;        // 1/h^2
+};
+
+// Batched operator L_b = sig[b] I + s * A(cth[b]) on one level, used by the V-cycle.
+template <typename T>
+struct OpBatch {
+  const T* sig;   // [B] identity shift (0 for tau_n A_n, mu_k for H_k)
+  const T* cth;   // [B] coefficient time factors (times c)
+  T s;            // scale of A (tau)
+  T omega;        // Jacobi weight
+};
+
+// ---- stencil / residual kernels (kernels_stencil.cu) --------------------------------------
+// F (padded) = scale * pack(src) (+ u0 on slot 0 when u0 != nullptr), src packed [N][ns].
+void launch_pack(const double* src, const double* u0, double* dst, double scale, int dim, int n,
+                 int P, int logP, long long S, int N, cudaStream_t st);
+template <typename T>
+void launch_unpack(const T* src, double* dst, int dim, int n, int P, int logP, long long S, int N,
+                   cudaStream_t st);
+template <typename T>
+void launch_pack_typed(const double* src, T* dst, int dim, int n, int P, int logP, long long S,
+                       int N, cudaStream_t st);
+
+// out = B u (FP64)
+void launch_apply_B(const double* u, double* out, StencilGeom<double> g, const double* cth, double tau,
+                    int N, cudaStream_t st);
+
+// r_p = K u - tau A_n p - F   (written in precision Tp)
+template <typename Tp>
+void launch_resid_p(const double* u, const double* p, const double* F, Tp* rp, StencilGeom<double> g,
+                    const double* cth, double tau, int N, const int* done, cudaStream_t st);
+
+// r_u = F - K^T p - (K + K^T + tau A_n) u, partial sums of ||F - B u||^2 per block
+template <typename Tp>
+void launch_resid_u(const double* u, const double* p, const double* F, Tp* ru, double* partials,
+                    StencilGeom<double> g, const double* cth, double tau, int N, const int* done,
+                    cudaStream_t st);
+
+// out = scale * A(cthbar) z on one batch (Abar apply of the Hhat block solve)
+template <typename T>
+void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale, int N,
+                           const int* done, cudaStream_t st);
+
+// partial sums of ||v||^2 (padded vector, ghosts are zero)
+void launch_norm2_partials(const double* v, long long count, double* partials, cudaStream_t st);
+
+// Device state of one solve.
+struct SolveState {
+  int done;      // 1 once converged / failed / exhausted
+  int status;    // pt_status of the solve
+  int iters;     // number of Uzawa updates performed
+  int pad;
+  double fnorm2; // ||F||^2
+  double last_res;
+};
+
+// sum partials in fixed order; j-th residual -> hist[j], sets flags.
+void launch_finalize_residual(const double* partials, SolveState* state, double* hist, int j,
+                              double tol, int max_it, cudaStream_t st);
+void launch_finalize_fnorm(const double* partials, SolveState* state, cudaStream_t st);
+
+// elementwise y += a * x over count padded entries (x in Tp)
+template <typename Tp>
+void launch_axpy(double* y, const Tp* x, double a, long long count, const int* done, cudaStream_t st);
+
+// ---- multigrid (kernels_mg.cu) ----------------------------------------------------------
+struct MGLevelBufs {
+  void* b;  // rhs
+  void* x;  // smoothed iterate / correction
+  void* r;  // residual
+};
+
+template <typename T>
+struct MGPlan {
+  int dim, nlev, lc;  // number of levels, first level solved by the one-CTA coarse kernel
+  Level lev[kMaxLevels];
+  const T* tab;       // all level tables
+  T a0;
+  MGLevelBufs buf[kMaxLevels];
+  int B;              // slices in the batch
+};
+
+// One V(1,1) cycle with zero initial guess on all B slices: x = V(b).
+// mode 0: out = x;  mode 1: out += x (accumulate, out in FP64 when accum_fp64 != 0).
+template <typename T>
+void vcycle(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode, int out_fp64,
+            const int* done, cudaStream_t st);
+
+// exact batched tridiagonal solve for 1-D: x_b = (sig_b I + s A(cth_b))^-1 r_b
+template <typename T>
+void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T> g, OpBatch<T> op,
+                    int B, T* work, const int* done, cudaStream_t st);
+
+// ---- temporal DST (kernels_dst.cu) ------------------------------------------------------
+template <typename T>
+struct DstPlan {
+  int N, logN;
+  const T* tw;    // [N/2] (cos, sin)(2 pi k / N) interleaved
+  const T* pre;   // [N]   (cos, sin)(pi m / (2N)) interleaved
+};
+
+// in-place forward transform: x_k <- sum_n x_n sin((2k-1) n pi/(2N)) for every interior column
+// (ghost columns of the grid with n interior points per axis are written as zero)
+template <typename T>
+void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> plan, const int* done,
+                        cudaStream_t st);
+
+// inverse + update: u_n += omega * sum_k y_k sin((2k-1) n pi/(2N)); u in FP64 (mode 1) or
+// out = transform (mode 0, out of type T)
+template <typename T>
+void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
+                        int logP, DstPlan<T> plan, const int* done, cudaStream_t st);
+
+}  // namespace pt
