@@ -151,6 +151,19 @@ pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev);
  * how many GPU kernels a timed region launched. */
 unsigned long long pt_kernel_launch_count(void);
 
+/* ---- Per-kernel timing (tracing) ------------------------------------------------------
+ * pt_profile_enable(1) makes every later launch record a CUDA event pair on its stream; 0 stops
+ * recording.  Per kernel name the library accumulates the event-measured time, the number of
+ * launches, the algorithmic bytes (each operand read once, each result written once) and the
+ * FP64 operation count of those launches.  pt_profile_reset clears the totals.
+ * pt_profile_get(index, ...) synchronises the pending events and fills the totals of entry
+ * `index` (name truncated to name_len - 1 characters); it returns the number of entries, or
+ * -1 if index is out of range; index < 0 only returns the count.  Any output may be NULL. */
+void pt_profile_enable(int on);
+void pt_profile_reset(void);
+int pt_profile_get(int index, char* name, int name_len, double* total_ms, double* bytes,
+                   double* flops, unsigned long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

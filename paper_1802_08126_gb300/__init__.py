@@ -19,7 +19,8 @@ import numpy as np
 from . import _lib
 from ._lib import PT_EDIVERGED, PT_ENOTCONV, PT_OK  # noqa: F401
 
-__all__ = ["Problem", "PtError", "launch_count", "status_name"]
+__all__ = ["Problem", "PtError", "launch_count", "status_name", "profile_enable", "profile_reset",
+           "profile_totals"]
 
 
 class PtError(RuntimeError):
@@ -41,6 +42,30 @@ def _check(status: int, allowed=(PT_OK,)):
 def launch_count() -> int:
     """Kernel launches issued by the library so far (all problems)."""
     return int(_lib.load().pt_kernel_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Record CUDA-event timings of every later kernel launch (per kernel name)."""
+    _lib.load().pt_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    _lib.load().pt_profile_reset()
+
+
+def profile_totals() -> dict:
+    """{kernel name: {"ms", "bytes", "flops", "launches"}} accumulated since the last reset."""
+    L = _lib.load()
+    count = L.pt_profile_get(-1, None, 0, None, None, None, None)
+    out = {}
+    for k in range(count):
+        name = ctypes.create_string_buffer(64)
+        ms, b, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_ulonglong()
+        if L.pt_profile_get(k, name, 64, ctypes.byref(ms), ctypes.byref(b), ctypes.byref(fl), ctypes.byref(n)) < 0:
+            break
+        out[name.value.decode()] = {"ms": ms.value, "bytes": b.value, "flops": fl.value, "launches": n.value}
+    return out
 
 
 def _ptr(a) -> tuple:

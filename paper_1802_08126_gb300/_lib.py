@@ -15,7 +15,8 @@ PT_SOLVER_MG, PT_SOLVER_EXACT_1D = 0, 1
 EXPORTED = (
     "pt_problem_create", "pt_problem_set_rhs", "pt_solve", "pt_problem_destroy", "pt_last_error",
     "pt_status_string", "pt_apply_B", "pt_dst_forward", "pt_dst_inverse", "pt_precond_A",
-    "pt_precond_H", "pt_kernel_launch_count", "pt_problem_get_state",
+    "pt_precond_H", "pt_kernel_launch_count", "pt_problem_get_state", "pt_profile_enable",
+    "pt_profile_reset", "pt_profile_get",
 )
 
 
@@ -69,6 +70,12 @@ def load(path: str = LIB_PATH):
             fn.restype = i
         L.pt_problem_get_state.argtypes = [vp, vp, vp, i]
         L.pt_problem_get_state.restype = i
+        L.pt_profile_enable.argtypes = [i]
+        L.pt_profile_enable.restype = None
+        L.pt_profile_reset.argtypes = []
+        L.pt_profile_reset.restype = None
+        L.pt_profile_get.argtypes = [i, ctypes.c_char_p, i, dp, dp, dp, ctypes.POINTER(ctypes.c_ulonglong)]
+        L.pt_profile_get.restype = i
         L.pt_kernel_launch_count.argtypes = []
         L.pt_kernel_launch_count.restype = ctypes.c_ulonglong
         _lib = L

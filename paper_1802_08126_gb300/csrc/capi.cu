@@ -14,7 +14,6 @@
 
 namespace {
 thread_local std::string g_err;
-std::atomic<unsigned long long> g_launches{0};
 
 pt_status fail(pt_status s, const std::string& msg) {
   g_err = msg;
@@ -43,9 +42,6 @@ double trig(int kind, double arg) {
 }
 }  // namespace
 
-namespace pt {
-void note_launch(int count) { g_launches.fetch_add((unsigned long long)count, std::memory_order_relaxed); }
-}  // namespace pt
 
 using namespace pt;
 
@@ -570,8 +566,6 @@ const char* pt_status_string(pt_status s) {
   }
   return "PT_UNKNOWN";
 }
-
-unsigned long long pt_kernel_launch_count(void) { return g_launches.load(); }
 
 pt_status pt_problem_create(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff,
                             const double* f, int f_on_device, const double* u0, int u0_on_device,

@@ -254,9 +254,11 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
   }
   const int blocks = (int)(S / (2 * C));
   const ColGeom cg{dim, n, logP};
+  double interior = plan.N;
+  for (int d = 0; d < dim; ++d) interior *= n;
+  LaunchScope ls("dst_forward", st, 2.0 * sizeof(T) * interior);
   k_dst_forward<T><<<blocks, kThreads, smem, st>>>(x, S, cg, plan.N, plan.logN, C, (const T2*)plan.tw,
                                                    (const T2*)plan.pre, done);
-  note_launch();
 }
 
 template <typename T>
@@ -272,9 +274,11 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
   }
   const int blocks = (int)(S / (2 * C));
   const ColGeom cg{dim, n, logP};
+  double interior = plan.N;
+  for (int d = 0; d < dim; ++d) interior *= n;
+  LaunchScope ls("dst_inverse", st, (sizeof(T) + (mode == 1 ? 16.0 : (double)sizeof(T))) * interior);
   k_dst_inverse<T><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan.N, plan.logN, C,
                                                    (const T2*)plan.tw, (const T2*)plan.pre, done);
-  note_launch();
 }
 
 template void launch_dst_forward<float>(float*, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);

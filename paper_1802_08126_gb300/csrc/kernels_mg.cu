@@ -393,6 +393,13 @@ __global__ void k_tridiag(const T* __restrict__ r, void* out, int mode, int out_
   if (mode == 0) store_out<T>(out, base + n, 0, out_fp64, (T)0);  // ghost
 }
 
+template <int DIM>
+double level_dofs(int n, int B) {
+  double d = B;
+  for (int k = 0; k < DIM; ++k) d *= n;
+  return d;
+}
+
 template <int DIM, typename T>
 void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode,
                 int out_fp64, const int* done, cudaStream_t st) {
@@ -415,13 +422,22 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     const long long total = g.S * B;
     T* x = (T*)plan.buf[l].x;
     T* r = (T*)plan.buf[l].r;
-    k_jacobi0<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, g, op, total, done);
-    k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, r, g, op, total, done);
     const Level& C = plan.lev[l + 1];
+    const double df = level_dofs<DIM>(g.n, B), dc = level_dofs<DIM>(C.n, B), s = sizeof(T);
+    {
+      LaunchScope ls("mg_jacobi0", st, 2 * s * df);
+      k_jacobi0<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, g, op, total, done);
+    }
+    {
+      LaunchScope ls("mg_residual", st, 3 * s * df);
+      k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, r, g, op, total, done);
+    }
     const long long total_c = C.S * B;
-    k_restrict<DIM, T><<<grid_for(total_c), kThreads, 0, st>>>(r, (T*)plan.buf[l + 1].b, g.logP, g.S,
-                                                               C.n, C.logP, total_c, done);
-    note_launch(3);
+    {
+      LaunchScope ls("mg_restrict", st, s * (df + dc));
+      k_restrict<DIM, T><<<grid_for(total_c), kThreads, 0, st>>>(r, (T*)plan.buf[l + 1].b, g.logP, g.S,
+                                                                 C.n, C.logP, total_c, done);
+    }
     bl = (const T*)plan.buf[l + 1].b;
   }
   // coarse part: levels lc..nlev-1 in one CTA per slice
@@ -449,9 +465,10 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     const int dmode = plan.lc == 0 ? mode : 0;
     const int dfp64 = plan.lc == 0 ? out_fp64 : 0;
     const int threads = plan.lev[plan.lc].S >= 256 ? 256 : 128;
+    const double dl = level_dofs<DIM>(plan.lev[plan.lc].n, B);
+    LaunchScope ls("mg_coarse", st, dl * (sizeof(T) + (dfp64 ? (dmode == 1 ? 16.0 : 8.0) : (double)sizeof(T))));
     k_coarse_vcycle<DIM, T><<<B, threads, smem, st>>>(bl, plan.lev[plan.lc].S, dst, dmode, dfp64,
                                                       plan.tab, plan.a0, op, cp, done);
-    note_launch();
   }
   // upward sweep over the global levels
   for (int l = plan.lc - 1; l >= 0; --l) {
@@ -461,15 +478,25 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     T* x = (T*)plan.buf[l].x;
     T* r = (T*)plan.buf[l].r;
     const Level& C = plan.lev[l + 1];
-    k_prolong_add<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, (const T*)plan.buf[l + 1].x, g,
-                                                                C.logP, C.S, total, done);
-    k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, g, op, total, done);
-    if (l == 0)
+    const double df = level_dofs<DIM>(g.n, B), dc = level_dofs<DIM>(C.n, B), s = sizeof(T);
+    {
+      LaunchScope ls("mg_prolong_add", st, s * (2 * df + dc));
+      k_prolong_add<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, (const T*)plan.buf[l + 1].x, g,
+                                                                  C.logP, C.S, total, done);
+    }
+    {
+      LaunchScope ls("mg_residual", st, 3 * s * df);
+      k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, g, op, total, done);
+    }
+    if (l == 0) {
+      const double ob = out_fp64 ? (mode == 1 ? 16.0 : 8.0) : (mode == 1 ? 2 * s : s);
+      LaunchScope ls("mg_jacobi_update", st, (2 * s + ob) * df);
       k_jacobi_update<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, r, out, mode, out_fp64, g, op,
                                                                     total, done);
-    else
+    } else {
+      LaunchScope ls("mg_jacobi_update", st, 3 * s * df);
       k_jacobi_update<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, r, x, 0, 0, g, op, total, done);
-    note_launch(3);
+    }
   }
 }
 
@@ -488,8 +515,9 @@ void vcycle(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mo
 template <typename T>
 void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T> g, OpBatch<T> op,
                     int B, T* work, const int* done, cudaStream_t st) {
+  const double d = (double)B * g.n, ob = out_fp64 ? (mode == 1 ? 16.0 : 8.0) : (double)sizeof(T);
+  LaunchScope ls("tridiag", st, d * (sizeof(T) + ob));
   k_tridiag<T><<<(B + 63) / 64, 64, 0, st>>>(r, out, mode, out_fp64, g, op, B, work, done);
-  note_launch();
 }
 
 template void vcycle<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, const int*, cudaStream_t);

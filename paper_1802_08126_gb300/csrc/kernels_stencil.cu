@@ -229,12 +229,18 @@ __global__ void k_axpy(double* __restrict__ y, const Tp* __restrict__ x, double 
     } break;                                      \
   }
 
+inline double dofs(int dim, int n, int N) {
+  double d = N;
+  for (int k = 0; k < dim; ++k) d *= n;
+  return d;
+}
+
 void launch_pack(const double* src, const double* u0, double* dst, double scale, int dim, int n,
                  int P, int logP, long long S, int N, cudaStream_t st) {
   (void)P;
   const long long total = S * N;
+  LaunchScope ls("pack", st, 16.0 * dofs(dim, n, N));
   PT_DISPATCH_DIM(dim, k_pack<D><<<grid_for(total), kThreads, 0, st>>>(src, u0, dst, scale, n, logP, total));
-  note_launch();
 }
 
 template <typename T>
@@ -242,8 +248,8 @@ void launch_pack_typed(const double* src, T* dst, int dim, int n, int P, int log
                        int N, cudaStream_t st) {
   (void)P;
   const long long total = S * N;
+  LaunchScope ls("pack", st, (8.0 + sizeof(T)) * dofs(dim, n, N));
   PT_DISPATCH_DIM(dim, k_pack_typed<D, T><<<grid_for(total), kThreads, 0, st>>>(src, dst, n, logP, total));
-  note_launch();
 }
 
 template <typename T>
@@ -253,23 +259,23 @@ void launch_unpack(const T* src, double* dst, int dim, int n, int P, int logP, l
   long long ns = n;
   for (int d = 1; d < dim; ++d) ns *= n;
   const long long total = ns * N;
+  LaunchScope ls("unpack", st, (8.0 + sizeof(T)) * (double)total);
   PT_DISPATCH_DIM(dim, k_unpack<D, T><<<grid_for(total), kThreads, 0, st>>>(src, dst, n, logP, S, total));
-  note_launch();
 }
 
 void launch_apply_B(const double* u, double* out, StencilGeom<double> g, const double* cth, double tau,
                     int N, cudaStream_t st) {
   const long long total = g.S * N;
+  LaunchScope ls("apply_B", st, 16.0 * dofs(g.dim, g.n, N));
   PT_DISPATCH_DIM(g.dim, k_apply_B<D><<<grid_for(total), kThreads, 0, st>>>(u, out, g, cth, tau, total));
-  note_launch();
 }
 
 template <typename Tp>
 void launch_resid_p(const double* u, const double* p, const double* F, Tp* rp, StencilGeom<double> g,
                     const double* cth, double tau, int N, const int* done, cudaStream_t st) {
   const long long total = g.S * N;
+  LaunchScope ls("resid_p", st, (24.0 + sizeof(Tp)) * dofs(g.dim, g.n, N));
   PT_DISPATCH_DIM(g.dim, k_resid_p<D, Tp><<<grid_for(total), kThreads, 0, st>>>(u, p, F, rp, g, cth, tau, total, done));
-  note_launch();
 }
 
 template <typename Tp>
@@ -277,38 +283,38 @@ void launch_resid_u(const double* u, const double* p, const double* F, Tp* ru, d
                     StencilGeom<double> g, const double* cth, double tau, int N, const int* done,
                     cudaStream_t st) {
   const long long total = g.S * N;
+  LaunchScope ls("resid_u", st, (24.0 + sizeof(Tp)) * dofs(g.dim, g.n, N));
   PT_DISPATCH_DIM(g.dim, k_resid_u<D, Tp><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, ru, partials, g, cth, tau, N, total, done));
-  note_launch();
 }
 
 template <typename T>
 void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale, int N,
                            const int* done, cudaStream_t st) {
   const long long total = g.S * N;
+  LaunchScope ls("apply_Abar", st, 2.0 * sizeof(T) * dofs(g.dim, g.n, N));
   PT_DISPATCH_DIM(g.dim, k_apply_A_scaled<D, T><<<grid_for(total), kThreads, 0, st>>>(z, out, g, cth, scale, total, done));
-  note_launch();
 }
 
 void launch_norm2_partials(const double* v, long long count, double* partials, cudaStream_t st) {
+  LaunchScope ls("norm2", st, 8.0 * (double)count);
   k_norm2_partials<<<kReduceBlocks, kThreads, 0, st>>>(v, count, partials);
-  note_launch();
 }
 
 void launch_finalize_residual(const double* partials, SolveState* state, double* hist, int j,
                               double tol, int max_it, cudaStream_t st) {
+  LaunchScope ls("finalize", st, 8.0 * kReduceBlocks);
   k_finalize_residual<<<1, kReduceBlocks, 0, st>>>(partials, state, hist, j, tol, max_it);
-  note_launch();
 }
 
 void launch_finalize_fnorm(const double* partials, SolveState* state, cudaStream_t st) {
+  LaunchScope ls("finalize", st, 8.0 * kReduceBlocks);
   k_finalize_fnorm<<<1, kReduceBlocks, 0, st>>>(partials, state);
-  note_launch();
 }
 
 template <typename Tp>
 void launch_axpy(double* y, const Tp* x, double a, long long count, const int* done, cudaStream_t st) {
+  LaunchScope ls("axpy", st, (16.0 + sizeof(Tp)) * (double)count);
   k_axpy<Tp><<<grid_for(count), kThreads, 0, st>>>(y, x, a, count, done);
-  note_launch();
 }
 
 template void launch_pack_typed<float>(const double*, float*, int, int, int, int, long long, int, cudaStream_t);

@@ -22,7 +22,23 @@ constexpr int kMaxLevels = 16;
 constexpr int kReduceBlocks = 1024;  // fixed grid of the residual reduction (deterministic)
 constexpr int kCoarseMaxElems = 1024; // levels with P^dim <= this run inside one CTA per slice
 
-// Counts every kernel launch of the library (reported by pt_kernel_launch_count).
+// Counts every kernel launch of the library (reported by pt_kernel_launch_count) and, when
+// timing is enabled, brackets it with CUDA events on its stream.  `bytes` is the algorithmic
+// traffic of the launch (every operand read once, every result written once) and `flops` its
+// FP64 arithmetic, both used for roofline figures.
+class LaunchScope {
+ public:
+  LaunchScope(const char* name, cudaStream_t st, double bytes = 0.0, double flops = 0.0);
+  ~LaunchScope();
+  LaunchScope(const LaunchScope&) = delete;
+  LaunchScope& operator=(const LaunchScope&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t st_;
+  double bytes_, flops_;
+  void* e0_;
+};
 void note_launch(int count = 1);
 
 struct Level {
