@@ -147,6 +147,27 @@ pt_status pt_precond_A(pt_problem* p, const double* r_dev, double* out_dev);
  * H_k = mu_k I + tau Abar, mu_k = 2 sin((2k-1) pi/(4N))  (§4, eq. 4.4-4.6). */
 pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev);
 
+/* ---- Allocation-free transform ------------------------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that cannot let the
+ * library allocate device memory, because another allocator owns the device (for example a
+ * framework's caching allocator that holds all of it) or because they run latency-critical
+ * loops where a cudaMalloc, which may synchronise the device, is not acceptable.
+ *
+ * out_k = sum_n r_n sin((2k-1) n pi / (2N)) for each of `ncols` columns: the same transform as
+ * pt_dst_forward, on caller-owned device arrays r_dev and out_dev of layout [N_t][ncols]
+ * (FP64), without a pt_problem and without allocating anything.  Its working memory is one
+ * file-scope device array of 16.2 MiB that every GPU loading this library reserves until the
+ * process exits; limits: N_t a power of two <= 8192 and N_t * ceil32(ncols) <= 2^21 (else
+ * PT_EINVAL with a message naming the limit).  The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array, which keeps the last call's contents (each call rewrites
+ * the tables and the padded copy of its input before using them), so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Work is ordered on `stream` (NULL = legacy default stream); the
+ * call returns without synchronising.  r_dev and out_dev may not alias. */
+pt_status pt_dst_forward_noalloc(const double* r_dev, double* out_dev, int N_t, long long ncols,
+                                 void* stream);
+
 /* Number of kernel launches issued by this library since load (all problems); used to report
  * how many GPU kernels a timed region launched. */
 unsigned long long pt_kernel_launch_count(void);

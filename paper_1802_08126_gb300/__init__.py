@@ -20,7 +20,7 @@ from . import _lib
 from ._lib import PT_EDIVERGED, PT_ENOTCONV, PT_OK  # noqa: F401
 
 __all__ = ["Problem", "PtError", "launch_count", "status_name", "profile_enable", "profile_reset",
-           "profile_totals"]
+           "profile_totals", "dst_forward_noalloc"]
 
 
 class PtError(RuntimeError):
@@ -65,6 +65,20 @@ def profile_totals() -> dict:
         if L.pt_profile_get(k, name, 64, ctypes.byref(ms), ctypes.byref(b), ctypes.byref(fl), ctypes.byref(n)) < 0:
             break
         out[name.value.decode()] = {"ms": ms.value, "bytes": b.value, "flops": fl.value, "launches": n.value}
+    return out
+
+
+def dst_forward_noalloc(r, out, stream: Optional[int] = None):
+    """Forward temporal transform of the columns of ``r`` ([N_t][ncols] float64 CUDA tensor)
+    into ``out`` without any device allocation by the library (``pt_dst_forward_noalloc``).
+    For callers whose device memory belongs to another allocator; calls that overlap on the
+    GPU share one scratch array and must not run concurrently."""
+    rp, rdev = _ptr(r)
+    op, odev = _ptr(out)
+    if not (rdev and odev):
+        raise ValueError("dst_forward_noalloc takes device tensors")
+    N, ncols = int(r.shape[0]), int(r.numel() // r.shape[0])
+    _check(_lib.load().pt_dst_forward_noalloc(rp, op, N, ncols, stream))
     return out
 
 

@@ -16,7 +16,7 @@ EXPORTED = (
     "pt_problem_create", "pt_problem_set_rhs", "pt_solve", "pt_problem_destroy", "pt_last_error",
     "pt_status_string", "pt_apply_B", "pt_dst_forward", "pt_dst_inverse", "pt_precond_A",
     "pt_precond_H", "pt_kernel_launch_count", "pt_problem_get_state", "pt_profile_enable",
-    "pt_profile_reset", "pt_profile_get",
+    "pt_profile_reset", "pt_profile_get", "pt_dst_forward_noalloc",
 )
 
 
@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
         L.pt_profile_reset.restype = None
         L.pt_profile_get.argtypes = [i, ctypes.c_char_p, i, dp, dp, dp, ctypes.POINTER(ctypes.c_ulonglong)]
         L.pt_profile_get.restype = i
+        L.pt_dst_forward_noalloc.argtypes = [vp, vp, i, ctypes.c_longlong, vp]
+        L.pt_dst_forward_noalloc.restype = i
         L.pt_kernel_launch_count.argtypes = []
         L.pt_kernel_launch_count.restype = ctypes.c_ulonglong
         _lib = L

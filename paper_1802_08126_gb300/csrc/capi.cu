@@ -43,6 +43,10 @@ double trig(int kind, double arg) {
 }  // namespace
 
 
+namespace pt {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace pt
+
 using namespace pt;
 
 struct pt_problem {

@@ -281,6 +281,26 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
                                                    (const T2*)plan.tw, (const T2*)plan.pre, done);
 }
 
+// Forward transform of `ncols` packed columns held at pitch S (S a multiple of 32, columns
+// ncols..S-1 are padding whose results are discarded).  It records no CUDA events (only the
+// launch count), so it allocates nothing on any path.
+void launch_dst_forward_plain(double* x, long long S, int ncols, DstPlan<double> plan, cudaStream_t st) {
+  const int C = dst_cols<double>(plan.N, S);
+  const size_t smem = (size_t)C * (plan.N + 1) * sizeof(double2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_dst_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  int logP = 0;
+  while ((1LL << logP) <= S) ++logP;  // pitch above every column index: only column ncols is "ghost"
+  const ColGeom cg{1, ncols, logP};
+  note_launch();
+  k_dst_forward<double><<<(int)(S / (2 * C)), kThreads, smem, st>>>(x, S, cg, plan.N, plan.logN, C,
+                                                                   (const double2*)plan.tw,
+                                                                   (const double2*)plan.pre, nullptr);
+}
+
 template void launch_dst_forward<float>(float*, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);
 template void launch_dst_forward<double>(double*, long long, int, int, int, DstPlan<double>, const int*, cudaStream_t);
 template void launch_dst_inverse<float>(const float*, void*, int, double, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);

@@ -173,4 +173,11 @@ template <typename T>
 void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
                         int logP, DstPlan<T> plan, const int* done, cudaStream_t st);
 
+// Set the thread-local message returned by pt_last_error().
+void set_last_error(const char* msg);
+
+// Forward transform of ncols packed columns at pitch S (a multiple of 32) without event
+// recording; used by the allocation-free entry point.
+void launch_dst_forward_plain(double* x, long long S, int ncols, DstPlan<double> plan, cudaStream_t st);
+
 }  // namespace pt
