@@ -81,6 +81,9 @@ struct pt_problem {
   void* dst_tw = nullptr;                       // [N/2] complex
   void* dst_pre = nullptr;                      // [N] complex
   void* tri_work = nullptr;
+  bool hvar = true;                             // Abar has a non-constant coefficient
+  void* dinvH[kMaxLevels] = {};                 // [N] w / D of H_k per level (constant Abar)
+  void* jinvA[kMaxLevels] = {};                 // cached w / D of tau A_n per level (FP64, 2-D)
   double* partials = nullptr;
   SolveState* state = nullptr;
   double* hist = nullptr;
@@ -212,6 +215,11 @@ void apply_precond_A(pt_problem* p, const T* b, void* out, int mode, int out_fp6
   if (p->exact1d) {
     launch_tridiag<T>(b, out, mode, out_fp64, geom<T>(p, 0), op_A<T>(p), p->N, (T*)p->tri_work, done,
                       p->st);
+  } else if (p->dim == 2) {
+    const T* jinv[kMaxLevels];
+    for (int l = 0; l < kMaxLevels; ++l) jinv[l] = (const T*)p->jinvA[l];
+    vcycle2d<T>(mg_plan<T>(p), op_A<T>(p), b, out, mode, out_fp64, true, nullptr,
+                p->jinvA[0] ? jinv : nullptr, done, p->st);
   } else {
     vcycle<T>(mg_plan<T>(p), op_A<T>(p), b, out, mode, out_fp64, done, p->st);
   }
@@ -220,10 +228,16 @@ void apply_precond_A(pt_problem* p, const T* b, void* out, int mode, int out_fp6
 // H_k solve (exact in 1-D if requested, else one V-cycle)
 template <typename T>
 void apply_Hk_solve(pt_problem* p, const T* b, T* out, const int* done) {
-  if (p->exact1d)
+  if (p->exact1d) {
     launch_tridiag<T>(b, out, 0, 0, geom<T>(p, 0), op_H<T>(p), p->N, (T*)p->tri_work, done, p->st);
-  else
+  } else if (p->dim == 2) {
+    const T* dinv[kMaxLevels];
+    for (int l = 0; l < kMaxLevels; ++l) dinv[l] = (const T*)p->dinvH[l];
+    vcycle2d<T>(mg_plan<T>(p), op_H<T>(p), b, out, 0, 0, p->hvar, p->hvar ? nullptr : dinv, nullptr,
+                done, p->st);
+  } else {
     vcycle<T>(mg_plan<T>(p), op_H<T>(p), b, out, 0, 0, done, p->st);
+  }
 }
 
 // W1 = rhat (in place transform done by caller) -> W2 = yhat = (2 tau/N) H~^-1 Abar H~^-1 rhat
@@ -330,14 +344,17 @@ pt_status setup_precision(pt_problem* p) {
   p->W2 = alloc_padded<T>(p, L0, p->N, &st);
   if (!p->W2) return st;
   if (!p->exact1d) {
+    const bool fused = p->dim == 2;  // fused 2-D kernels keep no level-0 iterate and no residuals
     for (int l = 0; l <= p->lc && l < p->nlev; ++l) {
       if (l > 0) {
         p->mg_b[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
         if (!p->mg_b[l]) return st;
       }
-      p->mg_x[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
-      if (!p->mg_x[l]) return st;
-      if (l < p->lc) {
+      if (!fused || l > 0) {
+        p->mg_x[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
+        if (!p->mg_x[l]) return st;
+      }
+      if (!fused && l < p->lc) {
         p->mg_r[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
         if (!p->mg_r[l]) return st;
       }
@@ -361,6 +378,26 @@ pt_status setup_precision(pt_problem* p) {
   if ((st = upload<T>(p, p->cthA, cthA)) != PT_OK) return st;
   if ((st = upload<T>(p, p->sigH, mu)) != PT_OK) return st;
   if ((st = upload<T>(p, p->cthH, cthH)) != PT_OK) return st;
+  // Abar with a constant coefficient: its Jacobi factor w / (mu_k + 2 dim tau a0 / h^2) per level
+  p->hvar = !(std::fabs(p->cthbar) <= 1e-14 * std::fabs(p->coeff.a0));
+  if (!p->exact1d && p->dim == 2 && !p->hvar) {
+    for (int l = 0; l < p->lc; ++l) {
+      std::vector<double> dv(p->N);
+      const double a0s = p->tau * p->coeff.a0 / (p->lev[l].h * p->lev[l].h);
+      for (int k = 0; k < p->N; ++k) dv[k] = p->jacobi / (mu[k] + 2.0 * p->dim * a0s);
+      if (!(p->dinvH[l] = alloc_bytes(p, nb, &st))) return st;
+      if ((st = upload<T>(p, p->dinvH[l], dv)) != PT_OK) return st;
+    }
+  }
+  // FP64 2-D: cache w / D of every tau A_n (a division per point per smoothing step otherwise)
+  if (!p->exact1d && p->dim == 2 && sizeof(T) == 8) {
+    for (int l = 0; l < p->lc; ++l) {
+      T* j = alloc_padded<T>(p, p->lev[l], p->N, &st);
+      if (!j) return st;
+      p->jinvA[l] = j;
+      launch_make_jinv<T>(j, geom<T>(p, l), op_A<T>(p), p->N, p->st);
+    }
+  }
   // DST tables: twiddles e^{2 pi i k/N}, k < N/2, and e^{i pi m/(2N)}, m < N
   std::vector<double> tw(2 * std::max(1, p->N / 2)), pre(2 * p->N);
   for (int k = 0; k < p->N / 2; ++k) {

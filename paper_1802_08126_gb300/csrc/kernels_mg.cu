@@ -400,6 +400,41 @@ double level_dofs(int n, int B) {
   return d;
 }
 
+// levels lc..nlev-1 of all B slices: one CTA per slice in shared memory; the level-lc input is
+// bl, the result goes to `out` (mode) when lc == 0, else to the level-lc correction buffer.
+template <int DIM, typename T>
+void coarse_launch(const MGPlan<T>& plan, OpBatch<T> op, const T* bl, void* out, int mode,
+                   int out_fp64, const int* done, cudaStream_t st) {
+  const int B = plan.B;
+  CoarsePlan cp;
+  cp.nl = plan.nlev - plan.lc;
+  int off = 0;
+  for (int k = 0; k < cp.nl; ++k) {
+    const Level& L = plan.lev[plan.lc + k];
+    CoarseLevel& c = cp.lv[k];
+    c.n = L.n;
+    c.logP = L.logP;
+    c.S = (int)L.S;
+    c.guard = 0;
+    for (int d = 0, pk = 1; d < DIM; ++d, pk *= L.P) c.guard += pk;  // (-1,-1,-1) corner
+    c.guard = (c.guard + 3) & ~3;
+    c.off = off;
+    c.tab = L.tab;
+    c.h2inv_d = 1.0 / (L.h * L.h);
+    c.h2inv = (float)c.h2inv_d;
+    off += 3 * (c.guard + c.S);
+  }
+  const size_t smem = (size_t)off * sizeof(T);
+  void* dst = plan.lc == 0 ? out : plan.buf[plan.lc].x;
+  const int dmode = plan.lc == 0 ? mode : 0;
+  const int dfp64 = plan.lc == 0 ? out_fp64 : 0;
+  const int threads = plan.lev[plan.lc].S >= 256 ? 256 : 128;
+  const double dl = level_dofs<DIM>(plan.lev[plan.lc].n, B);
+  LaunchScope ls("mg_coarse", st, dl * (sizeof(T) + (dfp64 ? (dmode == 1 ? 16.0 : 8.0) : (double)sizeof(T))));
+  k_coarse_vcycle<DIM, T><<<B, threads, smem, st>>>(bl, plan.lev[plan.lc].S, dst, dmode, dfp64,
+                                                    plan.tab, plan.a0, op, cp, done);
+}
+
 template <int DIM, typename T>
 void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode,
                 int out_fp64, const int* done, cudaStream_t st) {
@@ -440,36 +475,7 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     }
     bl = (const T*)plan.buf[l + 1].b;
   }
-  // coarse part: levels lc..nlev-1 in one CTA per slice
-  {
-    CoarsePlan cp;
-    cp.nl = plan.nlev - plan.lc;
-    int off = 0;
-    for (int k = 0; k < cp.nl; ++k) {
-      const Level& L = plan.lev[plan.lc + k];
-      CoarseLevel& c = cp.lv[k];
-      c.n = L.n;
-      c.logP = L.logP;
-      c.S = (int)L.S;
-      c.guard = 0;
-      for (int d = 0, pk = 1; d < DIM; ++d, pk *= L.P) c.guard += pk;  // (-1,-1,-1) corner
-      c.guard = (c.guard + 3) & ~3;
-      c.off = off;
-      c.tab = L.tab;
-      c.h2inv_d = 1.0 / (L.h * L.h);
-      c.h2inv = (float)c.h2inv_d;
-      off += 3 * (c.guard + c.S);
-    }
-    const size_t smem = (size_t)off * sizeof(T);
-    void* dst = plan.lc == 0 ? out : plan.buf[plan.lc].x;
-    const int dmode = plan.lc == 0 ? mode : 0;
-    const int dfp64 = plan.lc == 0 ? out_fp64 : 0;
-    const int threads = plan.lev[plan.lc].S >= 256 ? 256 : 128;
-    const double dl = level_dofs<DIM>(plan.lev[plan.lc].n, B);
-    LaunchScope ls("mg_coarse", st, dl * (sizeof(T) + (dfp64 ? (dmode == 1 ? 16.0 : 8.0) : (double)sizeof(T))));
-    k_coarse_vcycle<DIM, T><<<B, threads, smem, st>>>(bl, plan.lev[plan.lc].S, dst, dmode, dfp64,
-                                                      plan.tab, plan.a0, op, cp, done);
-  }
+  coarse_launch<DIM, T>(plan, op, bl, out, mode, out_fp64, done, st);
   // upward sweep over the global levels
   for (int l = plan.lc - 1; l >= 0; --l) {
     const StencilGeom<T> g = geom(l);
@@ -513,6 +519,16 @@ void vcycle(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mo
 }
 
 template <typename T>
+void vcycle_coarse(const MGPlan<T>& plan, OpBatch<T> op, const T* bl, void* out, int mode, int out_fp64,
+                   const int* done, cudaStream_t st) {
+  switch (plan.dim) {
+    case 1: coarse_launch<1, T>(plan, op, bl, out, mode, out_fp64, done, st); break;
+    case 2: coarse_launch<2, T>(plan, op, bl, out, mode, out_fp64, done, st); break;
+    default: coarse_launch<3, T>(plan, op, bl, out, mode, out_fp64, done, st); break;
+  }
+}
+
+template <typename T>
 void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T> g, OpBatch<T> op,
                     int B, T* work, const int* done, cudaStream_t st) {
   const double d = (double)B * g.n, ob = out_fp64 ? (mode == 1 ? 16.0 : 8.0) : (double)sizeof(T);
@@ -522,6 +538,8 @@ void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T
 
 template void vcycle<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, const int*, cudaStream_t);
 template void vcycle<double>(const MGPlan<double>&, OpBatch<double>, const double*, void*, int, int, const int*, cudaStream_t);
+template void vcycle_coarse<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, const int*, cudaStream_t);
+template void vcycle_coarse<double>(const MGPlan<double>&, OpBatch<double>, const double*, void*, int, int, const int*, cudaStream_t);
 template void launch_tridiag<float>(const float*, void*, int, int, StencilGeom<float>, OpBatch<float>, int, float*, const int*, cudaStream_t);
 template void launch_tridiag<double>(const double*, void*, int, int, StencilGeom<double>, OpBatch<double>, int, double*, const int*, cudaStream_t);
 

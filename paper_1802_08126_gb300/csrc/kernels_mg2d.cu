@@ -1,0 +1,323 @@
+// Fused 2-D multigrid level kernels (same V(1,1) as kernels_mg.cu, fewer passes over HBM).
+//
+// With a zero initial guess the pre-smoothed iterate is x1 = w D^-1 b, a point-wise function of
+// the right-hand side, so it is never stored: the "down" kernel forms x1, the residual
+// r = b - L x1 and its full-weighting restriction in shared memory and writes only the coarse
+// right-hand side; the "up" kernel re-forms x1 from b, adds the prolonged coarse correction,
+// applies the post-smoothing step x3 = x2 + w D^-1 (b - L x2), and writes (or accumulates) x3.
+// Per level the fine grid is read twice and written once.
+//
+// Face coefficients are formed in shared memory from the 1-D tables (VAR) or are the constant
+// a0 (the reference operator Abar has a time-mean coefficient, constant for every workload
+// whose coefficient oscillates in time).  The Jacobi factor w D^-1 is a per-slice constant
+// (constant coefficient), read from a per-level cache (FP64 variable coefficient, where the
+// division would dominate the FP64 instruction budget), or computed (FP32).
+#include "stencil_common.cuh"
+
+namespace pt {
+namespace {
+
+constexpr int kDownTX = 16, kDownTY = 8;  // coarse points per down tile
+constexpr int kUpTX = 32, kUpTY = 16;     // fine points per up tile
+
+template <typename T>
+struct Mg2Args {
+  int nf, logPf;      // fine level
+  long long Sf;
+  int nc, logPc;      // coarse level
+  long long Sc;
+  const T* tab;       // fine-level tables: node_x, face_x, node_y, face_y (Pf each)
+  T a0s;              // s * a0 / h^2
+  T s_h2;             // s / h^2
+  const T* sig;       // [B]
+  const T* cth;       // [B]
+  const T* dinv;      // [B] w / D per slice (DM == 0)
+  const T* jinv;      // cached w / D, fine padded layout (DM == 1)
+  T omega;
+};
+
+// face coefficients of region (rows RH, cols RW, origin fy0, fx0), scaled by s/h^2:
+//   fxs[ry][rx] = lower x-face of point (fy0+ry, fx0+rx), rx in [0, RW]
+//   fys[ry][rx] = lower y-face of point (fy0+ry, fx0+rx), ry in [0, RH]
+template <typename T>
+__device__ __forceinline__ void load_faces(T* fxs, T* fys, int RW, int RH, int fx0, int fy0,
+                                           const Mg2Args<T>& a, T cths) {
+  const int Pf = 1 << a.logPf;
+  const T* nx = a.tab;
+  const T* fx = a.tab + Pf;
+  const T* ny = a.tab + 2 * Pf;
+  const T* fy = a.tab + 3 * Pf;
+  for (int k = threadIdx.x; k < RH * (RW + 1); k += blockDim.x) {
+    const int ry = k / (RW + 1), rx = k - ry * (RW + 1);
+    const int x = fx0 + rx, y = fy0 + ry;
+    T v = (T)0;
+    if (y >= 0 && y < a.nf && x >= 0 && x <= a.nf) v = a.a0s + cths * ny[y] * fx[x];
+    fxs[k] = v;
+  }
+  for (int k = threadIdx.x; k < (RH + 1) * RW; k += blockDim.x) {
+    const int ry = k / RW, rx = k - ry * RW;
+    const int x = fx0 + rx, y = fy0 + ry;
+    T v = (T)0;
+    if (x >= 0 && x < a.nf && y >= 0 && y <= a.nf) v = a.a0s + cths * nx[x] * fy[y];
+    fys[k] = v;
+  }
+}
+
+// w D^-1 at region point (ry, rx) = fine (y, x), interior only
+template <typename T, bool VAR, int DM>
+__device__ __forceinline__ T jacobi_factor(const Mg2Args<T>& a, int b, long long gi, const T* fxs,
+                                           const T* fys, int RW, int ry, int rx, T sig) {
+  if (DM == 0) return a.dinv[b];
+  if (DM == 1) return a.jinv[gi];
+  T dsum;
+  if (VAR) {
+    dsum = fxs[ry * (RW + 1) + rx] + fxs[ry * (RW + 1) + rx + 1] + fys[ry * RW + rx] + fys[(ry + 1) * RW + rx];
+  } else {
+    dsum = (T)4 * a.a0s;
+  }
+  return a.omega / (sig + dsum);
+}
+
+template <typename T, bool VAR, int DM>
+__global__ void __launch_bounds__(256) k_mg2_down(const T* __restrict__ bf, T* __restrict__ bc,
+                                                  Mg2Args<T> a, const int* done) {
+  if (stop_requested(done)) return;
+  constexpr int RW = 2 * kDownTX + 3, RH = 2 * kDownTY + 3;
+  __shared__ T sb[RH * RW];
+  __shared__ T sx[RH * RW];
+  __shared__ T sr[(RH - 2) * (RW - 2)];
+  __shared__ T sfx[VAR ? RH * (RW + 1) : 1];
+  __shared__ T sfy[VAR ? (RH + 1) * RW : 1];
+  const int b = blockIdx.z;
+  const int X0 = blockIdx.x * kDownTX, Y0 = blockIdx.y * kDownTY;  // coarse tile origin
+  const int fx0 = 2 * X0 - 1, fy0 = 2 * Y0 - 1;                   // fine region origin
+  const int Pf = 1 << a.logPf;
+  const long long base = (long long)b * a.Sf;
+  const T sig = a.sig[b];
+  const T cths = a.s_h2 * a.cth[b];
+  if (VAR) load_faces<T>(sfx, sfy, RW, RH, fx0, fy0, a, cths);
+  __syncthreads();
+  // b and x1 = w D^-1 b on the region (zero outside the interior)
+  for (int k = threadIdx.x; k < RH * RW; k += blockDim.x) {
+    const int ry = k / RW, rx = k - ry * RW;
+    const int x = fx0 + rx, y = fy0 + ry;
+    T bv = (T)0, xv = (T)0;
+    if (x >= 0 && x < a.nf && y >= 0 && y < a.nf) {
+      const long long gi = base + (long long)y * Pf + x;
+      bv = bf[gi];
+      xv = bv * jacobi_factor<T, VAR, DM>(a, b, gi, sfx, sfy, RW, ry, rx, sig);
+    }
+    sb[k] = bv;
+    sx[k] = xv;
+  }
+  __syncthreads();
+  // r = b - L x1 on the inner region (fine points 2X0 .. 2X0 + 2 TX)
+  for (int k = threadIdx.x; k < (RH - 2) * (RW - 2); k += blockDim.x) {
+    const int iy = k / (RW - 2), ix = k - iy * (RW - 2);
+    const int ry = iy + 1, rx = ix + 1;
+    const int c = ry * RW + rx;
+    const T xc = sx[c];
+    T Lx;
+    if (VAR) {
+      const T aw = sfx[ry * (RW + 1) + rx], ae = sfx[ry * (RW + 1) + rx + 1];
+      const T as = sfy[ry * RW + rx], an = sfy[(ry + 1) * RW + rx];
+      Lx = sig * xc + aw * (xc - sx[c - 1]) + ae * (xc - sx[c + 1]) + as * (xc - sx[c - RW]) +
+           an * (xc - sx[c + RW]);
+    } else {
+      Lx = (sig + (T)4 * a.a0s) * xc - a.a0s * ((sx[c - 1] + sx[c + 1]) + (sx[c - RW] + sx[c + RW]));
+    }
+    sr[k] = sb[c] - Lx;
+  }
+  __syncthreads();
+  // full weighting onto the coarse tile
+  const int Pc = 1 << a.logPc;
+  for (int k = threadIdx.x; k < kDownTX * kDownTY; k += blockDim.x) {
+    const int cy = k / kDownTX, cx = k - cy * kDownTX;
+    const int X = X0 + cx, Y = Y0 + cy;
+    if (X >= a.nc || Y >= a.nc) continue;
+    const int RW2 = RW - 2;
+    const int c = (2 * cy + 1) * RW2 + (2 * cx + 1);
+    const T r0 = (T)0.25 * (sr[c - RW2 - 1] + sr[c - RW2 + 1]) + (T)0.5 * sr[c - RW2];
+    const T r1 = (T)0.25 * (sr[c - 1] + sr[c + 1]) + (T)0.5 * sr[c];
+    const T r2 = (T)0.25 * (sr[c + RW2 - 1] + sr[c + RW2 + 1]) + (T)0.5 * sr[c + RW2];
+    bc[(long long)b * a.Sc + (long long)Y * Pc + X] = (T)0.25 * (r0 + r2) + (T)0.5 * r1;
+  }
+}
+
+template <typename T, bool VAR, int DM>
+__global__ void __launch_bounds__(256) k_mg2_up(const T* __restrict__ bf, const T* __restrict__ ec,
+                                                void* out, int mode, int out_fp64, Mg2Args<T> a,
+                                                const int* done) {
+  if (stop_requested(done)) return;
+  constexpr int RW = kUpTX + 2, RH = kUpTY + 2;
+  constexpr int CW = kUpTX / 2 + 2, CH = kUpTY / 2 + 2;
+  __shared__ T sb[RH * RW];
+  __shared__ T sx[RH * RW];
+  __shared__ T se[CH * CW];
+  __shared__ T sfx[VAR ? RH * (RW + 1) : 1];
+  __shared__ T sfy[VAR ? (RH + 1) * RW : 1];
+  const int b = blockIdx.z;
+  const int X0 = blockIdx.x * kUpTX, Y0 = blockIdx.y * kUpTY;  // fine tile origin (even)
+  const int fx0 = X0 - 1, fy0 = Y0 - 1;
+  const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;                 // coarse region origin
+  const int Pf = 1 << a.logPf, Pc = 1 << a.logPc;
+  const long long base = (long long)b * a.Sf;
+  const T sig = a.sig[b];
+  const T cths = a.s_h2 * a.cth[b];
+  if (VAR) load_faces<T>(sfx, sfy, RW, RH, fx0, fy0, a, cths);
+  for (int k = threadIdx.x; k < CH * CW; k += blockDim.x) {
+    const int cy = k / CW, cx = k - cy * CW;
+    const int X = cx0 + cx, Y = cy0 + cy;
+    se[k] = (X >= 0 && X < a.nc && Y >= 0 && Y < a.nc) ? ec[(long long)b * a.Sc + (long long)Y * Pc + X] : (T)0;
+  }
+  __syncthreads();
+  // x2 = w D^-1 b + P e on the region
+  for (int k = threadIdx.x; k < RH * RW; k += blockDim.x) {
+    const int ry = k / RW, rx = k - ry * RW;
+    const int x = fx0 + rx, y = fy0 + ry;
+    T bv = (T)0, xv = (T)0;
+    if (x >= 0 && x < a.nf && y >= 0 && y < a.nf) {
+      const long long gi = base + (long long)y * Pf + x;
+      bv = bf[gi];
+      xv = bv * jacobi_factor<T, VAR, DM>(a, b, gi, sfx, sfy, RW, ry, rx, sig);
+      // d-linear interpolation: odd fine index = coarse point (x-1)/2, even = mean of x/2-1, x/2
+      const int ex = (x >> 1) - cx0, ey = (y >> 1) - cy0;  // smem index of coarse x/2, y/2
+      T row0, row1;
+      if (x & 1) {
+        row0 = se[(ey - ((y & 1) ? 0 : 1)) * CW + ex];
+        row1 = se[ey * CW + ex];
+      } else {
+        row0 = (T)0.5 * (se[(ey - ((y & 1) ? 0 : 1)) * CW + ex - 1] + se[(ey - ((y & 1) ? 0 : 1)) * CW + ex]);
+        row1 = (T)0.5 * (se[ey * CW + ex - 1] + se[ey * CW + ex]);
+      }
+      xv += (y & 1) ? row1 : (T)0.5 * (row0 + row1);
+    }
+    sb[k] = bv;
+    sx[k] = xv;
+  }
+  __syncthreads();
+  // x3 = x2 + w D^-1 (b - L x2) on the tile
+  for (int k = threadIdx.x; k < kUpTX * kUpTY; k += blockDim.x) {
+    const int iy = k / kUpTX, ix = k - iy * kUpTX;
+    const int x = X0 + ix, y = Y0 + iy;
+    if (x >= Pf || y >= Pf) continue;
+    const long long gi = base + (long long)y * Pf + x;
+    if (x >= a.nf || y >= a.nf) {
+      if (mode == 0) store_out<T>(out, gi, 0, out_fp64, (T)0);
+      continue;
+    }
+    const int ry = iy + 1, rx = ix + 1;
+    const int c = ry * RW + rx;
+    const T xc = sx[c];
+    T Lx;
+    if (VAR) {
+      const T aw = sfx[ry * (RW + 1) + rx], ae = sfx[ry * (RW + 1) + rx + 1];
+      const T as = sfy[ry * RW + rx], an = sfy[(ry + 1) * RW + rx];
+      Lx = sig * xc + aw * (xc - sx[c - 1]) + ae * (xc - sx[c + 1]) + as * (xc - sx[c - RW]) +
+           an * (xc - sx[c + RW]);
+    } else {
+      Lx = (sig + (T)4 * a.a0s) * xc - a.a0s * ((sx[c - 1] + sx[c + 1]) + (sx[c - RW] + sx[c + RW]));
+    }
+    const T jf = jacobi_factor<T, VAR, DM>(a, b, gi, sfx, sfy, RW, ry, rx, sig);
+    store_out<T>(out, gi, mode, out_fp64, xc + jf * (sb[c] - Lx));
+  }
+}
+
+// w D^-1 for every interior point of one level (FP64 variable-coefficient cache)
+template <typename T>
+__global__ void k_make_jinv(T* __restrict__ jinv, StencilGeom<T> g, OpBatch<T> op, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    T v = (T)0;
+    if (decode<2>(i, g.logP, g.n, t, x, y, z)) {
+      T am[3], ap[3];
+      face_coefs<2, T>(g.tab, g.P, x, y, z, op.cth[t], g.a0, am, ap);
+      v = op.omega / (op.sig[t] + op.s * g.h2inv * face_sum<2, T>(am, ap));
+    }
+    jinv[i] = v;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void vcycle2d(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode, int out_fp64,
+              bool var, const T* const* dinv_slice, const T* const* jinv, const int* done,
+              cudaStream_t st) {
+  const int B = plan.B;
+  auto args = [&](int l) {
+    Mg2Args<T> a;
+    const Level& F = plan.lev[l];
+    const Level& C = plan.lev[l + 1];
+    a.nf = F.n;
+    a.logPf = F.logP;
+    a.Sf = F.S;
+    a.nc = C.n;
+    a.logPc = C.logP;
+    a.Sc = C.S;
+    a.tab = plan.tab + F.tab;
+    const double h2inv = 1.0 / (F.h * F.h);
+    a.a0s = (T)((double)op.s * (double)plan.a0 * h2inv);
+    a.s_h2 = (T)((double)op.s * h2inv);
+    a.sig = op.sig;
+    a.cth = op.cth;
+    a.dinv = dinv_slice ? dinv_slice[l] : nullptr;
+    a.jinv = jinv ? jinv[l] : nullptr;
+    a.omega = op.omega;
+    return a;
+  };
+  const int dm = var ? (jinv ? 1 : 2) : 0;
+  const T* bl = b0;
+  for (int l = 0; l < plan.lc; ++l) {
+    const Mg2Args<T> a = args(l);
+    const dim3 grid((a.nc + kDownTX - 1) / kDownTX, (a.nc + kDownTY - 1) / kDownTY, B);
+    const double df = (double)B * a.nf * a.nf, dc = (double)B * a.nc * a.nc;
+    LaunchScope ls("mg2_down", st, sizeof(T) * (df + dc) + (dm == 1 ? sizeof(T) * df : 0.0));
+    T* bc = (T*)plan.buf[l + 1].b;
+    if (dm == 0)
+      k_mg2_down<T, false, 0><<<grid, 256, 0, st>>>(bl, bc, a, done);
+    else if (dm == 1)
+      k_mg2_down<T, true, 1><<<grid, 256, 0, st>>>(bl, bc, a, done);
+    else
+      k_mg2_down<T, true, 2><<<grid, 256, 0, st>>>(bl, bc, a, done);
+    bl = bc;
+  }
+  vcycle_coarse<T>(plan, op, bl, out, mode, out_fp64, done, st);
+  for (int l = plan.lc - 1; l >= 0; --l) {
+    const Mg2Args<T> a = args(l);
+    const int Pf = 1 << a.logPf;
+    const dim3 grid((Pf + kUpTX - 1) / kUpTX, (Pf + kUpTY - 1) / kUpTY, B);
+    const T* bf = l == 0 ? b0 : (const T*)plan.buf[l].b;
+    void* o = l == 0 ? out : plan.buf[l].x;
+    const int om = l == 0 ? mode : 0;
+    const int of = l == 0 ? out_fp64 : 0;
+    const double df = (double)B * a.nf * a.nf, dc = (double)B * a.nc * a.nc;
+    const double ob = of ? (om == 1 ? 16.0 : 8.0) : (om == 1 ? 2.0 * sizeof(T) : (double)sizeof(T));
+    LaunchScope ls("mg2_up", st, sizeof(T) * (df + dc) + ob * df + (dm == 1 ? sizeof(T) * df : 0.0));
+    const T* e = (const T*)plan.buf[l + 1].x;
+    if (dm == 0)
+      k_mg2_up<T, false, 0><<<grid, 256, 0, st>>>(bf, e, o, om, of, a, done);
+    else if (dm == 1)
+      k_mg2_up<T, true, 1><<<grid, 256, 0, st>>>(bf, e, o, om, of, a, done);
+    else
+      k_mg2_up<T, true, 2><<<grid, 256, 0, st>>>(bf, e, o, om, of, a, done);
+  }
+}
+
+template <typename T>
+void launch_make_jinv(T* jinv, StencilGeom<T> g, OpBatch<T> op, int B, cudaStream_t st) {
+  const long long total = g.S * B;
+  LaunchScope ls("make_jinv", st, sizeof(T) * (double)total);
+  k_make_jinv<T><<<grid_for(total), kThreads, 0, st>>>(jinv, g, op, total);
+}
+
+template void vcycle2d<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, bool,
+                              const float* const*, const float* const*, const int*, cudaStream_t);
+template void vcycle2d<double>(const MGPlan<double>&, OpBatch<double>, const double*, void*, int, int, bool,
+                               const double* const*, const double* const*, const int*, cudaStream_t);
+template void launch_make_jinv<float>(float*, StencilGeom<float>, OpBatch<float>, int, cudaStream_t);
+template void launch_make_jinv<double>(double*, StencilGeom<double>, OpBatch<double>, int, cudaStream_t);
+
+}  // namespace pt

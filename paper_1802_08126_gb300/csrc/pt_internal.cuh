@@ -148,6 +148,21 @@ template <typename T>
 void vcycle(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode, int out_fp64,
             const int* done, cudaStream_t st);
 
+// Levels lc..nlev-1 of a V-cycle (one CTA per slice); input bl at level lc.
+template <typename T>
+void vcycle_coarse(const MGPlan<T>& plan, OpBatch<T> op, const T* bl, void* out, int mode, int out_fp64,
+                   const int* done, cudaStream_t st);
+
+// Fused 2-D V-cycle (kernels_mg2d.cu).  var: variable face coefficients (else the constant a0);
+// dinv_slice[l]: per-level [B] arrays of w/D for constant coefficients; jinv[l]: per-level cached
+// w/D (padded layout) for variable coefficients, or nullptr to compute it in the kernels.
+template <typename T>
+void vcycle2d(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode, int out_fp64,
+              bool var, const T* const* dinv_slice, const T* const* jinv, const int* done,
+              cudaStream_t st);
+template <typename T>
+void launch_make_jinv(T* jinv, StencilGeom<T> g, OpBatch<T> op, int B, cudaStream_t st);
+
 // exact batched tridiagonal solve for 1-D: x_b = (sig_b I + s A(cth_b))^-1 r_b
 template <typename T>
 void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T> g, OpBatch<T> op,
