@@ -80,6 +80,11 @@ struct pt_problem {
   double cthbar = 0.0;
   void* dst_tw = nullptr;                       // [N/2] complex
   void* dst_pre = nullptr;                      // [N] complex
+  int blueM = 0, blueLogM = 0;                  // Bluestein length (N not a power of two)
+  void* blue_chirp = nullptr;                   // [N] complex
+  void* blue_gfwd = nullptr;                    // [M] complex
+  void* blue_ginv = nullptr;                    // [M] complex
+  void* blue_tw = nullptr;                      // [M/2] complex
   void* tri_work = nullptr;
   bool hvar = true;                             // Abar has a non-constant coefficient
   void* dinvH[kMaxLevels] = {};                 // [N] w / D of H_k per level (constant Abar)
@@ -206,7 +211,41 @@ DstPlan<T> dst_plan(const pt_problem* p) {
   d.logN = p->logN;
   d.tw = (const T*)p->dst_tw;
   d.pre = (const T*)p->dst_pre;
+  d.M = p->blueM;
+  d.logM = p->blueLogM;
+  d.chirp = (const T*)p->blue_chirp;
+  d.gfwd = (const T*)p->blue_gfwd;
+  d.ginv = (const T*)p->blue_ginv;
+  d.twM = (const T*)p->blue_tw;
   return d;
+}
+
+// In-place radix-2 FFT (sign -1) of n = 2^k complex values on the host, for the Bluestein
+// filter spectra (computed once per problem).
+void host_fft(std::vector<double>& re, std::vector<double>& im) {
+  const size_t n = re.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      std::swap(re[i], re[j]);
+      std::swap(im[i], im[j]);
+    }
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const double ang = -2.0 * M_PI / (double)len;
+    for (size_t i = 0; i < n; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const double wr = std::cos(ang * k), wi = std::sin(ang * k);
+        const size_t a = i + k, b = i + k + len / 2;
+        const double xr = re[b] * wr - im[b] * wi, xi = re[b] * wi + im[b] * wr;
+        re[b] = re[a] - xr;
+        im[b] = im[a] - xi;
+        re[a] += xr;
+        im[a] += xi;
+      }
+  }
 }
 
 // A~^-1 applied to rhs b (precision T, fine padded) -> out (mode 0 write T, mode 1 += into FP64)
@@ -315,7 +354,12 @@ pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff
       return fail(PT_EINVAL, "n + 1 must be a power of two >= 2");
   }
   if (grid->n[0] > 32767) return fail(PT_EINVAL, "n too large");
-  if (N_t < 1 || !is_pow2(N_t) || N_t > 8192) return fail(PT_EINVAL, "N_t must be a power of two in [1, 8192]");
+  if (N_t < 1 || N_t > 8192) return fail(PT_EINVAL, "N_t must be in [1, 8192]");
+  if (!is_pow2(N_t)) {
+    const int fp64 = !o || o->precision == PT_PREC_FP64;
+    if (N_t > (fp64 ? 2048 : 4096))
+      return fail(PT_EINVAL, "N_t that is not a power of two must be <= 2048 (FP64) or 4096 (mixed)");
+  }
   if (!(T > 0.0) || !std::isfinite(T)) return fail(PT_EINVAL, "T must be positive");
   if (!std::isfinite(coeff->a0) || !std::isfinite(coeff->c)) return fail(PT_EINVAL, "non-finite coefficient");
   if (std::fabs(coeff->c) >= coeff->a0) return fail(PT_EINVAL, "need |c| < a0 so that a > 0");
@@ -416,6 +460,49 @@ pt_status setup_precision(pt_problem* p) {
   if (!(p->dst_pre = alloc_bytes(p, sizeof(T) * pre.size(), &st))) return st;
   if ((st = upload<T>(p, p->dst_tw, tw)) != PT_OK) return st;
   if ((st = upload<T>(p, p->dst_pre, pre)) != PT_OK) return st;
+  if (!is_pow2(p->N)) {
+    // Bluestein: chirp c_m = e^{i pi m^2 / N} (phase reduced mod 2N), filters g with g_m = g_{M-m}
+    // = c_m (e^{-} DFT) or conj(c_m) (e^{+} DFT), their M-point spectra in bit-reversed order / M
+    const int N = p->N, M = p->blueM, logM = p->blueLogM;
+    std::vector<double> chirp(2 * N), twm(2 * (M / 2)), gf(2 * M), gi(2 * M);
+    for (int m = 0; m < N; ++m) {
+      const long long q = ((long long)m * m) % (2LL * N);
+      chirp[2 * m] = std::cos(M_PI * (double)q / N);
+      chirp[2 * m + 1] = std::sin(M_PI * (double)q / N);
+    }
+    for (int k = 0; k < M / 2; ++k) {
+      twm[2 * k] = std::cos(2.0 * M_PI * k / M);
+      twm[2 * k + 1] = std::sin(2.0 * M_PI * k / M);
+    }
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      std::vector<double> re(M, 0.0), im(M, 0.0);
+      for (int m = 0; m < N; ++m) {
+        const double cr = chirp[2 * m], ci = sgn == 0 ? chirp[2 * m + 1] : -chirp[2 * m + 1];
+        re[m] = cr;
+        im[m] = ci;
+        if (m > 0) {
+          re[M - m] = cr;
+          im[M - m] = ci;
+        }
+      }
+      host_fft(re, im);
+      std::vector<double>& g = sgn == 0 ? gf : gi;
+      for (int j = 0; j < M; ++j) {
+        int r = 0;
+        for (int b = 0; b < logM; ++b) r |= ((j >> b) & 1) << (logM - 1 - b);
+        g[2 * j] = re[r] / M;
+        g[2 * j + 1] = im[r] / M;
+      }
+    }
+    if (!(p->blue_chirp = alloc_bytes(p, sizeof(T) * chirp.size(), &st))) return st;
+    if (!(p->blue_tw = alloc_bytes(p, sizeof(T) * twm.size(), &st))) return st;
+    if (!(p->blue_gfwd = alloc_bytes(p, sizeof(T) * gf.size(), &st))) return st;
+    if (!(p->blue_ginv = alloc_bytes(p, sizeof(T) * gi.size(), &st))) return st;
+    if ((st = upload<T>(p, p->blue_chirp, chirp)) != PT_OK) return st;
+    if ((st = upload<T>(p, p->blue_tw, twm)) != PT_OK) return st;
+    if ((st = upload<T>(p, p->blue_gfwd, gf)) != PT_OK) return st;
+    if ((st = upload<T>(p, p->blue_ginv, gi)) != PT_OK) return st;
+  }
   return PT_OK;
 }
 
@@ -452,6 +539,10 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   p->n = grid->n[0];
   p->N = N_t;
   p->logN = ilog2(N_t);
+  if (!is_pow2(N_t)) {
+    p->blueLogM = ilog2(2LL * N_t - 1);
+    p->blueM = 1 << p->blueLogM;
+  }
   p->T = T;
   p->tau = T / N_t;
   p->coeff = *coeff;

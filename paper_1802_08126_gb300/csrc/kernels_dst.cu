@@ -52,20 +52,21 @@ __device__ __forceinline__ int bitrev(int v, int logN) {
   return logN == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - logN));
 }
 
-// radix-2 DIF stages over C columns of length N (row stride N+1); sgn = +1 inverse, -1 forward
+// radix-2 decimation-in-frequency stages over C columns of length `len` (column stride L):
+// natural order in, bit-reversed order out.  tw[k] = e^{2 pi i k / len}; sgn = +1 or -1.
 template <typename T, typename T2>
-__device__ __forceinline__ void dif_fft(T2* buf, int C, int N, int logN, const T2* __restrict__ tw,
-                                        T sgn) {
-  const int half = N >> 1;
-  for (int s = 0; s < logN; ++s) {
+__device__ __forceinline__ void dif_fft(T2* buf, int C, int L, int len, int loglen,
+                                        const T2* __restrict__ tw, T sgn) {
+  const int half = len >> 1;
+  for (int s = 0; s < loglen; ++s) {
     const int h = half >> s;  // span
-    const int tstep = 1 << s; // twiddle index stride: N / (2h)
+    const int tstep = 1 << s; // twiddle index stride: len / (2h)
     for (int idx = threadIdx.x; idx < C * half; idx += blockDim.x) {
       const int c = idx / half;
       const int b = idx - c * half;
       const int j = b & (h - 1);
-      const int i = ((b >> (logN - 1 - s)) << (logN - s)) + j;  // (b / h) * 2h + j
-      T2* col = buf + (size_t)c * (N + 1);
+      const int i = ((b >> (loglen - 1 - s)) << (loglen - s)) + j;  // (b / h) * 2h + j
+      T2* col = buf + (size_t)c * L;
       const T2 a = col[i];
       const T2 bb = col[i + h];
       const T2 w = tw[j * tstep];
@@ -80,12 +81,107 @@ __device__ __forceinline__ void dif_fft(T2* buf, int C, int N, int logN, const T
   }
 }
 
-template <typename T>
-__global__ void k_dst_forward(T* x, long long S, ColGeom cg, int N, int logN, int C,
-                              const typename Vec2<T>::type* __restrict__ tw,
-                              const typename Vec2<T>::type* __restrict__ pre, const int* done) {
+// radix-2 decimation-in-time stages: bit-reversed order in, natural order out.
+template <typename T, typename T2>
+__device__ __forceinline__ void dit_fft(T2* buf, int C, int L, int len, int loglen,
+                                        const T2* __restrict__ tw, T sgn) {
+  const int half = len >> 1;
+  for (int s = 0; s < loglen; ++s) {
+    const int h = 1 << s;
+    for (int idx = threadIdx.x; idx < C * half; idx += blockDim.x) {
+      const int c = idx / half;
+      const int b = idx - c * half;
+      const int j = b & (h - 1);
+      const int i = ((b >> s) << (s + 1)) + j;
+      T2* col = buf + (size_t)c * L;
+      const T2 w = tw[j << (loglen - 1 - s)];
+      const T wr = w.x, wi = sgn * w.y;
+      const T2 a = col[i];
+      const T2 b0 = col[i + h];
+      const T br = b0.x * wr - b0.y * wi, bi = b0.x * wi + b0.y * wr;
+      col[i].x = a.x + br;
+      col[i].y = a.y + bi;
+      col[i + h].x = a.x - br;
+      col[i + h].y = a.y - bi;
+    }
+    __syncthreads();
+  }
+}
+
+// N-point DFT X_k = sum_n x_n e^{sgn 2 pi i n k / N} of C columns for any N (Bluestein's
+// chirp-z): with c_m = e^{i pi m^2 / N} and w = conj(c) (sgn < 0) or c (sgn > 0),
+// X_k = w_k sum_n (x_n w_n) conj(w)_{k-n}, the convolution done by two M-point FFTs
+// (M a power of two >= 2N - 1) and the precomputed spectrum of the chirp, stored in
+// bit-reversed order and divided by M.  In and out in natural order, columns of stride L.
+template <typename T, typename T2>
+__device__ __forceinline__ void bluestein(T2* buf, int C, int L, const DstPlan<T>& p, T sgn) {
+  const T2* chirp = (const T2*)p.chirp;
+  const T2* filt = (const T2*)(sgn < (T)0 ? p.gfwd : p.ginv);
+  const T2* twM = (const T2*)p.twM;
+  for (int idx = threadIdx.x; idx < C * p.M; idx += blockDim.x) {
+    const int c = idx / p.M, m = idx - c * p.M;
+    T2* col = buf + (size_t)c * L;
+    T2 v;
+    if (m < p.N) {
+      const T2 x = col[m];
+      const T2 w = chirp[m];
+      const T wi = sgn < (T)0 ? -w.y : w.y;
+      v.x = x.x * w.x - x.y * wi;
+      v.y = x.x * wi + x.y * w.x;
+    } else {
+      v.x = (T)0;
+      v.y = (T)0;
+    }
+    col[m] = v;
+  }
+  __syncthreads();
+  dif_fft<T, T2>(buf, C, L, p.M, p.logM, twM, (T)-1);
+  for (int idx = threadIdx.x; idx < C * p.M; idx += blockDim.x) {
+    const int c = idx / p.M, m = idx - c * p.M;
+    T2* col = buf + (size_t)c * L;
+    const T2 x = col[m], g = filt[m];
+    T2 v;
+    v.x = x.x * g.x - x.y * g.y;
+    v.y = x.x * g.y + x.y * g.x;
+    col[m] = v;
+  }
+  __syncthreads();
+  dit_fft<T, T2>(buf, C, L, p.M, p.logM, twM, (T)1);
+  for (int idx = threadIdx.x; idx < C * p.N; idx += blockDim.x) {
+    const int c = idx / p.N, k = idx - c * p.N;
+    T2* col = buf + (size_t)c * L;
+    const T2 x = col[k];
+    const T2 w = chirp[k];
+    const T wi = sgn < (T)0 ? -w.y : w.y;
+    T2 v;
+    v.x = x.x * w.x - x.y * wi;
+    v.y = x.x * wi + x.y * w.x;
+    col[k] = v;
+  }
+  __syncthreads();
+}
+
+// the N-point transform of the C columns; returns through `slot` where output k lives
+template <typename T, typename T2, bool BLUE>
+__device__ __forceinline__ void fft_any(T2* buf, int C, int L, const DstPlan<T>& p, T sgn) {
+  if (BLUE)
+    bluestein<T, T2>(buf, C, L, p, sgn);
+  else
+    dif_fft<T, T2>(buf, C, L, p.N, p.logN, (const T2*)p.tw, sgn);
+}
+
+template <bool BLUE>
+__device__ __forceinline__ int out_slot(int k, int logN) {
+  return BLUE ? k : bitrev(k, logN);
+}
+
+template <typename T, bool BLUE>
+__global__ void k_dst_forward(T* x, long long S, ColGeom cg, DstPlan<T> plan, int C, const int* done) {
   using T2 = typename Vec2<T>::type;
   if (stop_requested(done)) return;
+  const int N = plan.N, logN = plan.logN;
+  const int L = BLUE ? plan.M + 1 : N + 1;  // column stride in shared memory
+  const T2* __restrict__ pre = (const T2*)plan.pre;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* buf = (T2*)smem_raw;
   const long long c0 = (long long)blockIdx.x * 2 * C;
@@ -99,7 +195,7 @@ __global__ void k_dst_forward(T* x, long long S, ColGeom cg, int N, int logN, in
       v.x *= (T)2;
       v.y *= (T)2;
     }
-    buf[(size_t)c * (N + 1) + m] = v;
+    buf[(size_t)c * L + m] = v;
   }
   __syncthreads();
   // pre-twiddle in pairs (m, N-m):  V[m] = e^{i pi m/(2N)} (w_m - i w_{N-m});  Z = V_a + i V_b
@@ -109,7 +205,7 @@ __global__ void k_dst_forward(T* x, long long S, ColGeom cg, int N, int logN, in
     const int m = idx - c * halfp;
     if (m == 0 || N == 1) continue;
     const int q = N - m;
-    T2* col = buf + (size_t)c * (N + 1);
+    T2* col = buf + (size_t)c * L;
     const T2 A = col[m], Bq = col[q];
     const T2 em = pre[m], eq = pre[q];
     // column a: w_a = A.x (at m), Bq.x (at q); column b: A.y, Bq.y
@@ -129,13 +225,13 @@ __global__ void k_dst_forward(T* x, long long S, ColGeom cg, int N, int logN, in
     col[m] = zm;
   }
   __syncthreads();
-  dif_fft<T, T2>(buf, C, N, logN, tw, (T)1);
-  // output: rhat_{j+1} = (-1)^j C3_j / 2, C3_{2i} = v_i, C3_{2i+1} = v_{N-1-i}; v_i at slot bitrev(i)
+  fft_any<T, T2, BLUE>(buf, C, L, plan, (T)1);
+  // output: rhat_{j+1} = (-1)^j C3_j / 2, C3_{2i} = v_i, C3_{2i+1} = v_{N-1-i}
   for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
     const int c = idx % C;
     const int j = idx / C;
     const int vi = (j & 1) ? (N - 1 - (j >> 1)) : (j >> 1);
-    T2 v = buf[(size_t)c * (N + 1) + bitrev(vi, logN)];
+    T2 v = buf[(size_t)c * L + out_slot<BLUE>(vi, logN)];
     const T sc = (j & 1) ? (T)-0.5 : (T)0.5;
     v.x = ghost_col(cg, c0 + 2 * c) ? (T)0 : v.x * sc;
     v.y = ghost_col(cg, c0 + 2 * c + 1) ? (T)0 : v.y * sc;
@@ -143,12 +239,14 @@ __global__ void k_dst_forward(T* x, long long S, ColGeom cg, int N, int logN, in
   }
 }
 
-template <typename T>
+template <typename T, bool BLUE>
 __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, double omega, long long S,
-                              ColGeom cg, int N, int logN, int C, const typename Vec2<T>::type* __restrict__ tw,
-                              const typename Vec2<T>::type* __restrict__ pre, const int* done) {
+                              ColGeom cg, DstPlan<T> plan, int C, const int* done) {
   using T2 = typename Vec2<T>::type;
   if (stop_requested(done)) return;
+  const int N = plan.N, logN = plan.logN;
+  const int L = BLUE ? plan.M + 1 : N + 1;
+  const T2* __restrict__ pre = (const T2*)plan.pre;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* buf = (T2*)smem_raw;
   const long long c0 = (long long)blockIdx.x * 2 * C;
@@ -165,10 +263,10 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
     } else {
       s = j >> 1;
     }
-    buf[(size_t)c * (N + 1) + s] = v;
+    buf[(size_t)c * L + s] = v;
   }
   __syncthreads();
-  dif_fft<T, T2>(buf, C, N, logN, tw, (T)-1);
+  fft_any<T, T2, BLUE>(buf, C, L, plan, (T)-1);
   // post: V_a[m] = (C_m + conj C_{N-m})/2, V_b[m] = (C_m - conj C_{N-m})/(2i);
   //       X[m] = Re(e^{-i pi m/(2N)} V[m]);  u_{N-m} = X[m]  (time slot N-1-m)
   const int halfp = (N >> 1) + 1;
@@ -177,10 +275,10 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
     const int m = idx / C;
     if (N == 1 && m > 0) continue;
     const bool ga = ghost_col(cg, c0 + 2 * c), gb = ghost_col(cg, c0 + 2 * c + 1);
-    const int q = (N - m) & (N - 1);
-    const T2* col = buf + (size_t)c * (N + 1);
-    const T2 Cm = col[bitrev(m, logN)];
-    const T2 Cq = col[bitrev(q, logN)];
+    const int q = m == 0 ? 0 : N - m;
+    const T2* col = buf + (size_t)c * L;
+    const T2 Cm = col[out_slot<BLUE>(m, logN)];
+    const T2 Cq = col[out_slot<BLUE>(q, logN)];
     // V_a[m] = ((Cm.x + Cq.x)/2, (Cm.y - Cq.y)/2); V_b[m] = ((Cm.y + Cq.y)/2, (Cq.x - Cm.x)/2)
     const T2 em = pre[m];
     const T var = (T)0.5 * (Cm.x + Cq.x), vai = (T)0.5 * (Cm.y - Cq.y);
@@ -225,9 +323,9 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
 }
 
 template <typename T>
-int dst_cols(int N, long long S) {
-  // complex columns per CTA: a power of two, <= 16, using at most ~100 KB of shared memory
-  const long long bytes = (long long)(N + 1) * 2 * sizeof(T);
+int dst_cols(int L, long long S) {
+  // complex columns (stride L) per CTA: a power of two, <= 16, using at most ~100 KB of shared memory
+  const long long bytes = (long long)L * 2 * sizeof(T);
   long long C = (100 * 1024) / bytes;
   if (C < 1) C = 1;
   if (C > 16) C = 16;
@@ -242,14 +340,21 @@ int dst_cols(int N, long long S) {
 }  // namespace
 
 template <typename T>
+int plan_stride(const DstPlan<T>& plan) {
+  return plan.M > 0 ? plan.M + 1 : plan.N + 1;
+}
+
+template <typename T>
 void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> plan, const int* done,
                         cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
-  const int C = dst_cols<T>(plan.N, S);
-  const size_t smem = (size_t)C * (plan.N + 1) * sizeof(T2);
+  const int L = plan_stride(plan);
+  const int C = dst_cols<T>(L, S);
+  const size_t smem = (size_t)C * L * sizeof(T2);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_dst_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dst_forward<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dst_forward<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const int blocks = (int)(S / (2 * C));
@@ -257,19 +362,23 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
   double interior = plan.N;
   for (int d = 0; d < dim; ++d) interior *= n;
   LaunchScope ls("dst_forward", st, 2.0 * sizeof(T) * interior);
-  k_dst_forward<T><<<blocks, kThreads, smem, st>>>(x, S, cg, plan.N, plan.logN, C, (const T2*)plan.tw,
-                                                   (const T2*)plan.pre, done);
+  if (plan.M > 0)
+    k_dst_forward<T, true><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
+  else
+    k_dst_forward<T, false><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
 }
 
 template <typename T>
 void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
                         int logP, DstPlan<T> plan, const int* done, cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
-  const int C = dst_cols<T>(plan.N, S);
-  const size_t smem = (size_t)C * (plan.N + 1) * sizeof(T2);
+  const int L = plan_stride(plan);
+  const int C = dst_cols<T>(L, S);
+  const size_t smem = (size_t)C * L * sizeof(T2);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_dst_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dst_inverse<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dst_inverse<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const int blocks = (int)(S / (2 * C));
@@ -277,28 +386,29 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
   double interior = plan.N;
   for (int d = 0; d < dim; ++d) interior *= n;
   LaunchScope ls("dst_inverse", st, (sizeof(T) + (mode == 1 ? 16.0 : (double)sizeof(T))) * interior);
-  k_dst_inverse<T><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan.N, plan.logN, C,
-                                                   (const T2*)plan.tw, (const T2*)plan.pre, done);
+  if (plan.M > 0)
+    k_dst_inverse<T, true><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);
+  else
+    k_dst_inverse<T, false><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);
 }
 
 // Forward transform of `ncols` packed columns held at pitch S (S a multiple of 32, columns
 // ncols..S-1 are padding whose results are discarded).  It records no CUDA events (only the
-// launch count), so it allocates nothing on any path.
+// launch count), so it allocates nothing on any path.  N must be a power of two.
 void launch_dst_forward_plain(double* x, long long S, int ncols, DstPlan<double> plan, cudaStream_t st) {
-  const int C = dst_cols<double>(plan.N, S);
-  const size_t smem = (size_t)C * (plan.N + 1) * sizeof(double2);
+  const int L = plan.N + 1;
+  const int C = dst_cols<double>(L, S);
+  const size_t smem = (size_t)C * L * sizeof(double2);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_dst_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dst_forward<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   int logP = 0;
   while ((1LL << logP) <= S) ++logP;  // pitch above every column index: only column ncols is "ghost"
   const ColGeom cg{1, ncols, logP};
   note_launch();
-  k_dst_forward<double><<<(int)(S / (2 * C)), kThreads, smem, st>>>(x, S, cg, plan.N, plan.logN, C,
-                                                                   (const double2*)plan.tw,
-                                                                   (const double2*)plan.pre, nullptr);
+  k_dst_forward<double, false><<<(int)(S / (2 * C)), kThreads, smem, st>>>(x, S, cg, plan, C, nullptr);
 }
 
 template void launch_dst_forward<float>(float*, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);

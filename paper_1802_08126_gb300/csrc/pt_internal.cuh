@@ -172,8 +172,14 @@ void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T
 template <typename T>
 struct DstPlan {
   int N, logN;
-  const T* tw;    // [N/2] (cos, sin)(2 pi k / N) interleaved
+  const T* tw;    // [N/2] (cos, sin)(2 pi k / N) interleaved (N a power of two)
   const T* pre;   // [N]   (cos, sin)(pi m / (2N)) interleaved
+  // Bluestein tables, used when M > 0 (N not a power of two): M = 2^logM >= 2N - 1
+  int M = 0, logM = 0;
+  const T* chirp = nullptr;  // [N] e^{i pi m^2 / N}
+  const T* gfwd = nullptr;   // [M] FFT_M of the chirp filter for the e^{-} transform, bit-reversed, / M
+  const T* ginv = nullptr;   // [M] same for the e^{+} transform
+  const T* twM = nullptr;    // [M/2] e^{2 pi i k / M}
 };
 
 // in-place forward transform: x_k <- sum_n x_n sin((2k-1) n pi/(2N)) for every interior column

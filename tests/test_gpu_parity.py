@@ -42,6 +42,36 @@ def rel_err(a, b):
 
 SMALL = [S.heat1d_mms(15, 16), S.heat2d_uniform(15, 8), S.heat2d_uniform(31, 4),
          S.heat3d_bumps(7, 4), S.heat2d_uniform(3, 1), S.heat1d_mms(1, 2)]
+# N not a power of two (Bluestein path of the temporal transform), including primes
+GENERAL_N = [S.heat2d_uniform(7, 3), S.heat2d_uniform(15, 12), S.heat1d_mms(15, 97),
+             S.heat2d_uniform(7, 1000), S.heat1d_mms(7, 2047)]
+
+
+@pytest.mark.parametrize("prob", GENERAL_N, ids=lambda p: p.name)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dst_general_N_matches_sine_sums(prob, precision):
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    rng = np.random.default_rng(7)
+    r = rng.standard_normal((prob.N, prob.ns))
+    with make(prob, precision) as P:
+        out = torch.empty_like(dev(r))
+        P.dst_forward(dev(r), out)
+        ref = st.dst_forward(r)
+        assert np.abs(host(out) - ref).max() <= tol * np.abs(ref).max() * np.log2(2 * prob.N)
+        P.dst_inverse(dev(r), out)
+        ref = st.dst_inverse(r)
+        assert np.abs(host(out) - ref).max() <= tol * np.abs(ref).max() * np.log2(2 * prob.N)
+
+
+@pytest.mark.parametrize("prob", [S.heat2d_uniform(15, 24), S.heat1d_mms(31, 37)], ids=lambda p: p.name)
+def test_general_N_solve_matches_oracle(prob):
+    f, u0 = S.source(prob), S.initial(prob)
+    with make(prob, omega=0.5) as P:
+        u = np.zeros((prob.N, prob.ns))
+        stt, it, hist = P.solve(1e-12, 1000, u_out=u)
+    assert stt == 0
+    ref = oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0)
+    assert rel_err(u, ref) <= FP64_TOL
 
 
 @pytest.mark.parametrize("prob", SMALL, ids=lambda p: p.name)
