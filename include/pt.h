@@ -83,7 +83,17 @@ typedef struct {
   double jacobi_weight;  /* weighted-Jacobi smoothing weight; <= 0 selects 2/3, 4/5, 6/7 by dim */
   void* stream;          /* cudaStream_t for all work of this problem; NULL = default stream */
   int check_every;       /* iterations between host polls of the device convergence flag; 0 = auto */
-  int reserved[7];       /* must be zero */
+  int autotune;          /* 1: before the first solve, time the candidate launch configurations
+                            (temporal-transform tile width, multigrid coarse-level split) and keep
+                            the fastest; results are cached per (dim, n, N_t, precision, solver) in
+                            the process and, when the environment variable PT_TUNE_CACHE names a
+                            file, in that JSON file.  0: defaults. */
+  int dst_cols;          /* complex columns per CTA of the temporal transform; 0 = automatic */
+  int coarse_elems;      /* multigrid levels with at most this many points per slice run in one
+                            CTA per slice; 0 = 1024; else a power of two in [64, 4096] */
+  int no_graphs;         /* 1: launch kernels one by one instead of replaying a captured CUDA
+                            graph of the iteration (kernel timing via pt_profile_* also does) */
+  int reserved[3];       /* must be zero */
 } pt_options;
 
 typedef struct pt_problem pt_problem; /* opaque, library-owned */
@@ -112,6 +122,18 @@ pt_status pt_problem_set_rhs(pt_problem* p, const double* f, int f_on_device, co
  * Returns PT_OK, PT_ENOTCONV (u_out still written) or PT_EDIVERGED, or an error. */
 pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_out_on_device,
                    double* res_hist, int* iters);
+
+/* Solve several problems together: one CUDA graph per launch holds one Uzawa iteration of every
+ * unfinished problem (each problem's captured iteration as a child graph), so problems of any
+ * grid and N_t share each launch; a problem that has converged stops doing work on the device
+ * (its kernels see its done flag) and is dropped from the graph when it is rebuilt.
+ *   ps[count]: distinct problems on the current device (each keeps its own data and options).
+ *   tol[count], max_it[count]: per-problem stopping rules as in pt_solve.
+ *   iters[count], status[count]: outputs (may be NULL); status[i] is PT_OK, PT_ENOTCONV or
+ *   PT_EDIVERGED.  Solutions stay on the device: read them with pt_problem_get_state.
+ * Returns PT_OK when every problem finished (whatever its status), or an error. */
+pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const int* max_it, int* iters,
+                         pt_status* status);
 
 /* Copy the current iterates u_j and p_j (packed [N_t][n_s], FP64) of the problem's last solve.
  * The pair (u_j, p_j) is the complete state of the stationary Uzawa iteration (a checkpoint).

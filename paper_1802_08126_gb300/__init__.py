@@ -20,7 +20,7 @@ from . import _lib
 from ._lib import PT_EDIVERGED, PT_ENOTCONV, PT_OK  # noqa: F401
 
 __all__ = ["Problem", "PtError", "launch_count", "status_name", "profile_enable", "profile_reset",
-           "profile_totals", "dst_forward_noalloc"]
+           "profile_totals", "dst_forward_noalloc", "solve_batch"]
 
 
 class PtError(RuntimeError):
@@ -66,6 +66,21 @@ def profile_totals() -> dict:
             break
         out[name.value.decode()] = {"ms": ms.value, "bytes": b.value, "flops": fl.value, "launches": n.value}
     return out
+
+
+def solve_batch(problems, tol, max_it):
+    """Solve several problems together (pt_solve_batch); returns (iters, statuses) lists.
+    ``tol`` and ``max_it`` are scalars or per-problem sequences."""
+    count = len(problems)
+    tols = [float(tol)] * count if np.isscalar(tol) else [float(t) for t in tol]
+    mits = [int(max_it)] * count if np.isscalar(max_it) else [int(m) for m in max_it]
+    hs = (ctypes.c_void_p * count)(*[p.handle.value for p in problems])
+    t = (ctypes.c_double * count)(*tols)
+    m = (ctypes.c_int * count)(*mits)
+    it = (ctypes.c_int * count)()
+    stt = (ctypes.c_int * count)()
+    _check(_lib.load().pt_solve_batch(hs, count, t, m, it, stt))
+    return list(it), list(stt)
 
 
 def dst_forward_noalloc(r, out, stream: Optional[int] = None):
@@ -117,7 +132,9 @@ class Problem:
 
     def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff, f, u0=None,
                  precision: str = "fp64", omega: float = 0.0, solver: str = "mg",
-                 stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0):
+                 stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0,
+                 autotune: bool = False, dst_cols: int = 0, coarse_elems: int = 0,
+                 graphs: bool = True):
         L = _lib.load()
         self._lib = L
         self.dim, self.n, self.N, self.T = dim, list(n)[:dim], N, float(T)
@@ -134,6 +151,10 @@ class Problem:
         opts.jacobi_weight = float(jacobi_weight)
         opts.stream = stream
         opts.check_every = int(check_every)
+        opts.autotune = 1 if autotune else 0
+        opts.dst_cols = int(dst_cols)
+        opts.coarse_elems = int(coarse_elems)
+        opts.no_graphs = 0 if graphs else 1
         self._opts = opts
         fp, fdev = _ptr(f)
         up, udev = _ptr(u0)

@@ -16,7 +16,7 @@ EXPORTED = (
     "pt_problem_create", "pt_problem_set_rhs", "pt_solve", "pt_problem_destroy", "pt_last_error",
     "pt_status_string", "pt_apply_B", "pt_dst_forward", "pt_dst_inverse", "pt_precond_A",
     "pt_precond_H", "pt_kernel_launch_count", "pt_problem_get_state", "pt_profile_enable",
-    "pt_profile_reset", "pt_profile_get", "pt_dst_forward_noalloc",
+    "pt_profile_reset", "pt_profile_get", "pt_dst_forward_noalloc", "pt_solve_batch",
 )
 
 
@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("omega", ctypes.c_double),
                 ("spatial_solver", ctypes.c_int), ("n_vcycles", ctypes.c_int),
                 ("jacobi_weight", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("check_every", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("check_every", ctypes.c_int), ("autotune", ctypes.c_int), ("dst_cols", ctypes.c_int),
+                ("coarse_elems", ctypes.c_int), ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lock = threading.Lock()
@@ -76,6 +77,8 @@ def load(path: str = LIB_PATH):
         L.pt_profile_reset.restype = None
         L.pt_profile_get.argtypes = [i, ctypes.c_char_p, i, dp, dp, dp, ctypes.POINTER(ctypes.c_ulonglong)]
         L.pt_profile_get.restype = i
+        L.pt_solve_batch.argtypes = [ctypes.POINTER(vp), i, dp, ip, ip, ip]
+        L.pt_solve_batch.restype = i
         L.pt_dst_forward_noalloc.argtypes = [vp, vp, i, ctypes.c_longlong, vp]
         L.pt_dst_forward_noalloc.restype = i
         L.pt_kernel_launch_count.argtypes = []

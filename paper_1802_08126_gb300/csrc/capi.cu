@@ -3,10 +3,16 @@
 // translation units; this file owns device memory, tables and the launch sequence.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -97,6 +103,19 @@ struct pt_problem {
   double* tmpB = nullptr;
   SolveState* host_state = nullptr;             // pinned
   size_t bytes = 0;
+  int dstC = 0;                                 // temporal-transform columns per CTA (0 = auto)
+  int coarse_elems = kCoarseMaxElems;           // one-CTA coarse-level threshold
+  int lc_min = 0;                               // smallest lc whose buffers exist (largest threshold)
+  int lc_max = 0;                               // largest lc whose buffers exist (smallest threshold)
+  bool tuned = false;
+  // captured iteration graph
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_iters = 0;
+  unsigned long long graph_kernels = 0;
+  double* graph_hist = nullptr;
+  int graph_dstC = -1, graph_lc = -1;
 };
 
 namespace {
@@ -217,6 +236,7 @@ DstPlan<T> dst_plan(const pt_problem* p) {
   d.gfwd = (const T*)p->blue_gfwd;
   d.ginv = (const T*)p->blue_ginv;
   d.twM = (const T*)p->blue_tw;
+  d.C = p->dstC;
   return d;
 }
 
@@ -290,43 +310,101 @@ void block_solve(pt_problem* p, const int* done) {
   apply_Hk_solve<T>(p, W1, W2, done);
 }
 
+// One Uzawa iteration (§3, eq. 3.1) on the problem's stream; every kernel returns at once when
+// the device done flag is set, and the finalize kernel advances the iteration index itself, so
+// the same launch sequence serves every iteration (and can be captured into a graph).
 template <typename T>
-pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* res_hist) {
-  const long long total = p->lev[0].S * p->N;
+void enqueue_iteration(pt_problem* p) {
   const int* done = &p->state->done;
-  // fresh start: u = p = 0, ||F||^2
-  PT_CUDA(cudaMemsetAsync(p->u, 0, sizeof(double) * total, p->st));
-  PT_CUDA(cudaMemsetAsync(p->p, 0, sizeof(double) * total, p->st));
-  launch_norm2_partials(p->F, total, p->partials, p->st);
-  launch_finalize_fnorm(p->partials, p->state, p->st);
-  PT_CHECK_LAUNCH();
   const StencilGeom<double> g = geom<double>(p, 0);
-  int check = p->opt.check_every;
-  if (check <= 0) check = total >= (1LL << 22) ? 1 : 8;
   T* W1 = (T*)p->W1;
   T* W2 = (T*)p->W2;
   const DstPlan<T> dp = dst_plan<T>(p);
-  for (int j = 0; j <= max_it; ++j) {
-    launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, p->tau, p->N, done, p->st);
-    apply_precond_A<T>(p, W1, p->p, 1, 1, done);
-    launch_resid_u<T>(p->u, p->p, p->F, W1, p->partials, g, p->cth_d, p->tau, p->N, done, p->st);
-    launch_finalize_residual(p->partials, p->state, p->hist, j, tol, max_it, p->st);
-    if (j < max_it) {
-      launch_dst_forward<T>(W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
-      block_solve<T>(p, done);
-      launch_dst_inverse<T>(W2, p->u, 1, p->omega, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done,
-                            p->st);
-    }
-    PT_CHECK_LAUNCH();
-    if ((j + 1) % check == 0 || j == max_it) {
-      PT_CUDA(cudaMemcpyAsync(p->host_state, p->state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->st));
-      PT_CUDA(cudaStreamSynchronize(p->st));
-      if (p->host_state->done) break;
-    }
+  launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, p->tau, p->N, done, p->st);
+  apply_precond_A<T>(p, W1, p->p, 1, 1, done);
+  launch_resid_u<T>(p->u, p->p, p->F, W1, p->partials, g, p->cth_d, p->tau, p->N, done, p->st);
+  launch_finalize_residual(p->partials, p->state, p->hist, p->st);
+  launch_dst_forward<T>(W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
+  block_solve<T>(p, done);
+  launch_dst_inverse<T>(W2, p->u, 1, p->omega, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
+}
+
+void enqueue_iteration_any(pt_problem* p) {
+  if (p->mixed)
+    enqueue_iteration<float>(p);
+  else
+    enqueue_iteration<double>(p);
+}
+
+// start of a solve: u = p = 0, ||F||^2, counters, tolerance and limit
+pt_status enqueue_reset(pt_problem* p, double tol, int max_it) {
+  const long long total = p->lev[0].S * p->N;
+  PT_CUDA(cudaMemsetAsync(p->u, 0, sizeof(double) * total, p->st));
+  PT_CUDA(cudaMemsetAsync(p->p, 0, sizeof(double) * total, p->st));
+  launch_norm2_partials(p->F, total, p->partials, p->st);
+  launch_finalize_fnorm(p->partials, p->state, tol, max_it, p->st);
+  PT_CHECK_LAUNCH();
+  return PT_OK;
+}
+
+void drop_graph(pt_problem* p) {
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->graph_exec = nullptr;
+  p->graph = nullptr;
+  p->graph_iters = 0;
+}
+
+// Capture `iters` consecutive iterations into a graph (on an internal stream).
+pt_status ensure_graph(pt_problem* p, int iters) {
+  if (p->graph_exec && p->graph_iters == iters && p->graph_hist == p->hist && p->graph_dstC == p->dstC &&
+      p->graph_lc == p->lc)
+    return PT_OK;
+  drop_graph(p);
+  if (!p->cap) PT_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+  cudaStream_t saved = p->st;
+  p->st = p->cap;
+  capture_begin();
+  cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < iters; ++k) enqueue_iteration_any(p);
+    e = cudaStreamEndCapture(p->cap, &p->graph);
   }
+  p->graph_kernels = capture_end();
+  p->st = saved;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    drop_graph(p);
+    return fail(PT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  PT_CUDA(cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
+  p->graph_iters = iters;
+  p->graph_hist = p->hist;
+  p->graph_dstC = p->dstC;
+  p->graph_lc = p->lc;
+  return PT_OK;
+}
+
+pt_status ensure_hist(pt_problem* p, int max_it) {
+  if (max_it + 1 > p->hist_cap) {
+    pt_status st = PT_OK;
+    if (!(p->hist = (double*)alloc_bytes(p, sizeof(double) * (max_it + 1), &st))) return st;
+    p->hist_cap = max_it + 1;
+  }
+  return PT_OK;
+}
+
+pt_status read_state(pt_problem* p, SolveState* out) {
   PT_CUDA(cudaMemcpyAsync(p->host_state, p->state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->st));
   PT_CUDA(cudaStreamSynchronize(p->st));
-  const SolveState hs = *p->host_state;
+  *out = *p->host_state;
+  return PT_OK;
+}
+
+pt_status finish_solve(pt_problem* p, int* iters_out, double* res_hist) {
+  SolveState hs;
+  pt_status st = read_state(p, &hs);
+  if (st != PT_OK) return st;
   if (!hs.done) return fail(PT_ECUDA, "solver state not finalised");
   if (iters_out) *iters_out = hs.iters;
   if (res_hist) {
@@ -336,6 +414,159 @@ pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* r
   if (hs.status == PT_ENOTCONV) g_err = "max_it reached before tol";
   if (hs.status == PT_EDIVERGED) g_err = "residual became non-finite";
   return (pt_status)hs.status;
+}
+
+long long padded_total(const pt_problem* p) { return p->lev[0].S * p->N; }
+
+pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* res_hist) {
+  pt_status st = enqueue_reset(p, tol, max_it);
+  if (st != PT_OK) return st;
+  const long long total = padded_total(p);
+  const bool small = total < (1LL << 22);
+  int check = p->opt.check_every;
+  if (check <= 0) check = small ? 8 : 1;
+  const bool graphs = !p->opt.no_graphs && !profiling_enabled();
+  const int per_launch = graphs ? (small ? std::min(check, 8) : 1) : 1;
+  if (graphs && (st = ensure_graph(p, per_launch)) != PT_OK) return st;
+  long long launched = 0, since_poll = 0;
+  for (;;) {
+    if (graphs) {
+      PT_CUDA(cudaGraphLaunch(p->graph_exec, p->st));
+      note_launch((int)p->graph_kernels);
+    } else {
+      enqueue_iteration_any(p);
+      PT_CHECK_LAUNCH();
+    }
+    launched += per_launch;
+    since_poll += per_launch;
+    if (since_poll >= check || launched > max_it) {
+      since_poll = 0;
+      SolveState hs;
+      if ((st = read_state(p, &hs)) != PT_OK) return st;
+      if (hs.done) break;
+      if (launched > (long long)max_it + per_launch + 1) return fail(PT_ECUDA, "solver did not stop at max_it");
+    }
+  }
+  return finish_solve(p, iters_out, res_hist);
+}
+
+// ---- autotuner ------------------------------------------------------------------------
+struct TuneChoice {
+  int dstC, coarse_elems;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+std::string tune_key(const pt_problem* p) {
+  std::ostringstream k;
+  k << "d" << p->dim << "_n" << p->n << "_N" << p->N << "_" << (p->mixed ? "mixed" : "fp64") << "_"
+    << (p->exact1d ? "exact" : "mg");
+  return k.str();
+}
+
+void tune_file_load() {
+  if (g_tune_file_loaded) return;
+  g_tune_file_loaded = true;
+  const char* path = std::getenv("PT_TUNE_CACHE");
+  if (!path) return;
+  std::ifstream in(path);
+  std::string line;
+  // one entry per line: "key": [dstC, coarse_elems],
+  while (std::getline(in, line)) {
+    const size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1), b0 = line.find('['), c = line.find(',', b0),
+                 b1 = line.find(']', b0);
+    if (q0 == std::string::npos || q1 == std::string::npos || b0 == std::string::npos || c == std::string::npos ||
+        b1 == std::string::npos)
+      continue;
+    TuneChoice t;
+    t.dstC = std::atoi(line.substr(b0 + 1, c - b0 - 1).c_str());
+    t.coarse_elems = std::atoi(line.substr(c + 1, b1 - c - 1).c_str());
+    g_tune_cache[line.substr(q0 + 1, q1 - q0 - 1)] = t;
+  }
+}
+
+void tune_file_save() {
+  const char* path = std::getenv("PT_TUNE_CACHE");
+  if (!path) return;
+  std::ofstream out(path);
+  out << "{\n";
+  size_t i = 0;
+  for (auto& kv : g_tune_cache)
+    out << "  \"" << kv.first << "\": [" << kv.second.dstC << ", " << kv.second.coarse_elems << "]"
+        << (++i < g_tune_cache.size() ? "," : "") << "\n";
+  out << "}\n";
+}
+
+int lc_for(const pt_problem* p, int elems) {
+  for (int l = 0; l < p->nlev; ++l)
+    if (p->lev[l].S <= elems) return l;
+  return p->nlev - 1;
+}
+
+void apply_choice(pt_problem* p, TuneChoice t) {
+  p->dstC = t.dstC;
+  p->coarse_elems = t.coarse_elems;
+  p->lc = std::min(std::max(lc_for(p, t.coarse_elems), p->lc_min), p->lc_max);
+}
+
+// Time a few iterations of each candidate (transform tile width x coarse-level split) on the
+// problem's own data and keep the fastest.  The numbers produced do not depend on the choice
+// beyond rounding (columns are independent in the transform; the coarse split only moves levels
+// between kernels), and the solve that follows starts from zero again.
+pt_status autotune(pt_problem* p) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_file_load();
+  const std::string key = tune_key(p);
+  auto it = g_tune_cache.find(key);
+  if (it != g_tune_cache.end()) {
+    apply_choice(p, it->second);
+    p->tuned = true;
+    return PT_OK;
+  }
+  std::vector<int> cols = {0};
+  for (int c = 1; c <= 16; c *= 2) {
+    const long long L = p->blueM > 0 ? p->blueM + 1 : p->N + 1;
+    const long long bytes = (long long)c * L * 2 * (p->mixed ? 4 : 8) * 2;
+    if (p->lev[0].S % (2 * c) == 0 && bytes <= 200 * 1024 && 2 * c <= p->lev[0].S) cols.push_back(c);
+  }
+  std::vector<int> coarse = {kCoarseMaxElems};
+  if (!p->exact1d)
+    for (int e : {256, 4096})
+      if (lc_for(p, e) >= p->lc_min && lc_for(p, e) <= p->lc_max && lc_for(p, e) != lc_for(p, kCoarseMaxElems))
+        coarse.push_back(e);
+  pt_status st = ensure_hist(p, 1 << 20);
+  if (st != PT_OK) return st;
+  cudaEvent_t e0, e1;
+  PT_CUDA(cudaEventCreate(&e0));
+  PT_CUDA(cudaEventCreate(&e1));
+  TuneChoice best{0, kCoarseMaxElems};
+  float best_ms = 1e30f;
+  for (int ce : coarse) {
+    for (int c : cols) {
+      apply_choice(p, TuneChoice{c, ce});
+      if ((st = enqueue_reset(p, 0.0, 1 << 20)) != PT_OK) break;
+      enqueue_iteration_any(p);
+      PT_CUDA(cudaEventRecord(e0, p->st));
+      for (int k = 0; k < 2; ++k) enqueue_iteration_any(p);
+      PT_CUDA(cudaEventRecord(e1, p->st));
+      PT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      PT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = TuneChoice{c, ce};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PT_OK) return st;
+  apply_choice(p, best);
+  g_tune_cache[key] = best;
+  tune_file_save();
+  p->tuned = true;
+  return PT_OK;
 }
 
 bool is_pow2(long long v) { return v >= 1 && (v & (v - 1)) == 0; }
@@ -373,8 +604,12 @@ pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff
     if (o->spatial_solver == PT_SOLVER_EXACT_1D && grid->dim != 1)
       return fail(PT_EINVAL, "exact spatial solves are available in 1-D only");
     if (o->n_vcycles > 1) return fail(PT_EINVAL, "n_vcycles > 1 is not supported");
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 3; ++i)
       if (o->reserved[i] != 0) return fail(PT_EINVAL, "reserved options must be zero");
+    if (o->dst_cols != 0 && (o->dst_cols < 0 || o->dst_cols > 16 || !is_pow2(o->dst_cols)))
+      return fail(PT_EINVAL, "dst_cols must be 0 or a power of two <= 16");
+    if (o->coarse_elems != 0 && (o->coarse_elems < 64 || o->coarse_elems > 4096 || !is_pow2(o->coarse_elems)))
+      return fail(PT_EINVAL, "coarse_elems must be 0 or a power of two in [64, 4096]");
   }
   return PT_OK;
 }
@@ -389,7 +624,7 @@ pt_status setup_precision(pt_problem* p) {
   if (!p->W2) return st;
   if (!p->exact1d) {
     const bool fused = p->dim == 2;  // fused 2-D kernels keep no level-0 iterate and no residuals
-    for (int l = 0; l <= p->lc && l < p->nlev; ++l) {
+    for (int l = 0; l <= p->lc_max && l < p->nlev; ++l) {
       if (l > 0) {
         p->mg_b[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
         if (!p->mg_b[l]) return st;
@@ -398,7 +633,7 @@ pt_status setup_precision(pt_problem* p) {
         p->mg_x[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
         if (!p->mg_x[l]) return st;
       }
-      if (!fused && l < p->lc) {
+      if (!fused && l < p->lc_max) {
         p->mg_r[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
         if (!p->mg_r[l]) return st;
       }
@@ -425,7 +660,7 @@ pt_status setup_precision(pt_problem* p) {
   // Abar with a constant coefficient: its Jacobi factor w / (mu_k + 2 dim tau a0 / h^2) per level
   p->hvar = !(std::fabs(p->cthbar) <= 1e-14 * std::fabs(p->coeff.a0));
   if (!p->exact1d && p->dim == 2 && !p->hvar) {
-    for (int l = 0; l < p->lc; ++l) {
+    for (int l = 0; l < p->lc_max; ++l) {
       std::vector<double> dv(p->N);
       const double a0s = p->tau * p->coeff.a0 / (p->lev[l].h * p->lev[l].h);
       for (int k = 0; k < p->N; ++k) dv[k] = p->jacobi / (mu[k] + 2.0 * p->dim * a0s);
@@ -435,7 +670,7 @@ pt_status setup_precision(pt_problem* p) {
   }
   // FP64 2-D: cache w / D of every tau A_n (a division per point per smoothing step otherwise)
   if (!p->exact1d && p->dim == 2 && sizeof(T) == 8) {
-    for (int l = 0; l < p->lc; ++l) {
+    for (int l = 0; l < p->lc_max; ++l) {
       T* j = alloc_padded<T>(p, p->lev[l], p->N, &st);
       if (!j) return st;
       p->jinvA[l] = j;
@@ -567,12 +802,12 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
     L.guard = padded_guard(L, p->dim);
     ++p->nlev;
   }
-  p->lc = p->nlev - 1;
-  for (int l = 0; l < p->nlev; ++l)
-    if (p->lev[l].S <= kCoarseMaxElems) {
-      p->lc = l;
-      break;
-    }
+  p->coarse_elems = p->opt.coarse_elems > 0 ? p->opt.coarse_elems : kCoarseMaxElems;
+  p->dstC = p->opt.dst_cols;
+  p->lc = lc_for(p, p->coarse_elems);
+  // buffers cover every coarse split the autotuner may choose (thresholds 256 .. 4096 points)
+  p->lc_min = std::min(p->lc, lc_for(p, 4096));
+  p->lc_max = std::max(p->lc, lc_for(p, 256));
   p->ns = 1;
   for (int d = 0; d < p->dim; ++d) p->ns *= p->n;
   // coefficient tables (node and face values of g_d per level)
@@ -735,13 +970,10 @@ pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_o
   if (!p) return fail(PT_EINVAL, "problem is NULL");
   if (max_it < 0 || !(tol >= 0.0)) return fail(PT_EINVAL, "need max_it >= 0 and tol >= 0");
   PT_CUDA(cudaSetDevice(p->device));
-  if (max_it + 1 > p->hist_cap) {
-    pt_status st = PT_OK;
-    if (!(p->hist = (double*)alloc_bytes(p, sizeof(double) * (max_it + 1), &st))) return st;
-    p->hist_cap = max_it + 1;
-  }
-  pt_status st = p->mixed ? uzawa<float>(p, tol, max_it, iters, res_hist)
-                          : uzawa<double>(p, tol, max_it, iters, res_hist);
+  pt_status st = ensure_hist(p, max_it);
+  if (st != PT_OK) return st;
+  if (p->opt.autotune && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+  st = uzawa(p, tol, max_it, iters, res_hist);
   if (st != PT_OK && st != PT_ENOTCONV && st != PT_EDIVERGED) return st;
   if (u_out) {
     const Level& L = p->lev[0];
@@ -761,6 +993,131 @@ pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_o
     PT_CUDA(cudaStreamSynchronize(p->st));
   }
   return st;
+}
+
+pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const int* max_it, int* iters,
+                         pt_status* status) {
+  g_err.clear();
+  if (!ps || count < 1 || !tol || !max_it) return fail(PT_EINVAL, "need problems, tol and max_it");
+  int dev = -1;
+  for (int i = 0; i < count; ++i) {
+    if (!ps[i]) return fail(PT_EINVAL, "NULL problem in batch");
+    if (max_it[i] < 0 || !(tol[i] >= 0.0)) return fail(PT_EINVAL, "need max_it >= 0 and tol >= 0");
+    if (dev >= 0 && ps[i]->device != dev) return fail(PT_EINVAL, "all problems must be on one device");
+    dev = ps[i]->device;
+    for (int k = 0; k < i; ++k)
+      if (ps[k] == ps[i]) return fail(PT_EINVAL, "a problem appears twice in the batch");
+  }
+  PT_CUDA(cudaSetDevice(dev));
+  pt_status st;
+  int max_rounds = 0;
+  for (int i = 0; i < count; ++i) {
+    pt_problem* p = ps[i];
+    if ((st = ensure_hist(p, max_it[i])) != PT_OK) return st;
+    if (p->opt.autotune && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+    if ((st = enqueue_reset(p, tol[i], max_it[i])) != PT_OK) return st;
+    max_rounds = std::max(max_rounds, max_it[i] + 1);
+  }
+  for (int i = 0; i < count; ++i) PT_CUDA(cudaStreamSynchronize(ps[i]->st));
+  const bool graphs = !profiling_enabled();
+  if (graphs)
+    for (int i = 0; i < count; ++i)
+      if ((st = ensure_graph(ps[i], 1)) != PT_OK) return st;
+  // device list of the solve states and a pinned copy of their done flags
+  cudaStream_t bst = nullptr;
+  SolveState** dstates = nullptr;
+  int* ddone = nullptr;
+  int* hdone = nullptr;
+  cudaGraph_t parent = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (parent) cudaGraphDestroy(parent);
+    if (dstates) cudaFree(dstates);
+    if (ddone) cudaFree(ddone);
+    if (hdone) cudaFreeHost(hdone);
+    if (bst) cudaStreamDestroy(bst);
+  };
+#define PT_BATCH_CUDA(call)                                                          \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      cleanup();                                                                     \
+      return fail(PT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    }                                                                                \
+  } while (0)
+  PT_BATCH_CUDA(cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking));
+  std::vector<SolveState*> hstates(count);
+  for (int i = 0; i < count; ++i) hstates[i] = ps[i]->state;
+  PT_BATCH_CUDA(cudaMalloc(&dstates, sizeof(SolveState*) * count));
+  PT_BATCH_CUDA(cudaMalloc(&ddone, sizeof(int) * count));
+  PT_BATCH_CUDA(cudaMallocHost(&hdone, sizeof(int) * count));
+  PT_BATCH_CUDA(cudaMemcpyAsync(dstates, hstates.data(), sizeof(SolveState*) * count, cudaMemcpyHostToDevice, bst));
+  std::vector<int> active(count);
+  for (int i = 0; i < count; ++i) active[i] = i;
+  unsigned long long kernels_per_round = 0;
+  // one graph holding one iteration of every unfinished problem
+  auto rebuild = [&]() -> cudaError_t {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (parent) cudaGraphDestroy(parent);
+    exec = nullptr;
+    parent = nullptr;
+    kernels_per_round = 0;
+    cudaError_t e = cudaGraphCreate(&parent, 0);
+    for (size_t a = 0; e == cudaSuccess && a < active.size(); ++a) {
+      cudaGraphNode_t node;
+      e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, ps[active[a]]->graph);
+      kernels_per_round += ps[active[a]]->graph_kernels;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, parent, 0);
+    return e;
+  };
+  if (graphs) PT_BATCH_CUDA(rebuild());
+  int check = ps[0]->opt.check_every > 0 ? ps[0]->opt.check_every : 4;
+  int rounds = 0;
+  while (!active.empty()) {
+    if (graphs) {
+      PT_BATCH_CUDA(cudaGraphLaunch(exec, bst));
+      note_launch((int)kernels_per_round);
+    } else {
+      for (int i : active) {
+        cudaStream_t saved = ps[i]->st;
+        ps[i]->st = bst;
+        enqueue_iteration_any(ps[i]);
+        ps[i]->st = saved;
+      }
+      PT_BATCH_CUDA(cudaGetLastError());
+    }
+    ++rounds;
+    if (rounds % check == 0 || rounds > max_rounds) {
+      launch_gather_done(dstates, count, ddone, bst);
+      PT_BATCH_CUDA(cudaMemcpyAsync(hdone, ddone, sizeof(int) * count, cudaMemcpyDeviceToHost, bst));
+      PT_BATCH_CUDA(cudaStreamSynchronize(bst));
+      std::vector<int> still;
+      for (int i : active)
+        if (!hdone[i]) still.push_back(i);
+      const size_t finished = active.size() - still.size();
+      if (still.empty()) break;
+      if (rounds > max_rounds + 1) {
+        cleanup();
+        return fail(PT_ECUDA, "batch did not stop at max_it");
+      }
+      if (finished > 0 && finished * 4 >= active.size()) {  // drop finished problems from the graph
+        active.swap(still);
+        if (graphs) PT_BATCH_CUDA(rebuild());
+      }
+    }
+  }
+  PT_BATCH_CUDA(cudaStreamSynchronize(bst));
+  cleanup();
+#undef PT_BATCH_CUDA
+  for (int i = 0; i < count; ++i) {
+    SolveState hs;
+    if ((st = read_state(ps[i], &hs)) != PT_OK) return st;
+    if (iters) iters[i] = hs.iters;
+    if (status) status[i] = (pt_status)hs.status;
+  }
+  return PT_OK;
 }
 
 pt_status pt_problem_get_state(pt_problem* p, double* u_out, double* p_out, int on_device) {
@@ -794,6 +1151,8 @@ void pt_problem_destroy(pt_problem* p) {
   if (!p) return;
   cudaSetDevice(p->device);
   cudaStreamSynchronize(p->st);
+  drop_graph(p);
+  if (p->cap) cudaStreamDestroy(p->cap);
   for (void* a : p->allocs) cudaFree(a);
   if (p->host_state) cudaFreeHost(p->host_state);
   delete p;

@@ -349,7 +349,7 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
                         cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
   const int L = plan_stride(plan);
-  const int C = dst_cols<T>(L, S);
+  const int C = plan.C > 0 ? plan.C : dst_cols<T>(L, S);
   const size_t smem = (size_t)C * L * sizeof(T2);
   static bool attr_set = false;
   if (!attr_set) {
@@ -373,7 +373,7 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
                         int logP, DstPlan<T> plan, const int* done, cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
   const int L = plan_stride(plan);
-  const int C = dst_cols<T>(L, S);
+  const int C = plan.C > 0 ? plan.C : dst_cols<T>(L, S);
   const size_t smem = (size_t)C * L * sizeof(T2);
   static bool attr_set = false;
   if (!attr_set) {

@@ -164,33 +164,37 @@ __global__ void k_norm2_partials(const double* __restrict__ v, long long count,
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// One block of kReduceBlocks threads sums the partials in a fixed order.
+// One block of kReduceBlocks threads sums the partials in a fixed order; the iteration index,
+// tolerance and iteration limit live in the state, so the launch is the same every iteration.
 __global__ void k_finalize_residual(const double* __restrict__ partials, SolveState* state,
-                                    double* __restrict__ hist, int j, double tol, int max_it) {
+                                    double* __restrict__ hist) {
   if (state->done) return;
   double v = partials[threadIdx.x];
   v = block_sum(v);
   if (threadIdx.x == 0) {
+    const int j = state->j;
     const double res = sqrt(v / state->fnorm2);
     hist[j] = res;
     state->last_res = res;
+    state->iters = j;
     if (!(res <= 1e30)) {  // NaN or overflow
       state->status = PT_EDIVERGED;
       state->done = 1;
-      state->iters = j;
-    } else if (res <= tol) {
+    } else if (res <= state->tol) {
       state->status = PT_OK;
       state->done = 1;
-      state->iters = j;
-    } else if (j >= max_it) {
+    } else if (j >= state->max_it) {
       state->status = PT_ENOTCONV;
       state->done = 1;
-      state->iters = j;
+    } else {
+      state->j = j + 1;
     }
   }
 }
 
-__global__ void k_finalize_fnorm(const double* __restrict__ partials, SolveState* state) {
+// start of a solve: ||F||^2 from the partials, counters reset
+__global__ void k_finalize_fnorm(const double* __restrict__ partials, SolveState* state, double tol,
+                                 int max_it) {
   double v = partials[threadIdx.x];
   v = block_sum(v);
   if (threadIdx.x == 0) {
@@ -198,8 +202,16 @@ __global__ void k_finalize_fnorm(const double* __restrict__ partials, SolveState
     state->done = 0;
     state->status = PT_ENOTCONV;
     state->iters = 0;
+    state->j = 0;
+    state->tol = tol;
+    state->max_it = max_it;
     state->last_res = 1.0;
   }
+}
+
+__global__ void k_gather_done(SolveState* const* __restrict__ states, int count, int* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    out[i] = states[i]->done;
 }
 
 template <typename Tp>
@@ -300,15 +312,20 @@ void launch_norm2_partials(const double* v, long long count, double* partials, c
   k_norm2_partials<<<kReduceBlocks, kThreads, 0, st>>>(v, count, partials);
 }
 
-void launch_finalize_residual(const double* partials, SolveState* state, double* hist, int j,
-                              double tol, int max_it, cudaStream_t st) {
+void launch_finalize_residual(const double* partials, SolveState* state, double* hist, cudaStream_t st) {
   LaunchScope ls("finalize", st, 8.0 * kReduceBlocks);
-  k_finalize_residual<<<1, kReduceBlocks, 0, st>>>(partials, state, hist, j, tol, max_it);
+  k_finalize_residual<<<1, kReduceBlocks, 0, st>>>(partials, state, hist);
 }
 
-void launch_finalize_fnorm(const double* partials, SolveState* state, cudaStream_t st) {
+void launch_finalize_fnorm(const double* partials, SolveState* state, double tol, int max_it,
+                           cudaStream_t st) {
   LaunchScope ls("finalize", st, 8.0 * kReduceBlocks);
-  k_finalize_fnorm<<<1, kReduceBlocks, 0, st>>>(partials, state);
+  k_finalize_fnorm<<<1, kReduceBlocks, 0, st>>>(partials, state, tol, max_it);
+}
+
+void launch_gather_done(SolveState* const* states, int count, int* out, cudaStream_t st) {
+  LaunchScope ls("gather_done", st, 12.0 * count);
+  k_gather_done<<<(count + 255) / 256, 256, 0, st>>>(states, count, out);
 }
 
 template <typename Tp>

@@ -66,10 +66,29 @@ void drain_locked() {
 
 }  // namespace
 
+thread_local int g_capturing = 0;
+thread_local unsigned long long g_captured = 0;
+
 void note_launch(int count) { g_launches.fetch_add((unsigned long long)count, std::memory_order_relaxed); }
+
+bool profiling_enabled() { return g_enabled.load(std::memory_order_relaxed) != 0; }
+
+void capture_begin() {
+  g_capturing = 1;
+  g_captured = 0;
+}
+
+unsigned long long capture_end() {
+  g_capturing = 0;
+  return g_captured;
+}
 
 LaunchScope::LaunchScope(const char* name, cudaStream_t st, double bytes, double flops)
     : name_(name), st_(st), bytes_(bytes), flops_(flops), e0_(nullptr) {
+  if (g_capturing) {  // recorded into a graph: counted when the graph is launched
+    ++g_captured;
+    return;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (g_enabled.load(std::memory_order_relaxed)) {
     std::lock_guard<std::mutex> lk(g_mu);

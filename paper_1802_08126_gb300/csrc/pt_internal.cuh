@@ -40,6 +40,11 @@ class LaunchScope {
   void* e0_;
 };
 void note_launch(int count = 1);
+bool profiling_enabled();
+// Launches between capture_begin and capture_end (same thread) are recorded into a CUDA graph:
+// they are not counted as executed; capture_end returns how many were recorded.
+void capture_begin();
+unsigned long long capture_end();
 
 struct Level {
   int n;             // interior points per axis
@@ -111,15 +116,22 @@ struct SolveState {
   int done;      // 1 once converged / failed / exhausted
   int status;    // pt_status of the solve
   int iters;     // number of Uzawa updates performed
-  int pad;
+  int j;         // index of the iterate whose residual the next finalize records
   double fnorm2; // ||F||^2
   double last_res;
+  double tol;
+  int max_it;
+  int pad;
 };
 
-// sum partials in fixed order; j-th residual -> hist[j], sets flags.
-void launch_finalize_residual(const double* partials, SolveState* state, double* hist, int j,
-                              double tol, int max_it, cudaStream_t st);
-void launch_finalize_fnorm(const double* partials, SolveState* state, cudaStream_t st);
+// sum partials in fixed order; residual of iterate state->j -> hist[j], sets flags, advances j.
+void launch_finalize_residual(const double* partials, SolveState* state, double* hist, cudaStream_t st);
+// start of a solve: ||F||^2 and the reset of the counters
+void launch_finalize_fnorm(const double* partials, SolveState* state, double tol, int max_it,
+                           cudaStream_t st);
+
+// out[i] = states[i]->done for a batch of solves
+void launch_gather_done(SolveState* const* states, int count, int* out, cudaStream_t st);
 
 // elementwise y += a * x over count padded entries (x in Tp)
 template <typename Tp>
@@ -180,6 +192,7 @@ struct DstPlan {
   const T* gfwd = nullptr;   // [M] FFT_M of the chirp filter for the e^{-} transform, bit-reversed, / M
   const T* ginv = nullptr;   // [M] same for the e^{+} transform
   const T* twM = nullptr;    // [M/2] e^{2 pi i k / M}
+  int C = 0;                 // complex columns per CTA (0: chosen from shared-memory size)
 };
 
 // in-place forward transform: x_k <- sum_n x_n sin((2k-1) n pi/(2N)) for every interior column

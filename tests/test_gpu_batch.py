@@ -1,0 +1,82 @@
+"""Batched solves (one CUDA graph launch per iteration for many uneven problems), graph replay
+versus plain launches, and the autotuner: all must return the same answers as solo solves."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1802_08126_gb300 import build
+    build.build()
+
+
+def make(prob, precision="fp64", **kw):
+    import paper_1802_08126_gb300 as ptu
+    return ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, S.source(prob), S.initial(prob),
+                       precision=precision, omega=0.5, **kw)
+
+
+def state_u(P, prob):
+    u = np.zeros((prob.N, prob.ns))
+    P.get_state(u_out=u)
+    return u
+
+
+def test_batch_of_uneven_problems_equals_solo_solves():
+    import paper_1802_08126_gb300 as ptu
+    probs = [S.batch_problem(i) for i in range(6)]
+    probs = [S.Problem(p.name, p.dim, [min(p.n[0], 63)] * 2, min(p.N, 300), p.T, p.coeff, p.f_kind, p.seed)
+             for p in probs] + [S.heat1d_mms(31, 37), S.heat3d_bumps(7, 16)]
+    precs = ["mixed", "fp64"] * (len(probs) // 2)
+    solo = []
+    for p, pr in zip(probs, precs):
+        with make(p, pr) as P:
+            st, it, _ = P.solve(1e-10, 600)
+            solo.append((st, it, state_u(P, p)))
+    Ps = [make(p, pr) for p, pr in zip(probs, precs)]
+    its, sts = ptu.solve_batch(Ps, 1e-10, 600)
+    for k, (p, P) in enumerate(zip(probs, Ps)):
+        assert sts[k] == 0 and solo[k][0] == 0
+        assert its[k] == solo[k][1], p.name
+        u = state_u(P, p)
+        assert np.array_equal(u, solo[k][2]), p.name
+        ref = oracle.implicit_euler(p.dim, p.n, p.N, p.T, p.coeff, S.source(p), S.initial(p))
+        assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= 1e-8
+        P.close()
+
+
+def test_graph_replay_equals_plain_launches():
+    prob = S.heat2d_uniform(31, 40)
+    out = []
+    for graphs in (True, False):
+        with make(prob, graphs=graphs) as P:
+            st, it, hist = P.solve(1e-11, 500)
+            out.append((it, hist.copy(), state_u(P, prob)))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_configuration_gives_the_same_solution(precision, tmp_path, monkeypatch):
+    monkeypatch.setenv("PT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    prob = S.heat2d_uniform(63, 48)
+    with make(prob, precision) as P:
+        P.solve(1e-10, 500)
+        base = state_u(P, prob)
+    with make(prob, precision, autotune=True) as P:
+        st, it, _ = P.solve(1e-10, 500)
+        tuned = state_u(P, prob)
+    assert st == 0
+    assert np.linalg.norm(tuned - base) / np.linalg.norm(base) <= (1e-12 if precision == "fp64" else 1e-9)
+    for cols, ce in [(1, 256), (4, 4096), (16, 0)]:
+        with make(prob, precision, dst_cols=cols, coarse_elems=ce) as P:
+            st, it, _ = P.solve(1e-10, 500)
+            u = state_u(P, prob)
+        assert st == 0
+        assert np.linalg.norm(u - base) / np.linalg.norm(base) <= (1e-12 if precision == "fp64" else 1e-9)
