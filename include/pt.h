@@ -77,7 +77,9 @@ typedef struct {
   int precision;         /* PT_PREC_FP64: everything in FP64.  PT_PREC_MIXED: preconditioner
                             (V-cycles, DSTs, block solves) in FP32; residuals, dot products
                             and the updates of u and p in FP64 (iterative refinement). */
-  double omega;          /* Uzawa damping (§3, eq. 3.1); <= 0 selects 0.5 */
+  double omega;          /* Uzawa damping (§3, eq. 3.1); <= 0 selects 1.5 / (1 + alpha) with
+                            alpha = max((a0+|c|)/a0, a0/(a0-|c|)), the constant of eq. 2.2 for
+                            the coefficient range against its time mean (0.5 for |c| = a0/2) */
   int spatial_solver;    /* PT_SOLVER_MG, or PT_SOLVER_EXACT_1D (dim == 1 only) */
   int n_vcycles;         /* V-cycles per spatial solve; 0 selects 1 */
   double jacobi_weight;  /* weighted-Jacobi smoothing weight; <= 0 selects 2/3, 4/5, 6/7 by dim */
@@ -100,7 +102,8 @@ typedef struct pt_problem pt_problem; /* opaque, library-owned */
 
 /* Create a problem and upload its data.
  *   grid, N_t >= 1, T > 0, coeff: the PDE and its discretisation (see above).
- *   f  : [N_t][n_s] values f(x_i, t_n), n = 1..N_t (host or device, see f_on_device); required.
+ *   f  : [N_t][n_s] values f(x_i, t_n), n = 1..N_t (host or device, see f_on_device); NULL means
+ *        f = 0 (see also pt_problem_set_rhs_uniform).
  *   u0 : [n_s] initial datum u_I, or NULL for zero.
  *   opts: may be NULL (all defaults).
  * Forms F = [tau f_1 + u0, tau f_2, ..., tau f_N] on the device (§2, after eq. 2.4),
@@ -113,6 +116,13 @@ pt_status pt_problem_create(const pt_grid* grid, int N_t, double T, const pt_coe
 /* Replace the source f (and u0) of an existing problem; same layouts as pt_problem_create. */
 pt_status pt_problem_set_rhs(pt_problem* p, const double* f, int f_on_device, const double* u0,
                              int u0_on_device);
+
+/* Replace the source by the synthetic field f(x_i, t_n) = 2 U - 1, U in [0,1) from the top 53 bits
+ * of draw q of SplitMix64 (Steele, Lea & Flood 2014) started at `seed`, q = (n-1) n_s + i the
+ * packed index of the point; generated on the device (no host copy).  u0 as in
+ * pt_problem_set_rhs. */
+pt_status pt_problem_set_rhs_uniform(pt_problem* p, unsigned long long seed, const double* u0,
+                                     int u0_on_device);
 
 /* Inexact Uzawa (§3, eq. 3.1) from u = p = 0 until ||F - B u_j|| / ||F|| <= tol or max_it updates.
  *   u_out   : [N_t][n_s] solution u_1..u_N (host or device per u_out_on_device), or NULL.
@@ -134,6 +144,40 @@ pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_o
  * Returns PT_OK when every problem finished (whatever its status), or an error. */
 pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const int* max_it, int* iters,
                          pt_status* status);
+
+/* ---- Serving: continuous batching of solves on one GPU -----------------------------------
+ * A server owns one worker thread and the device current at creation.  Submitted requests are
+ * queued; at every iteration boundary the worker admits queued requests while their estimated
+ * device memory fits `hbm_budget` (0: 85 % of the free memory) and fewer than `max_active`
+ * (0: 256) solves are active, keeps their state resident on the device, and advances all
+ * active solves by graph launches that hold one Uzawa iteration of each (pt_solve_batch's
+ * mechanism).  Finished solves are copied to host memory and their device memory is freed at
+ * once, so later requests are admitted while others are still running. */
+typedef struct pt_server pt_server;
+
+pt_status pt_server_create(size_t hbm_budget, int max_active, pt_server** out);
+
+/* Queue one solve.  The problem arguments are those of pt_problem_create (host arrays only; they
+ * are copied); f == NULL selects the synthetic source of pt_problem_set_rhs_uniform with f_seed.
+ * opts->stream is ignored.  *ticket identifies the request.  PT_ENOMEM if the request alone
+ * exceeds the budget, PT_EBUSY once the server is being destroyed. */
+pt_status pt_server_submit(pt_server* sv, const pt_grid* grid, int N_t, double T, const pt_coeff* coeff,
+                           const double* f, unsigned long long f_seed, const double* u0,
+                           const pt_options* opts, double tol, int max_it, unsigned long long* ticket);
+
+/* Wait at most timeout_ms (< 0: no limit) for a request; then copy its solution ([N_t][n_s], host,
+ * may be NULL), iteration count and solve status (PT_OK / PT_ENOTCONV / PT_EDIVERGED) and forget
+ * the ticket.  PT_ETIMEOUT if it is not finished in time (the request stays queued or running);
+ * the creation error of the request if it could not be started. */
+pt_status pt_server_wait(pt_server* sv, unsigned long long ticket, int timeout_ms, double* u_out,
+                         int* iters, pt_status* solve_status);
+
+/* Latency percentiles (submit to result on the host) over the finished requests, space-time DOFs
+ * per second from the first submission to the last completion, and the number finished. */
+pt_status pt_server_stats(pt_server* sv, double* p50_ms, double* p99_ms, double* dofs_per_s, int* completed);
+
+/* Finish every queued and running request, then stop the worker and free everything. */
+void pt_server_destroy(pt_server* sv);
 
 /* Copy the current iterates u_j and p_j (packed [N_t][n_s], FP64) of the problem's last solve.
  * The pair (u_j, p_j) is the complete state of the stationary Uzawa iteration (a checkpoint).

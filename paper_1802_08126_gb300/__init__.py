@@ -20,7 +20,7 @@ from . import _lib
 from ._lib import PT_EDIVERGED, PT_ENOTCONV, PT_OK  # noqa: F401
 
 __all__ = ["Problem", "PtError", "launch_count", "status_name", "profile_enable", "profile_reset",
-           "profile_totals", "dst_forward_noalloc", "solve_batch"]
+           "profile_totals", "dst_forward_noalloc", "solve_batch", "Server"]
 
 
 class PtError(RuntimeError):
@@ -66,6 +66,75 @@ def profile_totals() -> dict:
             break
         out[name.value.decode()] = {"ms": ms.value, "bytes": b.value, "flops": fl.value, "launches": n.value}
     return out
+
+
+def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=False):
+    o = _lib.Options()
+    o.precision = {"fp64": _lib.PT_PREC_FP64, "mixed": _lib.PT_PREC_MIXED}[precision]
+    o.omega = float(omega)
+    o.spatial_solver = {"mg": _lib.PT_SOLVER_MG, "exact": _lib.PT_SOLVER_EXACT_1D}[solver]
+    o.check_every = int(check_every)
+    o.autotune = 1 if autotune else 0
+    return o
+
+
+class Server:
+    """Continuous-batching solve server on the current device (wraps ``pt_server``)."""
+
+    def __init__(self, hbm_budget: int = 0, max_active: int = 0):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        _check(self._lib.pt_server_create(int(hbm_budget), int(max_active), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, dim, n, N, T, coeff, f=None, seed: int = 0, u0=None, tol: float = 1e-8,
+               max_it: int = 2000, **opts) -> int:
+        g = _lib.Grid()
+        g.dim = dim
+        for d in range(3):
+            g.n[d] = int(n[d]) if d < dim else 1
+        fp, fdev = _ptr(f)
+        up, udev = _ptr(u0)
+        if fdev or udev:
+            raise ValueError("server requests take host arrays")
+        o = _options(**opts)
+        t = ctypes.c_ulonglong()
+        _check(self._lib.pt_server_submit(self._h, ctypes.byref(g), int(N), float(T), ctypes.byref(_coeff(coeff)),
+                                          fp, int(seed) & 0xFFFFFFFFFFFFFFFF, up, ctypes.byref(o), float(tol),
+                                          int(max_it), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, u_out=None, timeout_ms: int = -1):
+        """Returns (solve status, iterations); raises PtError (e.g. PT_ETIMEOUT)."""
+        up, _ = _ptr(u_out)
+        it, stt = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.pt_server_wait(self._h, ctypes.c_ulonglong(ticket), int(timeout_ms), up,
+                                        ctypes.byref(it), ctypes.byref(stt)))
+        return stt.value, it.value
+
+    def stats(self):
+        p50, p99, rate = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        done = ctypes.c_int()
+        _check(self._lib.pt_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(rate),
+                                         ctypes.byref(done)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "dofs_per_s": rate.value, "completed": done.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pt_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def solve_batch(problems, tol, max_it):
@@ -171,6 +240,11 @@ class Problem:
         fp, fdev = _ptr(f)
         up, udev = _ptr(u0)
         _check(self._lib.pt_problem_set_rhs(self._h, fp, fdev, up, udev))
+
+    def set_rhs_uniform(self, seed: int, u0=None):
+        """Source f = U(-1,1) per space-time node from SplitMix64(seed), generated on the device."""
+        up, udev = _ptr(u0)
+        _check(self._lib.pt_problem_set_rhs_uniform(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, up, udev))
 
     def solve(self, tol: float, max_it: int, u_out=None, with_history: bool = True):
         """Run the Uzawa iteration; returns (status, iters, history).

@@ -17,6 +17,8 @@ EXPORTED = (
     "pt_status_string", "pt_apply_B", "pt_dst_forward", "pt_dst_inverse", "pt_precond_A",
     "pt_precond_H", "pt_kernel_launch_count", "pt_problem_get_state", "pt_profile_enable",
     "pt_profile_reset", "pt_profile_get", "pt_dst_forward_noalloc", "pt_solve_batch",
+    "pt_problem_set_rhs_uniform", "pt_server_create", "pt_server_submit", "pt_server_wait",
+    "pt_server_stats", "pt_server_destroy",
 )
 
 
@@ -77,6 +79,20 @@ def load(path: str = LIB_PATH):
         L.pt_profile_reset.restype = None
         L.pt_profile_get.argtypes = [i, ctypes.c_char_p, i, dp, dp, dp, ctypes.POINTER(ctypes.c_ulonglong)]
         L.pt_profile_get.restype = i
+        L.pt_problem_set_rhs_uniform.argtypes = [vp, ctypes.c_ulonglong, vp, i]
+        L.pt_problem_set_rhs_uniform.restype = i
+        ull = ctypes.c_ulonglong
+        L.pt_server_create.argtypes = [ctypes.c_size_t, i, ctypes.POINTER(vp)]
+        L.pt_server_create.restype = i
+        L.pt_server_submit.argtypes = [vp, ctypes.POINTER(Grid), i, ctypes.c_double, ctypes.POINTER(Coeff), vp,
+                                       ull, vp, ctypes.POINTER(Options), ctypes.c_double, i, ctypes.POINTER(ull)]
+        L.pt_server_submit.restype = i
+        L.pt_server_wait.argtypes = [vp, ull, i, vp, ip, ip]
+        L.pt_server_wait.restype = i
+        L.pt_server_stats.argtypes = [vp, dp, dp, dp, ip]
+        L.pt_server_stats.restype = i
+        L.pt_server_destroy.argtypes = [vp]
+        L.pt_server_destroy.restype = None
         L.pt_solve_batch.argtypes = [ctypes.POINTER(vp), i, dp, ip, ip, ip]
         L.pt_solve_batch.restype = i
         L.pt_dst_forward_noalloc.argtypes = [vp, vp, i, ctypes.c_longlong, vp]

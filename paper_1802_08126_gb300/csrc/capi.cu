@@ -418,6 +418,10 @@ pt_status finish_solve(pt_problem* p, int* iters_out, double* res_hist) {
 
 long long padded_total(const pt_problem* p) { return p->lev[0].S * p->N; }
 
+// Iterations per captured graph: small problems take 8 per launch, so that in a shared launch
+// (batch or server) they advance several iterations while a large problem does one.
+int graph_iterations(const pt_problem* p) { return padded_total(p) >= (1LL << 22) ? 1 : 8; }
+
 pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* res_hist) {
   pt_status st = enqueue_reset(p, tol, max_it);
   if (st != PT_OK) return st;
@@ -426,7 +430,7 @@ pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* r
   int check = p->opt.check_every;
   if (check <= 0) check = small ? 8 : 1;
   const bool graphs = !p->opt.no_graphs && !profiling_enabled();
-  const int per_launch = graphs ? (small ? std::min(check, 8) : 1) : 1;
+  const int per_launch = graphs ? std::min(check, graph_iterations(p)) : 1;
   if (graphs && (st = ensure_graph(p, per_launch)) != PT_OK) return st;
   long long launched = 0, since_poll = 0;
   for (;;) {
@@ -741,14 +745,14 @@ pt_status setup_precision(pt_problem* p) {
   return PT_OK;
 }
 
-pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, int u0_dev) {
-  if (!f) return fail(PT_EINVAL, "f is required");
+pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, int u0_dev,
+                   const unsigned long long* seed = nullptr) {
   const size_t fbytes = sizeof(double) * (size_t)p->ns * p->N;
   const double* fd = f;
   const double* u0d = u0;
   void* tf = nullptr;
   void* tu = nullptr;
-  if (!f_dev) {
+  if (f && !f_dev) {
     PT_CUDA(cudaMallocAsync(&tf, fbytes, p->st));
     PT_CUDA(cudaMemcpyAsync(tf, f, fbytes, cudaMemcpyHostToDevice, p->st));
     fd = (const double*)tf;
@@ -759,7 +763,12 @@ pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, 
     u0d = (const double*)tu;
   }
   const Level& L = p->lev[0];
-  launch_pack(fd, u0d, p->F, p->tau, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+  if (seed)
+    launch_pack_uniform(*seed, u0d, p->F, p->tau, p->dim, L.n, L.logP, L.S, p->N, p->st);
+  else if (fd)
+    launch_pack(fd, u0d, p->F, p->tau, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+  else
+    launch_pack_uniform(0, u0d, p->F, 0.0, p->dim, L.n, L.logP, L.S, p->N, p->st);  // f = 0
   PT_CHECK_LAUNCH();
   if (tf) PT_CUDA(cudaFreeAsync(tf, p->st));
   if (tu) PT_CUDA(cudaFreeAsync(tu, p->st));
@@ -784,7 +793,14 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   if (opts) p->opt = *opts;
   p->mixed = p->opt.precision == PT_PREC_MIXED;
   p->exact1d = p->opt.spatial_solver == PT_SOLVER_EXACT_1D;
-  p->omega = p->opt.omega > 0.0 ? p->opt.omega : 0.5;
+  if (p->opt.omega > 0.0) {
+    p->omega = p->opt.omega;
+  } else {
+    // alpha of eq. 2.2 for a in [a0 - |c|, a0 + |c|] against the mean coefficient a0
+    const double a0 = coeff->a0, c = std::fabs(coeff->c);
+    const double alpha = std::max((a0 + c) / a0, a0 / (a0 - c));
+    p->omega = 1.5 / (1.0 + alpha);
+  }
   p->jacobi = p->opt.jacobi_weight > 0.0 ? p->opt.jacobi_weight
                                          : (p->dim == 1 ? 2.0 / 3.0 : (p->dim == 2 ? 0.8 : 6.0 / 7.0));
   p->st = (cudaStream_t)p->opt.stream;
@@ -916,6 +932,56 @@ pt_status comp_precond_H(pt_problem* p, const double* r, double* out) {
 
 }  // namespace
 
+namespace pt {
+
+// Hooks used by the serving loop (server.cu).
+pt_status problem_begin(pt_problem* p, double tol, int max_it) {
+  pt_status st = ensure_hist(p, max_it);
+  if (st != PT_OK) return st;
+  if (p->opt.autotune && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+  if ((st = enqueue_reset(p, tol, max_it)) != PT_OK) return st;
+  if ((st = ensure_graph(p, graph_iterations(p))) != PT_OK) return st;
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  return PT_OK;
+}
+
+cudaGraph_t problem_graph(pt_problem* p, unsigned long long* kernels) {
+  if (kernels) *kernels = p->graph_kernels;
+  return p->graph;
+}
+
+SolveState* problem_state(pt_problem* p) { return p->state; }
+
+pt_status problem_result(pt_problem* p, int* iters, pt_status* status) {
+  SolveState hs;
+  pt_status st = read_state(p, &hs);
+  if (st != PT_OK) return st;
+  if (iters) *iters = hs.iters;
+  if (status) *status = (pt_status)hs.status;
+  return PT_OK;
+}
+
+size_t problem_bytes(const pt_problem* p) { return p->bytes; }
+
+long long problem_dofs(const pt_problem* p) { return p->ns * p->N; }
+
+// Upper estimate of the device bytes pt_problem_create will allocate (admission control).
+size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o) {
+  const int d = g->dim;
+  double P = g->n[0] + 1.0, padded = N_t;
+  for (int k = 0; k < d; ++k) padded *= P;
+  const bool mixed = o && o->precision == PT_PREC_MIXED;
+  const double s = mixed ? 4.0 : 8.0;
+  const double lev = 1.0 / ((1 << d) - 1);  // levels below the finest, relative to it
+  double per = 24.0 + 2.0 * s;              // u, p, F and two work vectors
+  per += (d == 2 ? 2.0 : 3.0) * s * lev;    // multigrid right-hand sides, iterates (and residuals)
+  if (d != 2) per += 2.0 * s;               // generic path: level-0 iterate and residual
+  if (d == 2 && !mixed) per += 8.0 * (1.0 + lev);  // cached Jacobi factors
+  return (size_t)(padded * per * 1.05) + (size_t)(4u << 20);
+}
+
+}  // namespace pt
+
 extern "C" {
 
 const char* pt_last_error(void) { return g_err.c_str(); }
@@ -962,6 +1028,16 @@ pt_status pt_problem_set_rhs(pt_problem* p, const double* f, int f_on_device, co
   if (!p) return fail(PT_EINVAL, "problem is NULL");
   PT_CUDA(cudaSetDevice(p->device));
   return load_rhs(p, f, f_on_device, u0, u0_on_device);
+}
+
+pt_status pt_problem_set_rhs_uniform(pt_problem* p, unsigned long long seed, const double* u0,
+                                     int u0_on_device) {
+  g_err.clear();
+  if (!p) return fail(PT_EINVAL, "problem is NULL");
+  PT_CUDA(cudaSetDevice(p->device));
+  pt_status st = load_rhs(p, nullptr, 0, u0, u0_on_device, &seed);
+  if (st == PT_OK) PT_CUDA(cudaStreamSynchronize(p->st));
+  return st;
 }
 
 pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_out_on_device,
@@ -1022,7 +1098,7 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
   const bool graphs = !profiling_enabled();
   if (graphs)
     for (int i = 0; i < count; ++i)
-      if ((st = ensure_graph(ps[i], 1)) != PT_OK) return st;
+      if ((st = ensure_graph(ps[i], graph_iterations(ps[i]))) != PT_OK) return st;
   // device list of the solve states and a pinned copy of their done flags
   cudaStream_t bst = nullptr;
   SolveState** dstates = nullptr;

@@ -27,6 +27,32 @@ __global__ void k_pack(const double* __restrict__ src, const double* __restrict_
   }
 }
 
+// F = scale * (2 U - 1) (+ u0 on slot 0) with U the top 53 bits of SplitMix64 draw q of stream
+// `seed`, q the packed index (t * ns + spatial index) of the point: the generator of Steele, Lea &
+// Flood (2014) used as a counter-based generator.
+template <int DIM>
+__global__ void k_pack_uniform(unsigned long long seed, const double* __restrict__ u0,
+                               double* __restrict__ dst, double scale, int n, int logP, long long total) {
+  const long long ns = DIM == 1 ? n : (DIM == 2 ? (long long)n * n : (long long)n * n * n);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    double v = 0.0;
+    if (decode<DIM>(i, logP, n, t, x, y, z)) {
+      const long long q = ((long long)z * n + y) * n + x;
+      unsigned long long h = seed + ((unsigned long long)(t * ns + q) + 1ull) * 0x9E3779B97F4A7C15ull;
+      h = (h ^ (h >> 30)) * 0xBF58476D1CE4E5B9ull;
+      h = (h ^ (h >> 27)) * 0x94D049BB133111EBull;
+      h ^= h >> 31;
+      const double uni = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+      v = scale * (2.0 * uni - 1.0);
+      if (u0 != nullptr && t == 0) v += u0[q];
+    }
+    dst[i] = v;
+  }
+}
+
 template <int DIM, typename T>
 __global__ void k_pack_typed(const double* __restrict__ src, T* __restrict__ dst, int n, int logP,
                              long long total) {
@@ -253,6 +279,13 @@ void launch_pack(const double* src, const double* u0, double* dst, double scale,
   const long long total = S * N;
   LaunchScope ls("pack", st, 16.0 * dofs(dim, n, N));
   PT_DISPATCH_DIM(dim, k_pack<D><<<grid_for(total), kThreads, 0, st>>>(src, u0, dst, scale, n, logP, total));
+}
+
+void launch_pack_uniform(unsigned long long seed, const double* u0, double* dst, double scale, int dim,
+                         int n, int logP, long long S, int N, cudaStream_t st) {
+  const long long total = S * N;
+  LaunchScope ls("pack", st, 8.0 * dofs(dim, n, N));
+  PT_DISPATCH_DIM(dim, k_pack_uniform<D><<<grid_for(total), kThreads, 0, st>>>(seed, u0, dst, scale, n, logP, total));
 }
 
 template <typename T>

@@ -81,6 +81,9 @@ struct OpBatch {
 // F (padded) = scale * pack(src) (+ u0 on slot 0 when u0 != nullptr), src packed [N][ns].
 void launch_pack(const double* src, const double* u0, double* dst, double scale, int dim, int n,
                  int P, int logP, long long S, int N, cudaStream_t st);
+// F (padded) = scale * (2 U - 1) (+ u0 on slot 0), U from SplitMix64(seed) at the packed index
+void launch_pack_uniform(unsigned long long seed, const double* u0, double* dst, double scale, int dim,
+                         int n, int logP, long long S, int N, cudaStream_t st);
 template <typename T>
 void launch_unpack(const T* src, double* dst, int dim, int n, int P, int logP, long long S, int N,
                    cudaStream_t st);
@@ -206,6 +209,15 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
 template <typename T>
 void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
                         int logP, DstPlan<T> plan, const int* done, cudaStream_t st);
+
+// Problem hooks for the serving loop (defined in capi.cu).
+pt_status problem_begin(pt_problem* p, double tol, int max_it);   // reset + captured iteration graph
+cudaGraph_t problem_graph(pt_problem* p, unsigned long long* kernels);
+SolveState* problem_state(pt_problem* p);
+pt_status problem_result(pt_problem* p, int* iters, pt_status* status);
+size_t problem_bytes(const pt_problem* p);
+long long problem_dofs(const pt_problem* p);
+size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o);
 
 // Set the thread-local message returned by pt_last_error().
 void set_last_error(const char* msg);

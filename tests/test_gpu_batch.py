@@ -80,3 +80,28 @@ def test_autotuned_configuration_gives_the_same_solution(precision, tmp_path, mo
             u = state_u(P, prob)
         assert st == 0
         assert np.linalg.norm(u - base) / np.linalg.norm(base) <= (1e-12 if precision == "fp64" else 1e-9)
+
+
+def test_device_generated_source_matches_host_generator():
+    """pt_problem_set_rhs_uniform draws the same SplitMix64 field on the device as the host
+    generator: the solutions agree bit for bit."""
+    prob = S.heat2d_uniform(31, 20, seed=0x1234ABCD5678)
+    with make(prob) as P:
+        P.solve(1e-11, 500)
+        u1 = state_u(P, prob)
+        P.set_rhs_uniform(prob.seed)
+        P.solve(1e-11, 500)
+        u2 = state_u(P, prob)
+    assert np.array_equal(u1, u2)
+
+
+def test_default_omega_rule():
+    """omega <= 0 selects 1.5 / (1 + alpha); for |c| = a0 / 2 that is the 0.5 used elsewhere."""
+    prob = S.heat2d_uniform(15, 16)
+    import paper_1802_08126_gb300 as ptu
+    out = []
+    for om in (0.0, 0.5):
+        with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, S.source(prob), None, omega=om) as P:
+            st, it, hist = P.solve(1e-10, 500)
+            out.append(hist.copy())
+    assert np.array_equal(out[0], out[1])
