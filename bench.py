@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="heat2d", choices=["heat2d", "heat1d", "heat3d", "batch", "serve"])
+    ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per arrival rate")
+    ap.add_argument("--rates", default="0.5,0.9,1.1", help="serve: arrival rates as fractions of capacity")
     return ap.parse_args()
 
 
@@ -171,14 +175,16 @@ def cpu_sample(prob, seconds, f=None):
     cores = oracle.max_threads()
     if f is None:
         f = S.source(prob, steps=min(prob.N, 64))
+    method = "cg" if prob.dim == 3 else "cholesky"  # the 3-D band is too wide to factor
+    u0 = S.initial(prob)
     t0 = time.perf_counter()
-    oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, None, steps=1)
+    oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, steps=1, method=method)
     one = time.perf_counter() - t0
     k = int(max(1, min(f.shape[0], seconds / max(one, 1e-3))))
     t0 = time.perf_counter()
-    oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, None, steps=k)
+    oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, steps=k, method=method)
     secs = time.perf_counter() - t0
-    return k * prob.ns / secs, k, secs, cores
+    return k * prob.ns / secs, k, secs, cores, method
 
 
 def run_reference(args, rank, ws, dist):
@@ -212,11 +218,161 @@ def run_reference(args, rank, ws, dist):
     return 0
 
 
+def make_batch_problem(ptu, p, precision="mixed"):
+    P = ptu.Problem(p.dim, p.n, p.N, p.T, p.coeff, None, None, precision=precision)
+    P.set_rhs_uniform(p.seed)
+    return P
+
+
+def run_batch(args, rank, ws, dist):
+    """512 independent 2-D problems (grids 31..255, N_t log-uniform in [16, 2048], c ~ U(0, 0.8),
+    k in {1..4}, f ~ U(-1,1) from per-problem seeds), mixed precision, solved with pt_solve_batch in
+    waves that fit the device memory; DOFs/s over the solve time of all waves."""
+    import torch
+
+    import paper_1802_08126_gb300 as ptu
+    from paper_1802_08126_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.set_device(local_rank())
+    probs = [S.batch_problem(i + rank * args.problems) for i in range(args.problems)]
+    # warm-up: three small batches of the smallest problems
+    small = sorted(probs, key=lambda p: p.dofs)[:8]
+    for _ in range(max(args.warmup, 3)):
+        Ps = [make_batch_problem(ptu, p) for p in small]
+        ptu.solve_batch(Ps, args.tol, args.max_it)
+        for P in Ps:
+            P.close()
+    total_dofs = sum(p.dofs for p in probs)
+    clocks = ClockSampler(local_rank())
+    clocks.start()
+    launches0 = ptu.launch_count()
+    solve_s, waves, its, statuses, i = 0.0, 0, [], [], 0
+    while i < len(probs):
+        free, _ = torch.cuda.mem_get_info()
+        budget = free - (24 << 30)
+        Ps, used = [], 0
+        while i < len(probs):
+            est = probs[i].dofs * 1.05 * 40  # bytes per DOF in mixed precision, padded, with margin
+            if Ps and used + est > budget:
+                break
+            Ps.append(make_batch_problem(ptu, probs[i]))
+            used += est
+            i += 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, sts = ptu.solve_batch(Ps, args.tol, args.max_it)
+        torch.cuda.synchronize()
+        solve_s += time.perf_counter() - t0
+        its += it
+        statuses += sts
+        waves += 1
+        for P in Ps:
+            P.close()
+    launches = ptu.launch_count() - launches0
+    clk = clocks.stop()
+    if dist is not None:
+        import torch.distributed as d
+        t = torch.tensor([solve_s], device="cuda", dtype=torch.float64)
+        d.all_reduce(t, op=d.ReduceOp.MAX)
+        solve_s = t.item()
+    if rank == 0:
+        line = {
+            "metric": METRIC + " (batched)", "value": ws * total_dofs / solve_s, "unit": "DOF/s",
+            "n_gpus": ws, "steps": 1, "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * solve_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": "batch%d_heat2d_mixed" % args.problems, "problems": len(probs),
+                       "dofs_per_gpu": total_dofs, "tol": args.tol, "waves": waves,
+                       "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
+                       "converged": int(sum(1 for x in statuses if x == 0)), "precision": "mixed",
+                       "l2": "inputs larger than L2 for most problems"},
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args, rank, ws, dist):
+    """Poisson arrivals of requests drawn from the batch distribution, served by pt_server at
+    several arrival rates given as fractions of the measured capacity; p50/p99 latency."""
+    import torch
+
+    import paper_1802_08126_gb300 as ptu
+    from paper_1802_08126_gb300 import build
+    if rank != 0:
+        return 0
+    build.build()
+    torch.cuda.set_device(local_rank())
+    rng = np.random.default_rng(5)
+    pool = [S.batch_problem(i, master_seed=5) for i in range(4 * args.requests)]
+    mean_dofs = float(np.mean([p.dofs for p in pool]))
+    # capacity: DOFs/s of one batch of the first requests
+    cap_probs = pool[:32]
+    Ps = [make_batch_problem(ptu, p) for p in cap_probs]
+    ptu.solve_batch(Ps, args.tol, args.max_it)
+    for P in Ps:
+        P.set_rhs_uniform(cap_probs[Ps.index(P)].seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ptu.solve_batch(Ps, args.tol, args.max_it)
+    torch.cuda.synchronize()
+    capacity = sum(p.dofs for p in cap_probs) / (time.perf_counter() - t0)
+    for P in Ps:
+        P.close()
+    results = []
+    for frac in [float(x) for x in args.rates.split(",")]:
+        lam = frac * capacity / mean_dofs  # requests per second
+        reqs = [pool[int(k)] for k in rng.integers(0, len(pool), args.requests)]
+        gaps = rng.exponential(1.0 / lam, args.requests)
+        with ptu.Server() as sv:
+            tickets = []
+            t_start = time.perf_counter()
+            t_next = t_start
+            for p, g in zip(reqs, gaps):
+                t_next += g
+                delay = t_next - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(sv.submit(p.dim, p.n, p.N, p.T, p.coeff, None, seed=p.seed, tol=args.tol,
+                                         max_it=args.max_it, precision="mixed"))
+            ok = 0
+            for t in tickets:
+                st, it = sv.wait(t)
+                ok += st == 0
+            st_ = sv.stats()
+            wall = time.perf_counter() - t_start
+        results.append({"rate_frac": frac, "req_per_s": lam, "p50_ms": st_["p50_ms"], "p99_ms": st_["p99_ms"],
+                        "dofs_per_s": st_["dofs_per_s"], "completed": st_["completed"], "converged": ok,
+                        "wall_s": wall})
+    best = max(r["dofs_per_s"] for r in results)
+    line = {
+        "metric": "p50/p99 solve latency and DOFs/s under Poisson arrivals", "value": best, "unit": "DOF/s",
+        "n_gpus": 1, "steps": len(results), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "serve_heat2d_mixed", "requests_per_rate": args.requests, "tol": args.tol,
+                   "capacity_dofs_per_s": capacity, "mean_request_dofs": mean_dofs},
+        "rates": results,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def local_rank():
+    return int(os.environ.get("LOCAL_RANK", "0"))
+
+
 def main():
     args = parse()
     rank, ws, local, dist = dist_init(args)
     if args.impl == "reference":
         return run_reference(args, rank, ws, dist)
+    if args.workload == "batch":
+        return run_batch(args, rank, ws, dist)
+    if args.workload == "serve":
+        return run_serve(args, rank, ws, dist)
 
     import torch
 
@@ -229,11 +385,24 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    prob = S.heat2d_uniform(args.n, args.nt)
+    if args.workload == "heat1d":
+        prob = S.heat1d_mms(63, 64)
+        solver, base_prec = "exact", "fp64"
+    elif args.workload == "heat3d":
+        prob = S.heat3d_bumps(127, 256)
+        solver, base_prec = "mg", "mixed"  # the 3-D workload is specified in mixed precision
+    else:
+        prob = S.heat2d_uniform(args.n, args.nt)
+        solver, base_prec = "mg", "fp64"
+    global WORKLOAD
+    WORKLOAD = {"heat1d": "heat1d_fd3_63_Nt64_T1_fp64_exact", "heat3d": "heat3d_fd7_127^3_Nt256_T2",
+                "heat2d": WORKLOAD}[args.workload]
     dofs = prob.dofs
     f = S.source(prob)
-    P = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, None, precision="fp64",
-                    omega=args.omega)
+    u0 = S.initial(prob)
+    P = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision=base_prec,
+                    omega=args.omega, solver=solver)
+    variant = "fp64" if base_prec == "mixed" else "mixed"
 
     def solve_once(Pr):
         st, it, hist = Pr.solve(args.tol, args.max_it)
@@ -299,12 +468,12 @@ def main():
     if not args.no_e2e:
         fh = torch.from_numpy(f).pin_memory().numpy()
         uh = torch.empty((prob.N, prob.ns), dtype=torch.float64).pin_memory().numpy()
-        P.set_rhs(fh)
+        P.set_rhs(fh, u0)
         P.solve(args.tol, args.max_it, u_out=uh)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            P.set_rhs(fh)
+            P.set_rhs(fh, u0)
             st, it, hist = P.solve(args.tol, args.max_it, u_out=uh)
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
@@ -320,23 +489,29 @@ def main():
         u64 = np.zeros((prob.N, prob.ns))
         P.solve(args.tol, args.max_it, u_out=u64)
 
-    # the mixed-precision form on the same workload
+    # the other precision on the same workload (mixed for the FP64 workloads, FP64 for the 3-D one)
     mixed = None
     if not args.no_mixed:
-        Pm = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, None, precision="mixed",
-                         omega=args.omega)
-        solve_once(Pm)
+        Pm = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision=variant,
+                         omega=args.omega, solver=solver)
+        vsteps = args.steps if variant == "mixed" else 1
+        if variant == "mixed":
+            solve_once(Pm)
+        ptu.profile_reset()
+        ptu.profile_enable(True)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         mits = []
-        for _ in range(args.steps):
+        for _ in range(vsteps):
             it, res = solve_once(Pm)
             mits.append(it)
         e1.record()
         torch.cuda.synchronize()
         mms = e0.elapsed_time(e1)
+        ptu.profile_enable(False)
+        vprof = ptu.profile_totals()
         um = np.zeros((prob.N, prob.ns))
         Pm.solve(args.tol, args.max_it, u_out=um)
         Pm.close()
@@ -344,30 +519,36 @@ def main():
             t = torch.tensor([mms], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             mms = t.item()
-        mixed = {"value": ws * dofs * args.steps / (mms / 1e3), "unit": "DOF/s",
-                 "ms_per_step": mms / args.steps, "iterations": mits[-1],
-                 "rel_l2_vs_fp64_path": float(np.linalg.norm(um - u64) / np.linalg.norm(u64))}
+        mixed = {"precision": variant, "value": ws * dofs * vsteps / (mms / 1e3), "unit": "DOF/s",
+                 "ms_per_step": mms / vsteps, "iterations": mits[-1],
+                 "rel_l2_mixed_vs_fp64_path": float(np.linalg.norm(um - u64) / np.linalg.norm(u64)),
+                 "kernels": {k: {"ms_per_step": v["ms"] / vsteps, "launches_per_step": v["launches"] / vsteps,
+                                 "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
+                             for k, v in sorted(vprof.items(), key=lambda kv: -kv[1]["ms"])}}
     P.close()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, k, secs, cores = cpu_sample(prob, args.cpu_seconds, f[:64])
+        v, k, secs, cores, method = cpu_sample(prob, args.cpu_seconds, f[:64])
         cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
-               "sample": "first %d of %d implicit-Euler steps, banded Cholesky per step (%.1f s)"
-                         % (k, prob.N, secs)}
+               "sample": "first %d of %d implicit-Euler steps, %s per step (%.1f s)"
+                         % (k, prob.N, "banded Cholesky" if method == "cholesky" else "CG to 1e-14", secs)}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [prob.n[0]] * 2, "N_t": prob.N, "T": prob.T,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if base_prec == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(prob.n), "precision": base_prec, "N_t": prob.N, "T": prob.T,
                        "dofs_per_gpu": dofs, "tol": args.tol, "omega": args.omega,
-                       "iterations": its[-1], "spatial_solver": "V(1,1) geometric multigrid",
+                       "iterations": its[-1],
+                       "spatial_solver": "exact tridiagonal" if solver == "exact"
+                       else "V(1,1) geometric multigrid (1 cycle per A_n solve, 2 per H_k solve)",
                        "l2": "inputs larger than L2 (533 MB per space-time vector)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "mixed": mixed, "kernels": phases,
+            "clocks": clk, ("fp64_path" if variant == "fp64" else "mixed"): mixed, "kernels": phases,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

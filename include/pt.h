@@ -81,7 +81,9 @@ typedef struct {
                             alpha = max((a0+|c|)/a0, a0/(a0-|c|)), the constant of eq. 2.2 for
                             the coefficient range against its time mean (0.5 for |c| = a0/2) */
   int spatial_solver;    /* PT_SOLVER_MG, or PT_SOLVER_EXACT_1D (dim == 1 only) */
-  int n_vcycles;         /* V-cycles per spatial solve; 0 selects 1 */
+  int n_vcycles;         /* V-cycles per H_k solve of the Schur preconditioner (1..4; 0 selects 2:
+                            the second cycle brings H~ close to H and roughly halves the Uzawa
+                            iterations); the A~_n solves always use one V-cycle */
   double jacobi_weight;  /* weighted-Jacobi smoothing weight; <= 0 selects 2/3, 4/5, 6/7 by dim */
   void* stream;          /* cudaStream_t for all work of this problem; NULL = default stream */
   int check_every;       /* iterations between host polls of the device convergence flag; 0 = auto */

@@ -96,11 +96,12 @@ class VCycle:
         return self._cycle(0, b, rhs)
 
 
-def st_vcycles(st):
+def st_vcycles(st, h_cycles: int = 2):
     """V-cycle solvers for the Uzawa preconditioners of a ``SpaceTime`` problem.
 
     Returns (Asolve, Hsolve): Asolve applies, slice n, one V-cycle for tau_n A_n
-    (coefficient at t_n); Hsolve(k, r) one V-cycle for H_k = mu_k I + tau Abar.
+    (coefficient at t_n); Hsolve(k, r) applies ``h_cycles`` steps of the V-cycle iteration
+    x <- x + V(r - H_k x) from x = 0 for H_k = mu_k I + tau Abar.
     """
     from .spacetime import assemble_A, mu
 
@@ -118,4 +119,10 @@ def st_vcycles(st):
 
     VA = VCycle(dim, n, build_A)
     VH = VCycle(dim, n, build_H)
-    return VA.apply, VH.apply_one
+
+    def Hsolve(k, r):
+        x = VH.apply_one(k, r)
+        for _ in range(h_cycles - 1):
+            x = x + VH.apply_one(k, r - VH.L[0][k] @ x)
+        return x
+    return VA.apply, Hsolve

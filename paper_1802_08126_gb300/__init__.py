@@ -203,7 +203,7 @@ class Problem:
                  precision: str = "fp64", omega: float = 0.0, solver: str = "mg",
                  stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0,
                  autotune: bool = False, dst_cols: int = 0, coarse_elems: int = 0,
-                 graphs: bool = True):
+                 graphs: bool = True, n_vcycles: int = 0):
         L = _lib.load()
         self._lib = L
         self.dim, self.n, self.N, self.T = dim, list(n)[:dim], N, float(T)
@@ -216,7 +216,7 @@ class Problem:
         opts.precision = {"fp64": _lib.PT_PREC_FP64, "mixed": _lib.PT_PREC_MIXED}[precision]
         opts.omega = float(omega)
         opts.spatial_solver = {"mg": _lib.PT_SOLVER_MG, "exact": _lib.PT_SOLVER_EXACT_1D}[solver]
-        opts.n_vcycles = 0
+        opts.n_vcycles = int(n_vcycles)
         opts.jacobi_weight = float(jacobi_weight)
         opts.stream = stream
         opts.check_every = int(check_every)

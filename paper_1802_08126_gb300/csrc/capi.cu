@@ -73,6 +73,8 @@ struct pt_problem {
   std::vector<void*> allocs;
   double *u = nullptr, *p = nullptr, *F = nullptr;
   void *W1 = nullptr, *W2 = nullptr;            // preconditioner precision, fine level
+  void* W3 = nullptr;                           // residual between V-cycles of an H_k solve
+  int nv_h = 2;                                 // V-cycles per H_k solve
   void* mg_b[kMaxLevels] = {};
   void* mg_x[kMaxLevels] = {};
   void* mg_r[kMaxLevels] = {};
@@ -284,18 +286,30 @@ void apply_precond_A(pt_problem* p, const T* b, void* out, int mode, int out_fp6
   }
 }
 
-// H_k solve (exact in 1-D if requested, else one V-cycle)
+// One V-cycle for all H_k: out = V(b) (mode 0) or out += V(b) (mode 1)
+template <typename T>
+void vcycle_H(pt_problem* p, const T* b, T* out, int mode, const int* done) {
+  if (p->dim == 2) {
+    const T* dinv[kMaxLevels];
+    for (int l = 0; l < kMaxLevels; ++l) dinv[l] = (const T*)p->dinvH[l];
+    vcycle2d<T>(mg_plan<T>(p), op_H<T>(p), b, out, mode, 0, p->hvar, p->hvar ? nullptr : dinv, nullptr,
+                done, p->st);
+  } else {
+    vcycle<T>(mg_plan<T>(p), op_H<T>(p), b, out, mode, 0, done, p->st);
+  }
+}
+
+// H_k solve (§4, eq. 4.6): exact in 1-D if requested, else nv_h V-cycles x <- x + V(b - H_k x)
 template <typename T>
 void apply_Hk_solve(pt_problem* p, const T* b, T* out, const int* done) {
   if (p->exact1d) {
     launch_tridiag<T>(b, out, 0, 0, geom<T>(p, 0), op_H<T>(p), p->N, (T*)p->tri_work, done, p->st);
-  } else if (p->dim == 2) {
-    const T* dinv[kMaxLevels];
-    for (int l = 0; l < kMaxLevels; ++l) dinv[l] = (const T*)p->dinvH[l];
-    vcycle2d<T>(mg_plan<T>(p), op_H<T>(p), b, out, 0, 0, p->hvar, p->hvar ? nullptr : dinv, nullptr,
-                done, p->st);
-  } else {
-    vcycle<T>(mg_plan<T>(p), op_H<T>(p), b, out, 0, 0, done, p->st);
+    return;
+  }
+  vcycle_H<T>(p, b, out, 0, done);
+  for (int c = 1; c < p->nv_h; ++c) {
+    launch_op_residual<T>(b, out, (T*)p->W3, geom<T>(p, 0), op_H<T>(p), p->N, done, p->st);
+    vcycle_H<T>(p, (const T*)p->W3, out, 1, done);
   }
 }
 
@@ -607,7 +621,7 @@ pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff
       return fail(PT_EINVAL, "bad spatial_solver");
     if (o->spatial_solver == PT_SOLVER_EXACT_1D && grid->dim != 1)
       return fail(PT_EINVAL, "exact spatial solves are available in 1-D only");
-    if (o->n_vcycles > 1) return fail(PT_EINVAL, "n_vcycles > 1 is not supported");
+    if (o->n_vcycles < 0 || o->n_vcycles > 4) return fail(PT_EINVAL, "n_vcycles must be in [0, 4]");
     for (int i = 0; i < 3; ++i)
       if (o->reserved[i] != 0) return fail(PT_EINVAL, "reserved options must be zero");
     if (o->dst_cols != 0 && (o->dst_cols < 0 || o->dst_cols > 16 || !is_pow2(o->dst_cols)))
@@ -626,6 +640,10 @@ pt_status setup_precision(pt_problem* p) {
   if (!p->W1) return st;
   p->W2 = alloc_padded<T>(p, L0, p->N, &st);
   if (!p->W2) return st;
+  if (!p->exact1d && p->nv_h > 1) {
+    p->W3 = alloc_padded<T>(p, L0, p->N, &st);
+    if (!p->W3) return st;
+  }
   if (!p->exact1d) {
     const bool fused = p->dim == 2;  // fused 2-D kernels keep no level-0 iterate and no residuals
     for (int l = 0; l <= p->lc_max && l < p->nlev; ++l) {
@@ -792,6 +810,7 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   p->coeff = *coeff;
   if (opts) p->opt = *opts;
   p->mixed = p->opt.precision == PT_PREC_MIXED;
+  p->nv_h = p->opt.n_vcycles > 0 ? p->opt.n_vcycles : 2;
   p->exact1d = p->opt.spatial_solver == PT_SOLVER_EXACT_1D;
   if (p->opt.omega > 0.0) {
     p->omega = p->opt.omega;

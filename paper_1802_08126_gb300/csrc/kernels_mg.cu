@@ -524,6 +524,20 @@ void vcycle(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mo
 }
 
 template <typename T>
+void launch_op_residual(const T* b, const T* x, T* r, StencilGeom<T> g, OpBatch<T> op, int B,
+                        const int* done, cudaStream_t st) {
+  const long long total = g.S * B;
+  double d = B;
+  for (int k = 0; k < g.dim; ++k) d *= g.n;
+  LaunchScope ls("mg_residual", st, 3.0 * sizeof(T) * d);
+  switch (g.dim) {
+    case 1: k_residual<1, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, g, op, total, done); break;
+    case 2: k_residual<2, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, g, op, total, done); break;
+    default: k_residual<3, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, g, op, total, done); break;
+  }
+}
+
+template <typename T>
 void vcycle_coarse(const MGPlan<T>& plan, OpBatch<T> op, const T* bl, void* out, int mode, int out_fp64,
                    const int* done, cudaStream_t st) {
   switch (plan.dim) {
@@ -543,6 +557,8 @@ void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T
 
 template void vcycle<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, const int*, cudaStream_t);
 template void vcycle<double>(const MGPlan<double>&, OpBatch<double>, const double*, void*, int, int, const int*, cudaStream_t);
+template void launch_op_residual<float>(const float*, const float*, float*, StencilGeom<float>, OpBatch<float>, int, const int*, cudaStream_t);
+template void launch_op_residual<double>(const double*, const double*, double*, StencilGeom<double>, OpBatch<double>, int, const int*, cudaStream_t);
 template void vcycle_coarse<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, const int*, cudaStream_t);
 template void vcycle_coarse<double>(const MGPlan<double>&, OpBatch<double>, const double*, void*, int, int, const int*, cudaStream_t);
 template void launch_tridiag<float>(const float*, void*, int, int, StencilGeom<float>, OpBatch<float>, int, float*, const int*, cudaStream_t);

@@ -163,12 +163,17 @@ template <typename T>
 void vcycle(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int mode, int out_fp64,
             const int* done, cudaStream_t st);
 
+// r = b - L x for a batch of slices on one level (L = sig I + s A(cth) per slice)
+template <typename T>
+void launch_op_residual(const T* b, const T* x, T* r, StencilGeom<T> g, OpBatch<T> op, int B,
+                        const int* done, cudaStream_t st);
+
 // Levels lc..nlev-1 of a V-cycle (one CTA per slice); input bl at level lc.
 template <typename T>
 void vcycle_coarse(const MGPlan<T>& plan, OpBatch<T> op, const T* bl, void* out, int mode, int out_fp64,
                    const int* done, cudaStream_t st);
 
-// Fused 2-D V-cycle (kernels_mg2d.cu).  var: variable face coefficients (else the constant a0);
+// Fused 2-D V-cycle (kernels_mg2d.cu); mode 1 accumulates into out (precision T when !out_fp64).  var: variable face coefficients (else the constant a0);
 // dinv_slice[l]: per-level [B] arrays of w/D for constant coefficients; jinv[l]: per-level cached
 // w/D (padded layout) for variable coefficients, or nullptr to compute it in the kernels.
 template <typename T>

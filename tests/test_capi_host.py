@@ -59,7 +59,7 @@ def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0):
 
 
 @pytest.mark.parametrize("kw", [dict(n=6), dict(N=3000), dict(N=0), dict(dim=4), dict(c=1.0),
-                                dict(solver=1, dim=2), dict(nv=2), dict(reserved=1)])
+                                dict(solver=1, dim=2), dict(nv=5), dict(reserved=1)])
 def test_invalid_arguments_rejected_on_host(lib, kw):
     st, h = _create(lib, **kw)
     assert st == _lib.PT_EINVAL

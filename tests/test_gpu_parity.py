@@ -103,13 +103,16 @@ def test_apply_B_matches_oracle(prob):
 
 @pytest.mark.parametrize("prob", SMALL[:4], ids=lambda p: p.name)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_vcycle_preconditioners_match_oracle_vcycle(prob, precision):
+@pytest.mark.parametrize("cycles", [1, 2, 3])
+def test_vcycle_preconditioners_match_oracle_vcycle(prob, precision, cycles):
     tol = 1e-11 if precision == "fp64" else 5e-6
     T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
-    Asolve, Hsolve = mg.st_vcycles(T)
+    Asolve, Hsolve = mg.st_vcycles(T, h_cycles=cycles)
     rng = np.random.default_rng(5)
     r = rng.standard_normal((prob.N, prob.ns))
-    with make(prob, precision) as P:
+    import paper_1802_08126_gb300 as ptu
+    with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, S.source(prob), S.initial(prob),
+                     precision=precision, omega=0.5, n_vcycles=cycles) as P:
         out = torch.empty_like(dev(r))
         P.precond_A(dev(r), out)
         ref = Asolve(r)

@@ -126,7 +126,7 @@ def test_uzawa_contraction_bound(use_mg):
     F = T.rhs(f, u0)
     N, m = p.N, T.ns
     if use_mg:
-        Asolve, Hsolve = mg.st_vcycles(T)
+        Asolve, Hsolve = mg.st_vcycles(T, h_cycles=1)
     else:
         Asolve, Hsolve = T.exact_A_solver(), T.exact_H_solver()
     # dense A~^-1 (block diagonal) and H~^-1 from the solvers' actions on unit vectors
