@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="override the workload's precision (profiling runs)")
     ap.add_argument("--workload", default="heat2d", choices=["heat2d", "heat1d", "heat3d", "batch", "serve"])
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per arrival rate")
@@ -394,6 +396,8 @@ def main():
     else:
         prob = S.heat2d_uniform(args.n, args.nt)
         solver, base_prec = "mg", "fp64"
+    if args.precision:
+        base_prec = args.precision
     global WORKLOAD
     WORKLOAD = {"heat1d": "heat1d_fd3_63_Nt64_T1_fp64_exact", "heat3d": "heat3d_fd7_127^3_Nt256_T2",
                 "heat2d": WORKLOAD}[args.workload]

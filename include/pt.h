@@ -97,7 +97,10 @@ typedef struct {
                             CTA per slice; 0 = 1024; else a power of two in [64, 4096] */
   int no_graphs;         /* 1: launch kernels one by one instead of replaying a captured CUDA
                             graph of the iteration (kernel timing via pt_profile_* also does) */
-  int reserved[3];       /* must be zero */
+  int h_solver;          /* H_k solves of the Schur preconditioner: 0 = automatic (exact, by spatial
+                            sine transforms, when the reference coefficient is constant and
+                            dim == 2; else V-cycles), 1 = V-cycles, 2 = exact (error if unavailable) */
+  int reserved[2];       /* must be zero */
 } pt_options;
 
 typedef struct pt_problem pt_problem; /* opaque, library-owned */

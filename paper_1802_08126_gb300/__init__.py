@@ -68,8 +68,9 @@ def profile_totals() -> dict:
     return out
 
 
-def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=False):
+def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=False, h_solver="auto"):
     o = _lib.Options()
+    o.h_solver = {"auto": 0, "vcycle": 1, "exact": 2}[h_solver]
     o.precision = {"fp64": _lib.PT_PREC_FP64, "mixed": _lib.PT_PREC_MIXED}[precision]
     o.omega = float(omega)
     o.spatial_solver = {"mg": _lib.PT_SOLVER_MG, "exact": _lib.PT_SOLVER_EXACT_1D}[solver]
@@ -203,7 +204,7 @@ class Problem:
                  precision: str = "fp64", omega: float = 0.0, solver: str = "mg",
                  stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0,
                  autotune: bool = False, dst_cols: int = 0, coarse_elems: int = 0,
-                 graphs: bool = True, n_vcycles: int = 0):
+                 graphs: bool = True, n_vcycles: int = 0, h_solver: str = "auto"):
         L = _lib.load()
         self._lib = L
         self.dim, self.n, self.N, self.T = dim, list(n)[:dim], N, float(T)
@@ -224,6 +225,7 @@ class Problem:
         opts.dst_cols = int(dst_cols)
         opts.coarse_elems = int(coarse_elems)
         opts.no_graphs = 0 if graphs else 1
+        opts.h_solver = {"auto": 0, "vcycle": 1, "exact": 2}[h_solver]
         self._opts = opts
         fp, fdev = _ptr(f)
         up, udev = _ptr(u0)

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
                 ("spatial_solver", ctypes.c_int), ("n_vcycles", ctypes.c_int),
                 ("jacobi_weight", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("check_every", ctypes.c_int), ("autotune", ctypes.c_int), ("dst_cols", ctypes.c_int),
-                ("coarse_elems", ctypes.c_int), ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("coarse_elems", ctypes.c_int), ("no_graphs", ctypes.c_int), ("h_solver", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lock = threading.Lock()

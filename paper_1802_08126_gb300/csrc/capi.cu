@@ -74,6 +74,11 @@ struct pt_problem {
   double *u = nullptr, *p = nullptr, *F = nullptr;
   void *W1 = nullptr, *W2 = nullptr;            // preconditioner precision, fine level
   void* W3 = nullptr;                           // residual between V-cycles of an H_k solve
+  double* bres = nullptr;                       // F - B u of the current iterate (mixed precision)
+  bool hdst = false;                            // exact H_k solves by spatial sine transforms
+  void* dsti_tw = nullptr;                      // [n+1] complex e^{2 pi i k / (2(n+1))}
+  double* dsti_lam = nullptr;                   // [n] (4 a0/h^2) sin^2(pi k h / 2)
+  double* dsti_mu = nullptr;                    // [N] mu_k
   int nv_h = 2;                                 // V-cycles per H_k solve
   void* mg_b[kMaxLevels] = {};
   void* mg_x[kMaxLevels] = {};
@@ -313,15 +318,26 @@ void apply_Hk_solve(pt_problem* p, const T* b, T* out, const int* done) {
   }
 }
 
-// W1 = rhat (in place transform done by caller) -> W2 = yhat = (2 tau/N) H~^-1 Abar H~^-1 rhat
+// W1 = rhat (after the temporal transform) -> yhat = (2 tau/N) H~_k^-1 Abar H~_k^-1 rhat for all k
+// (§4, eq. 4.4/4.6); returns the buffer holding yhat (W1 for the exact transform solve, else W2).
 template <typename T>
-void block_solve(pt_problem* p, const int* done) {
+T* block_solve(pt_problem* p, const int* done) {
   T* W1 = (T*)p->W1;
   T* W2 = (T*)p->W2;
+  if (p->hdst) {
+    const Level& L = p->lev[0];
+    const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
+    launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, (const T*)p->dsti_tw, p->st);
+    launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, (const T*)p->dsti_tw, p->dsti_lam, p->dsti_mu,
+                        p->tau, c0, true, p->st);
+    launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, (const T*)p->dsti_tw, p->st);
+    return W1;
+  }
   apply_Hk_solve<T>(p, W1, W2, done);
   launch_apply_A_scaled<T>(W2, W1, geom<T>(p, 0), (T)p->cthbar, (T)(2.0 * p->tau / p->N), p->N, done,
                            p->st);
   apply_Hk_solve<T>(p, W1, W2, done);
+  return W2;
 }
 
 // One Uzawa iteration (§3, eq. 3.1) on the problem's stream; every kernel returns at once when
@@ -334,13 +350,23 @@ void enqueue_iteration(pt_problem* p) {
   T* W1 = (T*)p->W1;
   T* W2 = (T*)p->W2;
   const DstPlan<T> dp = dst_plan<T>(p);
-  launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, p->tau, p->N, done, p->st);
-  apply_precond_A<T>(p, W1, p->p, 1, 1, done);
-  launch_resid_u<T>(p->u, p->p, p->F, W1, p->partials, g, p->cth_d, p->tau, p->N, done, p->st);
-  launch_finalize_residual(p->partials, p->state, p->hist, p->st);
+  if (p->mixed) {
+    // outer residual in FP64 first (and the convergence test), then the p-update and r_u
+    launch_resid_bres_mixed(p->u, p->p, p->F, p->bres, (float*)W1, p->partials, g, p->cth_d, p->tau, p->N,
+                            done, p->st);
+    launch_finalize_residual(p->partials, p->state, p->hist, p->st);
+    apply_precond_A<T>(p, W1, p->p, 1, 1, done);
+    launch_resid_u_from_bres(p->bres, p->u, p->p, (float*)W1, p->lev[0].S, p->N, p->dim, p->n, done, p->st);
+  } else {
+    launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, p->tau, p->N, done, p->st);
+    apply_precond_A<T>(p, W1, p->p, 1, 1, done);
+    launch_resid_u<T>(p->u, p->p, p->F, W1, p->partials, g, p->cth_d, p->tau, p->N, done, p->st);
+    launch_finalize_residual(p->partials, p->state, p->hist, p->st);
+  }
   launch_dst_forward<T>(W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
-  block_solve<T>(p, done);
-  launch_dst_inverse<T>(W2, p->u, 1, p->omega, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
+  T* yhat = block_solve<T>(p, done);
+  launch_dst_inverse<T>(yhat, p->u, 1, p->omega, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
+  (void)W2;
 }
 
 void enqueue_iteration_any(pt_problem* p) {
@@ -622,8 +648,9 @@ pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff
     if (o->spatial_solver == PT_SOLVER_EXACT_1D && grid->dim != 1)
       return fail(PT_EINVAL, "exact spatial solves are available in 1-D only");
     if (o->n_vcycles < 0 || o->n_vcycles > 4) return fail(PT_EINVAL, "n_vcycles must be in [0, 4]");
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
       if (o->reserved[i] != 0) return fail(PT_EINVAL, "reserved options must be zero");
+    if (o->h_solver < 0 || o->h_solver > 2) return fail(PT_EINVAL, "h_solver must be 0, 1 or 2");
     if (o->dst_cols != 0 && (o->dst_cols < 0 || o->dst_cols > 16 || !is_pow2(o->dst_cols)))
       return fail(PT_EINVAL, "dst_cols must be 0 or a power of two <= 16");
     if (o->coarse_elems != 0 && (o->coarse_elems < 64 || o->coarse_elems > 4096 || !is_pow2(o->coarse_elems)))
@@ -689,6 +716,29 @@ pt_status setup_precision(pt_problem* p) {
       if (!(p->dinvH[l] = alloc_bytes(p, nb, &st))) return st;
       if ((st = upload<T>(p, p->dinvH[l], dv)) != PT_OK) return st;
     }
+  }
+  // exact H_k solves by spatial sine transforms (constant reference coefficient, 2-D)
+  p->hdst = !p->exact1d && p->dim == 2 && !p->hvar && p->opt.h_solver != 1;
+  if (p->hdst) {
+    const int M = p->n + 1;
+    std::vector<double> tw(2 * M), lam(p->n), mud(mu.begin(), mu.end());
+    for (int k = 0; k < M; ++k) {
+      tw[2 * k] = std::cos(M_PI * k / M);  // e^{2 pi i k / (2M)}
+      tw[2 * k + 1] = std::sin(M_PI * k / M);
+    }
+    const double h = 1.0 / M;
+    for (int k = 1; k <= p->n; ++k) {
+      const double sn = std::sin(M_PI * k * h / 2.0);
+      lam[k - 1] = 4.0 * p->coeff.a0 / (h * h) * sn * sn;
+    }
+    if (!(p->dsti_tw = alloc_bytes(p, sizeof(T) * tw.size(), &st))) return st;
+    if (!(p->dsti_lam = (double*)alloc_bytes(p, sizeof(double) * lam.size(), &st))) return st;
+    if (!(p->dsti_mu = (double*)alloc_bytes(p, sizeof(double) * mud.size(), &st))) return st;
+    if ((st = upload<T>(p, p->dsti_tw, tw)) != PT_OK) return st;
+    if ((st = upload<double>(p, p->dsti_lam, lam)) != PT_OK) return st;
+    if ((st = upload<double>(p, p->dsti_mu, mud)) != PT_OK) return st;
+  } else if (p->opt.h_solver == 2) {
+    return fail(PT_EINVAL, "exact H_k solves need dim == 2 and a reference coefficient constant in space");
   }
   // FP64 2-D: cache w / D of every tau A_n (a division per point per smoothing step otherwise)
   if (!p->exact1d && p->dim == 2 && sizeof(T) == 8) {
@@ -876,6 +926,7 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   if (!(p->u = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->p = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->F = alloc_padded<double>(p, L0, p->N, &st))) return st;
+  if (p->mixed && !(p->bres = alloc_padded<double>(p, L0, p->N, &st))) return st;
   st = p->mixed ? setup_precision<float>(p) : setup_precision<double>(p);
   if (st != PT_OK) return st;
   if (!(p->partials = (double*)alloc_bytes(p, sizeof(double) * kReduceBlocks, &st))) return st;
@@ -942,11 +993,12 @@ pt_status comp_precond_H(pt_problem* p, const double* r, double* out) {
   pt_status st;
   if ((st = pack_into<T>(p, r, (T*)p->W1)) != PT_OK) return st;
   launch_dst_forward<T>((T*)p->W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dst_plan<T>(p), nullptr, p->st);
-  block_solve<T>(p, nullptr);
-  launch_dst_inverse<T>((const T*)p->W2, p->W1, 0, 1.0, p->lev[0].S, p->dim, p->n, p->lev[0].logP,
-                        dst_plan<T>(p), nullptr, p->st);
+  T* yhat = block_solve<T>(p, nullptr);
+  T* dest = yhat == (T*)p->W1 ? (T*)p->W2 : (T*)p->W1;
+  launch_dst_inverse<T>(yhat, dest, 0, 1.0, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dst_plan<T>(p), nullptr,
+                        p->st);
   PT_CHECK_LAUNCH();
-  return unpack_from<T>(p, (const T*)p->W1, out);
+  return unpack_from<T>(p, dest, out);
 }
 
 }  // namespace
@@ -992,7 +1044,8 @@ size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o) {
   const bool mixed = o && o->precision == PT_PREC_MIXED;
   const double s = mixed ? 4.0 : 8.0;
   const double lev = 1.0 / ((1 << d) - 1);  // levels below the finest, relative to it
-  double per = 24.0 + 2.0 * s;              // u, p, F and two work vectors
+  double per = 24.0 + 3.0 * s;              // u, p, F and three work vectors
+  if (mixed) per += 8.0;                    // stored outer residual
   per += (d == 2 ? 2.0 : 3.0) * s * lev;    // multigrid right-hand sides, iterates (and residuals)
   if (d != 2) per += 2.0 * s;               // generic path: level-0 iterate and residual
   if (d == 2 && !mixed) per += 8.0 * (1.0 + lev);  // cached Jacobi factors

@@ -161,6 +161,63 @@ __global__ void k_resid_u(const double* __restrict__ u, const double* __restrict
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// Mixed precision, first half of an iteration: the outer residual bres = F - K u - tau A_t u in
+// FP64 (stored, with its squared-norm partials), and the A~ input
+//   r_p = K u - tau A_t p - F = -bres - tau A_t (p + u)
+// whose second term is a stencil on w = p + u, a quantity that tends to zero, taken in FP32.
+template <int DIM>
+__global__ void k_resid_bres_mixed(const double* __restrict__ u, const double* __restrict__ p,
+                                   const double* __restrict__ F, double* __restrict__ bres,
+                                   float* __restrict__ rp, double* __restrict__ partials,
+                                   StencilGeom<double> g, const double* __restrict__ cth, double tau,
+                                   long long total, const int* done) {
+  if (stop_requested(done)) return;
+  double acc = 0.0;
+  const float tauf = (float)tau, h2f = (float)g.h2inv;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    double b = 0.0;
+    float r = 0.f;
+    if (decode<DIM>(i, g.logP, g.n, t, x, y, z)) {
+      double am[3], ap[3];
+      face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
+      const double uc = u[i];
+      const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
+      const double um = t > 0 ? u[i - g.S] : 0.0;
+      b = F[i] - (uc - um) - tau * Au;
+      acc += b * b;
+      const float wc = (float)(p[i] + uc);
+      long long off[3] = {1, g.P, (long long)g.P * g.P};
+      float aw = 0.f;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const float wm = (float)(p[i - off[d]] + u[i - off[d]]);
+        const float wp = (float)(p[i + off[d]] + u[i + off[d]]);
+        aw += (float)am[d] * (wc - wm) + (float)ap[d] * (wc - wp);
+      }
+      r = (float)(-b) - tauf * h2f * aw;
+    }
+    bres[i] = b;
+    rp[i] = r;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// Mixed precision, second residual without a stencil: r_u = bres - K^T (p + u)
+__global__ void k_resid_u_from_bres(const double* __restrict__ bres, const double* __restrict__ u,
+                                    const double* __restrict__ p, float* __restrict__ ru, long long S,
+                                    long long total, const int* done) {
+  if (stop_requested(done)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double next = i + S < total ? p[i + S] + u[i + S] : 0.0;
+    ru[i] = (float)(bres[i] - (p[i] + u[i]) + next);
+  }
+}
+
 template <int DIM, typename T>
 __global__ void k_apply_A_scaled(const T* __restrict__ z, T* __restrict__ out, StencilGeom<T> g,
                                  T cth, T scale, long long total, const int* done) {
@@ -330,6 +387,21 @@ void launch_resid_u(const double* u, const double* p, const double* F, Tp* ru, d
   const long long total = g.S * N;
   LaunchScope ls("resid_u", st, (24.0 + sizeof(Tp)) * dofs(g.dim, g.n, N));
   PT_DISPATCH_DIM(g.dim, k_resid_u<D, Tp><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, ru, partials, g, cth, tau, N, total, done));
+}
+
+void launch_resid_bres_mixed(const double* u, const double* p, const double* F, double* bres, float* rp,
+                             double* partials, StencilGeom<double> g, const double* cth, double tau, int N,
+                             const int* done, cudaStream_t st) {
+  const long long total = g.S * N;
+  LaunchScope ls("resid_bres", st, (24.0 + 8.0 + 4.0) * dofs(g.dim, g.n, N));
+  PT_DISPATCH_DIM(g.dim, k_resid_bres_mixed<D><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, bres, rp, partials, g, cth, tau, total, done));
+}
+
+void launch_resid_u_from_bres(const double* bres, const double* u, const double* p, float* ru, long long S,
+                              int N, int dim, int n, const int* done, cudaStream_t st) {
+  const long long total = S * N;
+  LaunchScope ls("resid_u_bres", st, (24.0 + 4.0) * dofs(dim, n, N));
+  k_resid_u_from_bres<<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done);
 }
 
 template <typename T>

@@ -106,6 +106,14 @@ void launch_resid_u(const double* u, const double* p, const double* F, Tp* ru, d
                     StencilGeom<double> g, const double* cth, double tau, int N, const int* done,
                     cudaStream_t st);
 
+// Mixed precision: bres = F - B u (FP64, stored, norm partials) and r_p = -bres - tau A_n (p + u)
+// with the second stencil in FP32; then r_u = bres - K^T (p + u) (no stencil).
+void launch_resid_bres_mixed(const double* u, const double* p, const double* F, double* bres, float* rp,
+                             double* partials, StencilGeom<double> g, const double* cth, double tau, int N,
+                             const int* done, cudaStream_t st);
+void launch_resid_u_from_bres(const double* bres, const double* u, const double* p, float* ru, long long S,
+                              int N, int dim, int n, const int* done, cudaStream_t st);
+
 // out = scale * A(cthbar) z on one batch (Abar apply of the Hhat block solve)
 template <typename T>
 void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale, int N,
@@ -214,6 +222,16 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
 template <typename T>
 void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
                         int logP, DstPlan<T> plan, const int* done, cudaStream_t st);
+
+// Spatial sine transforms of type I (kernels_dsti.cu), in place on padded slices:
+//   rows:  every x-line v <- S v;  cols: every line along axis 1 (y) or 2 (z) v <- S v, or with
+//   `scale`, v <- S diag(g) S v with g the exact block-solve factor c0 l / (mu_k + tau l)^2.
+// tw: e^{2 pi i k / (2(n+1))}, k < n + 1; lam: (4 a0 / h^2) sin^2(pi k h / 2), k = 1..n; mu: [B].
+template <typename T>
+void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const T* tw, cudaStream_t st);
+template <typename T>
+void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const T* tw,
+                      const double* lam, const double* mu, double tau, double c0, bool scale, cudaStream_t st);
 
 // Problem hooks for the serving loop (defined in capi.cu).
 pt_status problem_begin(pt_problem* p, double tol, int max_it);   // reset + captured iteration graph

@@ -112,7 +112,7 @@ def test_vcycle_preconditioners_match_oracle_vcycle(prob, precision, cycles):
     r = rng.standard_normal((prob.N, prob.ns))
     import paper_1802_08126_gb300 as ptu
     with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, S.source(prob), S.initial(prob),
-                     precision=precision, omega=0.5, n_vcycles=cycles) as P:
+                     precision=precision, omega=0.5, n_vcycles=cycles, h_solver="vcycle") as P:
         out = torch.empty_like(dev(r))
         P.precond_A(dev(r), out)
         ref = Asolve(r)
@@ -120,6 +120,24 @@ def test_vcycle_preconditioners_match_oracle_vcycle(prob, precision, cycles):
         P.precond_H(dev(r), out)
         ref = T.apply_Hinv(r, Hsolve)
         assert rel_err(host(out), ref) <= tol
+
+
+@pytest.mark.parametrize("prob", [S.heat2d_uniform(15, 8), S.heat2d_uniform(31, 12), S.heat2d_uniform(7, 2),
+                                  S.heat2d_uniform(63, 5)], ids=lambda p: p.name)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_exact_transform_H_matches_oracle_direct_solves(prob, precision):
+    """H~^-1 with exact H_k solves done by spatial sine transforms equals Phi^-1 Hhat^-1 Phi^-T
+    with sparse direct H_k solves (§4, eq. 4.4)."""
+    tol = 1e-11 if precision == "fp64" else 5e-6
+    T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal((prob.N, prob.ns))
+    import paper_1802_08126_gb300 as ptu
+    with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, S.source(prob), None, precision=precision,
+                     h_solver="exact") as P:
+        out = torch.empty_like(dev(r))
+        P.precond_H(dev(r), out)
+    assert rel_err(host(out), T.apply_Hinv(r, T.exact_H_solver())) <= tol
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -161,13 +179,19 @@ def test_heat1d_exact_solves_matches_oracle_and_mirror_history():
 
 @pytest.mark.parametrize("prob", [S.heat2d_uniform(31, 32), S.heat3d_bumps(7, 16), S.heat1d_mms(31, 16)],
                          ids=lambda p: p.name)
-def test_multigrid_solve_history_and_solution(prob):
+@pytest.mark.parametrize("hsol", ["vcycle", "exact"])
+def test_multigrid_solve_history_and_solution(prob, hsol):
+    if hsol == "exact" and prob.dim != 2:
+        pytest.skip("transform H_k solves are 2-D")
     f, u0 = S.source(prob), S.initial(prob)
     T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
     F = T.rhs(f, u0)
     Asolve, Hsolve = mg.st_vcycles(T)
+    if hsol == "exact":
+        Hsolve = T.exact_H_solver()
     _, _, hist_ref = T.uzawa(F, 0.5, 15, Asolve, lambda k, r: Hsolve(k, r))
-    with make(prob, omega=0.5) as P:
+    import paper_1802_08126_gb300 as ptu
+    with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, omega=0.5, h_solver=hsol) as P:
         _, it, hist = P.solve(0.0, 15)
         assert np.abs(hist - hist_ref).max() <= 1e-9 * hist_ref.max()
         u = np.zeros((prob.N, prob.ns))
