@@ -350,13 +350,22 @@ void enqueue_iteration(pt_problem* p) {
   T* W1 = (T*)p->W1;
   T* W2 = (T*)p->W2;
   const DstPlan<T> dp = dst_plan<T>(p);
-  if (p->mixed) {
+  if (p->bres && p->dim == 2 && p->lev[0].P >= 32) {
+    // outer residual first (and the convergence test), then the p-update and the stencil-free r_u
+    const Level& L0 = p->lev[0];
+    launch_resid_bres_2d<T>(p->u, p->p, p->F, p->bres, W1, p->partials, p->tab_d + L0.tab, p->tab_f + L0.tab,
+                            p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N, done, p->st);
+    launch_finalize_residual(p->partials, p->state, p->hist, p->st);
+    apply_precond_A<T>(p, W1, p->p, 1, 1, done);
+    launch_resid_u_from_bres<T>(p->bres, p->u, p->p, W1, L0.S, p->N, p->dim, p->n, done, p->st);
+  } else if (p->mixed) {
     // outer residual in FP64 first (and the convergence test), then the p-update and r_u
     launch_resid_bres_mixed(p->u, p->p, p->F, p->bres, (float*)W1, p->partials, g, p->cth_d, p->tau, p->N,
                             done, p->st);
     launch_finalize_residual(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->p, 1, 1, done);
-    launch_resid_u_from_bres(p->bres, p->u, p->p, (float*)W1, p->lev[0].S, p->N, p->dim, p->n, done, p->st);
+    launch_resid_u_from_bres<float>(p->bres, p->u, p->p, (float*)W1, p->lev[0].S, p->N, p->dim, p->n, done,
+                                    p->st);
   } else {
     launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, p->tau, p->N, done, p->st);
     apply_precond_A<T>(p, W1, p->p, 1, 1, done);
@@ -926,7 +935,8 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   if (!(p->u = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->p = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->F = alloc_padded<double>(p, L0, p->N, &st))) return st;
-  if (p->mixed && !(p->bres = alloc_padded<double>(p, L0, p->N, &st))) return st;
+  if ((p->mixed || (p->dim == 2 && L0.P >= 32)) && !(p->bres = alloc_padded<double>(p, L0, p->N, &st)))
+    return st;
   st = p->mixed ? setup_precision<float>(p) : setup_precision<double>(p);
   if (st != PT_OK) return st;
   if (!(p->partials = (double*)alloc_bytes(p, sizeof(double) * kReduceBlocks, &st))) return st;
@@ -1045,7 +1055,7 @@ size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o) {
   const double s = mixed ? 4.0 : 8.0;
   const double lev = 1.0 / ((1 << d) - 1);  // levels below the finest, relative to it
   double per = 24.0 + 3.0 * s;              // u, p, F and three work vectors
-  if (mixed) per += 8.0;                    // stored outer residual
+  if (mixed || d == 2) per += 8.0;          // stored outer residual
   per += (d == 2 ? 2.0 : 3.0) * s * lev;    // multigrid right-hand sides, iterates (and residuals)
   if (d != 2) per += 2.0 * s;               // generic path: level-0 iterate and residual
   if (d == 2 && !mixed) per += 8.0 * (1.0 + lev);  // cached Jacobi factors

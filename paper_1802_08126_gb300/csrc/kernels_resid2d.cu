@@ -1,0 +1,141 @@
+// 2-D residual kernels with a small FP64 instruction count (the FP64 rate of this GPU is 1/64 of
+// its FP32 rate, so these kernels are bound by FP64 instruction issue, not by memory).
+//
+// One pass forms, for every interior point of every step t,
+//   bres = F - (u_t - u_{t-1}) - tau A_t u_t          (outer residual F - B u, FP64, stored)
+//   r_p  = -bres - tau A_t (p_t + u_t)                 (= K u - tau A_t p - F, first line of eq. 3.1)
+// and the squared norm of bres; the second residual r_u = bres - K^T (p + u) is then a
+// stencil-free pass.  w = p + u tends to zero, so its stencil is taken in FP32 in the mixed-
+// precision form (the A~ input is rounded to FP32 anyway) and in FP64 in the plain form.
+//
+// Each warp sweeps a strip of kRows rows for 32 consecutive columns: the rows above and below
+// stay in registers, x-neighbours of w come from warp shuffles, and the face coefficients
+// (tau/h^2)(a0 + c g_t(t) g_x g_y) are one FMA each from per-row / per-column factors.
+#include "stencil_common.cuh"
+
+namespace pt {
+namespace {
+
+constexpr int kRows = 16;
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_resid_bres_2d(
+    const double* __restrict__ u, const double* __restrict__ p, const double* __restrict__ F,
+    double* __restrict__ bres, W* __restrict__ rp, double* __restrict__ partials,
+    const double* __restrict__ tab, const float* __restrict__ tabf, const double* __restrict__ cth,
+    double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, const int* done) {
+  if (stop_requested(done)) return;
+  const int P = 1 << logP;
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  // fixed grid (deterministic partial sums): each warp takes strips wg, wg + gridDim*8, ...
+  for (long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wg < nwarps;
+       wg += (long long)gridDim.x * (blockDim.x >> 5)) {
+    const int wx_count = P >> 5, strips = P / kRows;
+    const int wx = (int)(wg % wx_count);
+    const long long rest = wg / wx_count;
+    const int strip = (int)(rest % strips);
+    const int t = (int)(rest / strips);
+    const int x = (wx << 5) + lane;
+    const int y0 = strip * kRows;
+    const double* nx = tab;
+    const double* fx = tab + P;
+    const double* ny = tab + 2 * P;
+    const double* fy = tab + 3 * P;
+    const double ct = s_h2 * cth[t];  // (tau/h^2) c g_t(t_t)
+    const float a0f = (float)a0s, ctf = (float)ct;
+    const float* nxf = tabf;
+    const float* fxf = tabf + P;
+    const float* nyf = tabf + 2 * P;
+    const float* fyf = tabf + 3 * P;
+    const bool xin = x < n;
+    const double fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
+    const double gxc = ct * nx[x];
+    const float fxlf = fxf[x], fxrf = fxf[x + 1 < P ? x + 1 : x], gxcf = ctf * nxf[x];
+    const long long base = (long long)t * S + x;
+    auto at = [&](int y) { return base + (long long)y * P; };
+    // rows y0-1 and y0 of u and w
+    double u_m = u[at(y0) - P];
+    double u_c = u[at(y0)];
+    W w_m = (W)(p[at(y0) - P] + u_m);
+    W w_c = (W)(p[at(y0)] + u_c);
+    double ayl = fma(gxc, fy[y0], a0s);  // lower y-face of row y0
+    float aylf = fmaf(gxcf, fyf[y0], a0f);
+    for (int k = 0; k < kRows; ++k) {
+      const int y = y0 + k;
+      const bool yin = y < n;
+      double u_p = 0.0;
+      W w_p = (W)0;
+      if (y + 1 < P) {
+        u_p = u[at(y + 1)];
+        w_p = (W)(p[at(y + 1)] + u_p);
+      }
+      // x-neighbours of w from the neighbouring lanes; the two edge lanes compute theirs
+      W wW = __shfl_up_sync(0xffffffffu, w_c, 1);
+      W wE = __shfl_down_sync(0xffffffffu, w_c, 1);
+      if (lane == 0 && yin) wW = (W)(p[at(y) - 1] + u[at(y) - 1]);
+      if (lane == 31 && yin && x + 1 < P) wE = (W)(p[at(y) + 1] + u[at(y) + 1]);
+      const double ayu = fma(gxc, fy[y + 1 < P ? y + 1 : y], a0s);  // upper y-face
+      const float ayuf = fmaf(gxcf, fyf[y + 1 < P ? y + 1 : y], a0f);
+      double b = 0.0;
+      W r = (W)0;
+      if (xin && yin) {
+        const long long i = at(y);
+        const double gy = ct * ny[y];
+        const double axl = fma(gy, fxl, a0s), axr = fma(gy, fxr, a0s);
+        const double uW = u[i - 1], uE = u[i + 1];
+        const double um = t > 0 ? u[i - S] : 0.0;
+        const double su = axl * (u_c - uW) + axr * (u_c - uE) + ayl * (u_c - u_m) + ayu * (u_c - u_p);
+        b = F[i] - (u_c - um) - su;
+        acc = fma(b, b, acc);
+        W sw;
+        if (sizeof(W) == 4) {
+          const float gyf = ctf * nyf[y];
+          const float axlf = fmaf(gyf, fxlf, a0f), axrf = fmaf(gyf, fxrf, a0f);
+          sw = (W)(axlf * ((float)w_c - (float)wW) + axrf * ((float)w_c - (float)wE) +
+                   aylf * ((float)w_c - (float)w_m) + ayuf * ((float)w_c - (float)w_p));
+        } else {
+          sw = (W)(axl * ((double)w_c - (double)wW) + axr * ((double)w_c - (double)wE) +
+                   ayl * ((double)w_c - (double)w_m) + ayu * ((double)w_c - (double)w_p));
+        }
+        r = (W)(-b) - sw;
+      }
+      if (y < P) {
+        bres[at(y)] = b;
+        rp[at(y)] = r;
+      }
+      u_m = u_c;
+      u_c = u_p;
+      w_m = w_c;
+      w_c = w_p;
+      ayl = ayu;
+      aylf = ayuf;
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+}  // namespace
+
+template <typename W>
+void launch_resid_bres_2d(const double* u, const double* p, const double* F, double* bres, W* rp,
+                          double* partials, const double* tab, const float* tabf, const double* cth, double a0,
+                          double tau, double h, int n, int logP, long long S, int N, const int* done,
+                          cudaStream_t st) {
+  const int P = 1 << logP;
+  const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
+  const double s_h2 = tau / (h * h);
+  LaunchScope ls("resid_bres", st, (24.0 + 8.0 + sizeof(W)) * (double)n * n * N);
+  k_resid_bres_2d<W><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth, s_h2 * a0,
+                                                       s_h2, n, logP, S, N, nwarps, done);
+}
+
+template void launch_resid_bres_2d<float>(const double*, const double*, const double*, double*, float*, double*,
+                                          const double*, const float*, const double*, double, double, double, int,
+                                          int, long long, int, const int*, cudaStream_t);
+template void launch_resid_bres_2d<double>(const double*, const double*, const double*, double*, double*, double*,
+                                           const double*, const float*, const double*, double, double, double, int,
+                                           int, long long, int, const int*, cudaStream_t);
+
+}  // namespace pt

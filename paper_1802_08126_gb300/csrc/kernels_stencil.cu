@@ -206,15 +206,16 @@ __global__ void k_resid_bres_mixed(const double* __restrict__ u, const double* _
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Mixed precision, second residual without a stencil: r_u = bres - K^T (p + u)
+// Second residual without a stencil: r_u = bres - K^T (p + u)
+template <typename Tp>
 __global__ void k_resid_u_from_bres(const double* __restrict__ bres, const double* __restrict__ u,
-                                    const double* __restrict__ p, float* __restrict__ ru, long long S,
+                                    const double* __restrict__ p, Tp* __restrict__ ru, long long S,
                                     long long total, const int* done) {
   if (stop_requested(done)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const double next = i + S < total ? p[i + S] + u[i + S] : 0.0;
-    ru[i] = (float)(bres[i] - (p[i] + u[i]) + next);
+    ru[i] = (Tp)(bres[i] - (p[i] + u[i]) + next);
   }
 }
 
@@ -397,12 +398,17 @@ void launch_resid_bres_mixed(const double* u, const double* p, const double* F, 
   PT_DISPATCH_DIM(g.dim, k_resid_bres_mixed<D><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, bres, rp, partials, g, cth, tau, total, done));
 }
 
-void launch_resid_u_from_bres(const double* bres, const double* u, const double* p, float* ru, long long S,
+template <typename Tp>
+void launch_resid_u_from_bres(const double* bres, const double* u, const double* p, Tp* ru, long long S,
                               int N, int dim, int n, const int* done, cudaStream_t st) {
   const long long total = S * N;
-  LaunchScope ls("resid_u_bres", st, (24.0 + 4.0) * dofs(dim, n, N));
-  k_resid_u_from_bres<<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done);
+  LaunchScope ls("resid_u_bres", st, (24.0 + sizeof(Tp)) * dofs(dim, n, N));
+  k_resid_u_from_bres<Tp><<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done);
 }
+template void launch_resid_u_from_bres<float>(const double*, const double*, const double*, float*, long long, int,
+                                              int, int, const int*, cudaStream_t);
+template void launch_resid_u_from_bres<double>(const double*, const double*, const double*, double*, long long, int,
+                                               int, int, const int*, cudaStream_t);
 
 template <typename T>
 void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale, int N,
