@@ -76,9 +76,10 @@ struct pt_problem {
   void* W3 = nullptr;                           // residual between V-cycles of an H_k solve
   double* bres = nullptr;                       // F - B u of the current iterate (mixed precision)
   bool hdst = false;                            // exact H_k solves by spatial sine transforms
-  void* dsti_tw = nullptr;                      // [n+1] complex e^{2 pi i k / (2(n+1))}
-  double* dsti_lam = nullptr;                   // [n] (4 a0/h^2) sin^2(pi k h / 2)
-  double* dsti_mu = nullptr;                    // [N] mu_k
+  void* dsti_tw = nullptr;                      // [n+1] complex e^{-2 pi i e / (n+1)}   (type T)
+  void* dsti_sn = nullptr;                      // [(n+1)/2 + 1] sin(pi j / (n+1)) / 2
+  void* dsti_lam = nullptr;                     // [n+1] (4 a0/h^2) sin^2(pi k h / 2) at k-1, 0 at n
+  void* dsti_mu = nullptr;                      // [N] mu_k
   int nv_h = 2;                                 // V-cycles per H_k solve
   void* mg_b[kMaxLevels] = {};
   void* mg_x[kMaxLevels] = {};
@@ -327,10 +328,10 @@ T* block_solve(pt_problem* p, const int* done) {
   if (p->hdst) {
     const Level& L = p->lev[0];
     const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
-    launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, (const T*)p->dsti_tw, p->st);
-    launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, (const T*)p->dsti_tw, p->dsti_lam, p->dsti_mu,
+    launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
+    launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_lam, p->dsti_mu,
                         p->tau, c0, true, p->st);
-    launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, (const T*)p->dsti_tw, p->st);
+    launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
     return W1;
   }
   apply_Hk_solve<T>(p, W1, W2, done);
@@ -727,27 +728,31 @@ pt_status setup_precision(pt_problem* p) {
     }
   }
   // exact H_k solves by spatial sine transforms (constant reference coefficient, 2-D)
-  p->hdst = !p->exact1d && p->dim == 2 && !p->hvar && p->opt.h_solver != 1;
+  p->hdst = !p->exact1d && p->dim == 2 && !p->hvar && p->opt.h_solver != 1 && p->n + 1 <= kDstiMaxM;
   if (p->hdst) {
     const int M = p->n + 1;
-    std::vector<double> tw(2 * M), lam(p->n), mud(mu.begin(), mu.end());
-    for (int k = 0; k < M; ++k) {
-      tw[2 * k] = std::cos(M_PI * k / M);  // e^{2 pi i k / (2M)}
-      tw[2 * k + 1] = std::sin(M_PI * k / M);
+    std::vector<double> tw(2 * M), sn(M / 2 + 1), lam(M, 0.0), mud(mu.begin(), mu.end());
+    for (int e = 0; e < M; ++e) {
+      tw[2 * e] = std::cos(2.0 * M_PI * e / M);  // e^{-2 pi i e / M}
+      tw[2 * e + 1] = -std::sin(2.0 * M_PI * e / M);
     }
+    for (int j = 0; j <= M / 2; ++j) sn[j] = 0.5 * std::sin(M_PI * j / M);
     const double h = 1.0 / M;
     for (int k = 1; k <= p->n; ++k) {
-      const double sn = std::sin(M_PI * k * h / 2.0);
-      lam[k - 1] = 4.0 * p->coeff.a0 / (h * h) * sn * sn;
+      const double s = std::sin(M_PI * k * h / 2.0);
+      lam[k - 1] = 4.0 * p->coeff.a0 / (h * h) * s * s;
     }
     if (!(p->dsti_tw = alloc_bytes(p, sizeof(T) * tw.size(), &st))) return st;
-    if (!(p->dsti_lam = (double*)alloc_bytes(p, sizeof(double) * lam.size(), &st))) return st;
-    if (!(p->dsti_mu = (double*)alloc_bytes(p, sizeof(double) * mud.size(), &st))) return st;
+    if (!(p->dsti_sn = alloc_bytes(p, sizeof(T) * sn.size(), &st))) return st;
+    if (!(p->dsti_lam = alloc_bytes(p, sizeof(T) * lam.size(), &st))) return st;
+    if (!(p->dsti_mu = alloc_bytes(p, sizeof(T) * mud.size(), &st))) return st;
     if ((st = upload<T>(p, p->dsti_tw, tw)) != PT_OK) return st;
-    if ((st = upload<double>(p, p->dsti_lam, lam)) != PT_OK) return st;
-    if ((st = upload<double>(p, p->dsti_mu, mud)) != PT_OK) return st;
+    if ((st = upload<T>(p, p->dsti_sn, sn)) != PT_OK) return st;
+    if ((st = upload<T>(p, p->dsti_lam, lam)) != PT_OK) return st;
+    if ((st = upload<T>(p, p->dsti_mu, mud)) != PT_OK) return st;
   } else if (p->opt.h_solver == 2) {
-    return fail(PT_EINVAL, "exact H_k solves need dim == 2 and a reference coefficient constant in space");
+    return fail(PT_EINVAL,
+                "exact H_k solves need dim == 2, n + 1 <= 4096 and a reference coefficient constant in space");
   }
   // FP64 2-D: cache w / D of every tau A_n (a division per point per smoothing step otherwise)
   if (!p->exact1d && p->dim == 2 && sizeof(T) == 8) {

@@ -1,256 +1,412 @@
 // Exact spatial solves for the Schur preconditioner when the reference operator has a constant
 // coefficient (Abar = a0 L_h, L_h the finite-difference Laplacian).  The sine transform of type I
-// along each axis, (S v)_k = sum_{j=1}^{n} v_j sin(pi j k / (n+1)), diagonalises L_h with
-// eigenvalues (4/h^2) sum_d sin^2(pi k_d h / 2) and satisfies S S = ((n+1)/2) I.  Hence the block
+// along each axis, (S v)_k = sum_{j=1}^{n} v_j sin(pi j k / M), M = n + 1, diagonalises L_h with
+// eigenvalues (4/h^2) sum_d sin^2(pi k_d h / 2) and satisfies S S = (M/2) I.  Hence the block
 // solve of §4, eq. 4.4,
 //     Hhat_k^-1 = (2 tau / N) H_k^-1 Abar H_k^-1,  H_k = mu_k I + tau Abar,
 // is, in the doubly transformed basis, the point-wise factor
-//     (2 tau / N) (2/(n+1))^d a0 l / (mu_k + tau a0 l)^2,   l = the eigenvalue of L_h,
+//     (2 tau / N) (2/M)^d a0 l / (mu_k + tau a0 l)^2,   l = the eigenvalue of L_h,
 // between two spatial transforms (this is the exact H of eq. 4.4, gamma = Gamma = 1 in eq. 4.7).
 //
-// Each 1-D transform is computed through one complex FFT of length 2(n+1) of the odd extension
-// [0, v_1 .. v_n, 0, -v_n .. -v_1], whose spectrum is -2i (S v); two real lines share one complex
-// transform (real and imaginary parts).  Rows (x) are contiguous; columns (y, z) are strided by
-// the pitch and are handled as tiles of consecutive columns, like the temporal transform.
+// One DST-I of length n costs one real DFT of length M instead of the 2M of the odd extension:
+// with x_0 = x_M = 0 and s_j = sin(pi j / M), the sequence
+//     y_j = s_j (x_j + x_{M-j}) + (x_j - x_{M-j}) / 2,   j = 0 .. M-1,
+// has the real DFT Y_k = R_k + i I_k (e^{-2 pi i j k / M} convention) with
+//     S_{2k} = -I_k,   S_{2k+1} = S_{2k-1} + R_k,   S_1 = R_0 / 2
+// (the symmetric part of y pairs with the cosines, the antisymmetric part with the sines; the
+// odd outputs are a prefix sum over k).  Two real lines share one complex FFT of length M, and
+// each pair of lines is handled by one warp: radix-8 / 4 / 2 Stockham passes through a padded
+// shared-memory ping-pong pair, the prefix sum as a chunked warp scan.
 #include "fft_common.cuh"
 
 namespace pt {
 namespace {
 
-struct DstIArgs {
-  int n, M, logM2;   // interior points, M = n + 1, log2(2M)
-  int dim;
-  long long S;       // slice stride
-  long long stride;  // element distance between consecutive points along the transformed axis
-  int nlines_slice;  // lines of one slice along this axis (including ghost lines)
-};
+constexpr int kWarpsMax = 8;
 
-// odd extension of line pair (a, b) into column c of the FFT buffer (length 2M, stride L)
-template <typename T, typename T2>
-__device__ __forceinline__ void put_odd(T2* col, int M, int j, T va, T vb) {
-  T2 v, w;
-  v.x = va;
-  v.y = vb;
-  w.x = -va;
-  w.y = -vb;
-  col[j + 1] = v;          // v_{j+1} at position j+1
-  col[2 * M - 1 - j] = w;  // -v_{j+1} at position 2M - (j+1)
+// padded shared-memory index: one spare element per 8 keeps radix-8 strided writes conflict-free
+__device__ __forceinline__ int pd(int e) { return e + (e >> 3); }
+__host__ __device__ constexpr int padded_len(int M) { return M + (M >> 3) + 1; }
+
+template <typename T2>
+__device__ __forceinline__ T2 mk(decltype(T2::x) x, decltype(T2::x) y) {
+  T2 r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename T2>
+__device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
+template <typename T2>
+__device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 w) {
+  return mk<T2>(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+template <typename T2>
+__device__ __forceinline__ T2 mul_mi(T2 a) { return mk<T2>(a.y, -a.x); }  // a * (-i)
+
+// forward DFTs of length 2, 4, 8 in registers, natural order in and out (omega_R = e^{-2 pi i/R})
+template <typename T2>
+__device__ __forceinline__ void dft2(T2* u) {
+  const T2 a = u[0];
+  u[0] = cadd(a, u[1]);
+  u[1] = csub(a, u[1]);
+}
+template <typename T2>
+__device__ __forceinline__ void dft4(T2& u0, T2& u1, T2& u2, T2& u3) {
+  const T2 s02 = cadd(u0, u2), d02 = csub(u0, u2), s13 = cadd(u1, u3), d13 = mul_mi(csub(u1, u3));
+  u0 = cadd(s02, s13);
+  u2 = csub(s02, s13);
+  u1 = cadd(d02, d13);
+  u3 = csub(d02, d13);
+}
+template <typename T2>
+__device__ __forceinline__ void dft8(T2* u) {
+  using T = decltype(T2::x);
+  const T r = (T)0.70710678118654752440;  // 1/sqrt(2)
+  T2 e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
+  T2 o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
+  dft4(e0, e1, e2, e3);
+  dft4(o0, o1, o2, o3);
+  o1 = mk<T2>((o1.x + o1.y) * r, (o1.y - o1.x) * r);   // * e^{-i pi/4}
+  o2 = mul_mi(o2);                                       // * e^{-i pi/2}
+  o3 = mk<T2>((o3.y - o3.x) * r, -(o3.x + o3.y) * r);  // * e^{-3 i pi/4}
+  u[0] = cadd(e0, o0);
+  u[4] = csub(e0, o0);
+  u[1] = cadd(e1, o1);
+  u[5] = csub(e1, o1);
+  u[2] = cadd(e2, o2);
+  u[6] = csub(e2, o2);
+  u[3] = cadd(e3, o3);
+  u[7] = csub(e3, o3);
+}
+template <int LR, typename T2>
+__device__ __forceinline__ void dftR(T2* u) {
+  if (LR == 1) dft2(u);
+  if (LR == 2) dft4(u[0], u[1], u[2], u[3]);
+  if (LR == 3) dft8(u);
 }
 
-// rows along x, in place: v <- S v for every (slice, y, z) line
-template <typename T>
-__global__ void k_dsti_rows(T* x, DstIArgs a, const typename Vec2<T>::type* __restrict__ tw, int C,
-                            long long nlines) {
-  using T2 = typename Vec2<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* buf = (T2*)smem_raw;
-  const int L = 2 * a.M + 1;
-  const long long line0 = (long long)blockIdx.x * 2 * C;
-  const int P = a.M;
-  for (int idx = threadIdx.x; idx < C * a.n; idx += blockDim.x) {
-    const int c = idx / a.n, j = idx - c * a.n;
-    const long long la = line0 + 2 * c, lb = la + 1;
-    const T va = la < nlines ? x[la * P + j] : (T)0;
-    const T vb = lb < nlines ? x[lb * P + j] : (T)0;
-    put_odd<T, T2>(buf + (size_t)c * L, a.M, j, va, vb);
-  }
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    T2 z;
-    z.x = (T)0;
-    z.y = (T)0;
-    buf[(size_t)c * L] = z;
-    buf[(size_t)c * L + a.M] = z;
-  }
-  __syncthreads();
-  dif_fft<T, T2>(buf, C, L, 2 * a.M, a.logM2, tw, (T)-1);
-  // (S v_a)_k = -Im C_k / 2, (S v_b)_k = Re C_k / 2; the ghost entry (and ghost lines) stay zero
-  for (int idx = threadIdx.x; idx < C * P; idx += blockDim.x) {
-    const int c = idx / P, k = idx - c * P;
-    const long long la = line0 + 2 * c, lb = la + 1;
-    T ya = (T)0, yb = (T)0;
-    if (k < a.n) {
-      const T2 v = buf[(size_t)c * L + bitrev(k + 1, a.logM2)];
-      ya = (T)-0.5 * v.y;
-      yb = (T)0.5 * v.x;
+// One Stockham (autosort) radix-2^LR pass of a length-M = 2^logM FFT, after passes of total
+// radix p = 2^s: butterfly i reads in[i + m M/R], twiddles input m by omega_{pR}^{m k}
+// (k = i mod p), and writes out[(i - k) R + k + m p].  tw[e] = e^{-2 pi i e / M}.
+template <int LR, typename T2>
+__device__ __forceinline__ void stockham_pass(const T2* __restrict__ in, T2* __restrict__ out, int logM, int s,
+                                              const T2* __restrict__ tw, int lane) {
+  constexpr int R = 1 << LR;
+  const int nb = 1 << (logM - LR);
+  const int p = 1 << s;
+  const int tsh = logM - s - LR;
+  for (int i = lane; i < nb; i += 32) {
+    const int k = i & (p - 1);
+    T2 u[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) u[m] = in[pd(i + m * nb)];
+    if (s > 0) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) u[m] = cmul(u[m], __ldg(&tw[(m * k) << tsh]));
     }
-    const int ga = (int)(la % a.nlines_slice), gb = (int)(lb % a.nlines_slice);
-    // line index within a slice: y (2-D) or z*P + y (3-D); ghost when y == n or z == n
-    auto ghost = [&](int li) { return (li % P) == a.n || (a.dim == 3 && (li / P) == a.n); };
-    if (la < nlines) x[la * P + k] = ghost(ga) ? (T)0 : ya;
-    if (lb < nlines) x[lb * P + k] = ghost(gb) ? (T)0 : yb;
+    dftR<LR>(u);
+    const int j = ((i - k) << LR) + k;
+#pragma unroll
+    for (int m = 0; m < R; ++m) out[pd(j + m * p)] = u[m];
   }
 }
 
-// Columns along a strided axis: v <- S v; with `scale`, v <- S diag(g) S v where g is the exact
-// block solve factor of the header comment (computed from the frequencies of all axes).
-struct ScaleArgs {
-  int enabled;
-  const double* lam;   // [n] (4 a0 / h^2) sin^2(pi k h / 2), k = 1..n (x, y and z share it)
-  const double* mu;    // [N] mu_k of the temporal basis
-  double tau;          // reference step
-  double c0;           // (2 tau / N) (2 / M)^d
-};
+// FFT of the warp's sequence in `a` (padded, natural order); `b` is scratch.  Returns the buffer
+// holding the spectrum (natural order).
+template <typename T2>
+__device__ __forceinline__ T2* warp_fft(T2* a, T2* b, int logM, const T2* __restrict__ tw, int lane) {
+  int s = 0;
+  while (s < logM) {
+    const int rem = logM - s;
+    if (rem >= 5 || rem == 3) {
+      stockham_pass<3>(a, b, logM, s, tw, lane);
+      s += 3;
+    } else if (rem == 4 || rem == 2) {
+      stockham_pass<2>(a, b, logM, s, tw, lane);
+      s += 2;
+    } else {
+      stockham_pass<1>(a, b, logM, s, tw, lane);
+      s += 1;
+    }
+    __syncwarp();
+    T2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
 
-template <typename T>
-__global__ void k_dsti_cols(T* x, DstIArgs a, ScaleArgs sc, const typename Vec2<T>::type* __restrict__ tw,
-                            int C) {
-  using T2 = typename Vec2<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = 2 * a.M + 1;
-  T2* buf = (T2*)smem_raw;
-  T2* buf2 = buf + (size_t)C * L;  // second buffer for the transform back (scale mode)
-  const int P = a.M;
-  const int slice = blockIdx.y;
-  // the 2C columns of this block: consecutive indices within the plane orthogonal to the axis
-  const long long col0 = (long long)blockIdx.x * 2 * C;
-  // column q -> base offset within the slice: for the y axis (stride P) q = z*P + x, for the z
-  // axis (stride P^2) q = y*P + x
-  auto col_base = [&](long long q) -> long long {
-    if (a.stride == P) return (q / P) * (long long)P * P + (q % P);  // y axis: plane z, column x
-    return q;                                                          // z axis: q = y*P + x
+// z_j = (y^a_j + i y^b_j) / 2 from x_j = read(j - 1) (position j-1 holds x_j, x_0 = x_M = 0);
+// sn[j] = sin(pi j / M) / 2 for j <= M/2.
+template <typename T, typename T2, typename Read>
+__device__ __forceinline__ void dsti_pre(T2* z, int M, const T* __restrict__ sn, int lane, Read read) {
+  const int H = M >> 1;
+  for (int j = lane; j <= H; j += 32) {
+    if (j == 0) {
+      z[0] = mk<T2>((T)0, (T)0);
+      continue;
+    }
+    const T2 xj = read(j - 1), xm = read(M - j - 1);
+    const T s = sn[j];
+    const T Aa = xj.x + xm.x, Ab = xj.y + xm.y;
+    const T Da = (T)0.25 * (xj.x - xm.x), Db = (T)0.25 * (xj.y - xm.y);
+    z[pd(j)] = mk<T2>(fma(s, Aa, Da), fma(s, Ab, Db));
+    if (j != H) z[pd(M - j)] = mk<T2>(fma(s, Aa, -Da), fma(s, Ab, -Db));
+  }
+}
+
+// From the spectrum Z of the packed pair: write(pos, (S^a, S^b)) for every position 0 .. M-1
+// (S_q at position q-1, the ghost position M-1 gets 0).
+template <typename T, typename T2, typename Write>
+__device__ __forceinline__ void dsti_post(const T2* Z, int M, int lane, Write write) {
+  const int H = M >> 1;
+  const int K = H >= 32 ? H >> 5 : 1;  // k's per lane, contiguous
+  const int k0 = lane * K;
+  const bool act = k0 < H;
+  // contributions to the odd outputs: c_0 = R_0 / 2, c_k = R_k (the 1/2 of the pair split is in z)
+  auto contrib = [&](int k) -> T2 {
+    const T2 zk = Z[pd(k)];
+    if (k == 0) return zk;
+    const T2 zm = Z[pd(M - k)];
+    return mk<T2>(zk.x + zm.x, zk.y + zm.y);
   };
-  const long long sbase = (long long)slice * a.S;
-  for (int idx = threadIdx.x; idx < C * a.n; idx += blockDim.x) {
-    const int j = idx / C, c = idx - j * C;  // c fastest: consecutive columns, coalesced
-    const long long qa = col0 + 2 * c;
-    const T va = x[sbase + col_base(qa) + (long long)j * a.stride];
-    const T vb = x[sbase + col_base(qa + 1) + (long long)j * a.stride];
-    put_odd<T, T2>(buf + (size_t)c * L, a.M, j, va, vb);
-  }
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    T2 z;
-    z.x = (T)0;
-    z.y = (T)0;
-    buf[(size_t)c * L] = z;
-    buf[(size_t)c * L + a.M] = z;
-    if (sc.enabled) {
-      buf2[(size_t)c * L] = z;
-      buf2[(size_t)c * L + a.M] = z;
+  T ta = (T)0, tb = (T)0;
+  if (act) {
+    for (int q = 0; q < K; ++q) {
+      const T2 c = contrib(k0 + q);
+      ta += c.x;
+      tb += c.y;
     }
+  }
+  // warp inclusive scan of the chunk totals
+  T ia = ta, ib = tb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T va = __shfl_up_sync(0xffffffffu, ia, o);
+    const T vb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += va;
+      ib += vb;
+    }
+  }
+  if (!act) return;
+  T pa = ia - ta, pb = ib - tb;
+  for (int q = 0; q < K; ++q) {
+    const int k = k0 + q;
+    const T2 c = contrib(k);
+    pa += c.x;
+    pb += c.y;
+    write(2 * k, mk<T2>(pa, pb));  // S_{2k+1}
+    if (k == 0) {
+      write(M - 1, mk<T2>((T)0, (T)0));
+    } else {
+      const T2 zk = Z[pd(k)], zm = Z[pd(M - k)];
+      write(2 * k - 1, mk<T2>(zm.y - zk.y, zk.x - zm.x));  // S_{2k} = -I_k
+    }
+  }
+}
+
+// 1 / d for d > 0 in FP64: single-precision reciprocal and one Newton-Raphson step
+// r <- r (2 - d r), relative error about 1e-14 (the square of the single-precision error).
+__device__ __forceinline__ double recip_pos(double d) {
+  const double r = (double)__frcp_rn((float)d);
+  return fma(r, fma(-d, r, 1.0), r);
+}
+__device__ __forceinline__ float recip_pos(float d) { return __frcp_rn(d); }
+
+template <typename T>
+struct DstiTabs {
+  const typename Vec2<T>::type* tw;  // [M]   e^{-2 pi i e / M}
+  const T* sn;                       // [M/2 + 1] sin(pi j / M) / 2
+  const T* lam;                      // [M]   (4 a0 / h^2) sin^2(pi (pos+1) h / 2), 0 at the ghost
+  const T* mu;                       // [N]   mu_k
+};
+
+// Rows (x, contiguous): every line pair of every slice, in place.  Lines 2q and 2q+1.
+template <typename T>
+__global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x, int logM, int dim,
+                                                              long long npairs, DstiTabs<T> tb) {
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = 1 << logM;
+  const int W = padded_len(M);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  T2* A = (T2*)smem_raw + (size_t)warp * (2 * W + 1);
+  T2* B = A + W;
+  for (long long pr = (long long)blockIdx.x * wpb + warp; pr < npairs; pr += (long long)gridDim.x * wpb) {
+    const long long la = 2 * pr;
+    T* xa = x + la * M;
+    T* xb = xa + M;
+    dsti_pre<T, T2>(A, M, tb.sn, lane, [&](int pos) { return mk<T2>(xa[pos], xb[pos]); });
+    __syncwarp();
+    T2* Z = warp_fft<T2>(A, B, logM, tb.tw, lane);
+    T2* O = Z == A ? B : A;
+    dsti_post<T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
+    __syncwarp();
+    // ghost lines: y == n (2-D and 3-D) or z == n (3-D)
+    auto ghost = [&](long long l) {
+      const long long y = l & (M - 1);
+      return y == M - 1 || (dim == 3 && ((l >> logM) & (M - 1)) == M - 1);
+    };
+    const bool ga = ghost(la), gb = ghost(la + 1);
+    for (int pos = lane; pos < M; pos += 32) {
+      const T2 v = O[pd(pos)];
+      xa[pos] = ga ? (T)0 : v.x;
+      xb[pos] = gb ? (T)0 : v.y;
+    }
+    __syncwarp();
+  }
+}
+
+// Columns along a strided axis (1: y, stride M; 2: z, stride M^2), in place.  A block takes 2C
+// consecutive columns (x .. x + 2C - 1) of one plane of one slice; warp w transforms columns
+// 2w, 2w+1.  With `scale`, the column pair gets S diag(g) S, g the exact block-solve factor.
+template <typename T>
+__global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x, int logM, int dim, int axis,
+                                                              long long S, int scale, T tau, T c0,
+                                                              DstiTabs<T> tb) {
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = 1 << logM;
+  const int W = padded_len(M);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int C = blockDim.x >> 5;
+  const int tiles_x = M / (2 * C);
+  const int tx = blockIdx.x % tiles_x;
+  const int o = blockIdx.x / tiles_x;  // other in-plane coordinate (3-D), 0 in 2-D
+  const int slice = blockIdx.y;
+  const long long stride = axis == 1 ? (long long)M : (long long)M * M;
+  const int x0 = tx * 2 * C;
+  // column base: y axis -> o = z, z axis -> o = y
+  const long long base = (long long)slice * S + (axis == 1 ? (long long)o * M * M : (long long)o * M) + x0;
+  T2* bufs = (T2*)smem_raw;
+  auto bufA = [&](int w) { return bufs + (size_t)w * (2 * W + 1); };
+  // load the tile (columns fastest, coalesced); position M-1 is never read by the transform
+  for (int idx = threadIdx.x; idx < 2 * C * (M - 1); idx += blockDim.x) {
+    const int pos = idx / (2 * C), c = idx - pos * 2 * C;
+    ((T*)(bufA(c >> 1) + pd(pos)))[c & 1] = x[base + pos * stride + c];
   }
   __syncthreads();
-  dif_fft<T, T2>(buf, C, L, 2 * a.M, a.logM2, tw, (T)-1);
-  T2* out = buf;
-  if (sc.enabled) {
-    // spectrum -> scaled odd extension in buf2 -> transform again
-    const double mu = sc.mu[slice];
-    for (int idx = threadIdx.x; idx < C * a.n; idx += blockDim.x) {
-      const int c = idx / a.n, k = idx - c * a.n;
-      const T2 v = buf[(size_t)c * L + bitrev(k + 1, a.logM2)];
-      const long long qa = col0 + 2 * c;
-      T g[2];
-      for (int s = 0; s < 2; ++s) {
-        const long long q = qa + s;
-        const int cx = (int)(q % P);
-        const int cy = (int)(q / P);  // y index (z-axis pass) or z index (y-axis pass, 3-D)
-        double l = (cx < a.n ? sc.lam[cx] : 0.0) + sc.lam[k];
-        if (a.dim == 3) l += cy < a.n ? sc.lam[cy] : 0.0;
-        const bool ghost = cx >= a.n || (a.dim == 3 && cy >= a.n);
-        const double d = mu + sc.tau * l;
-        g[s] = ghost ? (T)0 : (T)(sc.c0 * l / (d * d));
-      }
-      put_odd<T, T2>(buf2 + (size_t)c * L, a.M, k, (T)-0.5 * v.y * g[0], (T)0.5 * v.x * g[1]);
-    }
-    __syncthreads();
-    dif_fft<T, T2>(buf2, C, L, 2 * a.M, a.logM2, tw, (T)-1);
-    out = buf2;
+  T2* A = bufA(warp);
+  T2* B = A + W;
+  const int xa = x0 + 2 * warp;
+  const bool ghost_o = dim == 3 && o == M - 1;
+  dsti_pre<T, T2>(B, M, tb.sn, lane, [&](int pos) { return A[pd(pos)]; });
+  __syncwarp();
+  T2* Z = warp_fft<T2>(B, A, logM, tb.tw, lane);
+  T2* O = Z == A ? B : A;
+  if (scale) {
+    // g = c0 l / (mu + tau l)^2, l = lam_x + lam_axis (+ lam_y in 3-D); 0 on ghost columns
+    const T mu = tb.mu[slice];
+    const T lo = dim == 3 ? tb.lam[o] : (T)0;
+    const T la = tb.lam[xa] + lo, lb = tb.lam[xa + 1] + lo;
+    const bool za = xa == M - 1 || ghost_o, zb = xa + 1 == M - 1 || ghost_o;
+    dsti_post<T, T2>(Z, M, lane, [&](int pos, T2 v) {
+      const T ly = tb.lam[pos];
+      const T l1 = la + ly, l2 = lb + ly;
+      const T r1 = recip_pos(fma(tau, l1, mu)), r2 = recip_pos(fma(tau, l2, mu));
+      const T g1 = za ? (T)0 : c0 * l1 * r1 * r1, g2 = zb ? (T)0 : c0 * l2 * r2 * r2;
+      O[pd(pos)] = mk<T2>(v.x * g1, v.y * g2);
+    });
+    __syncwarp();
+    T2* P2 = O == A ? B : A;
+    dsti_pre<T, T2>(P2, M, tb.sn, lane, [&](int pos) { return O[pd(pos)]; });
+    __syncwarp();
+    T2* Z2 = warp_fft<T2>(P2, O, logM, tb.tw, lane);
+    T2* O2 = Z2 == A ? B : A;
+    dsti_post<T, T2>(Z2, M, lane, [&](int pos, T2 v) { O2[pd(pos)] = v; });
+    O = O2;
+  } else {
+    dsti_post<T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
   }
-  for (int idx = threadIdx.x; idx < C * P; idx += blockDim.x) {
-    const int k = idx / C, c = idx - k * C;
-    const long long qa = col0 + 2 * c;
-    T ya = (T)0, yb = (T)0;
-    if (k < a.n) {
-      const T2 v = out[(size_t)c * L + bitrev(k + 1, a.logM2)];
-      ya = (T)-0.5 * v.y;
-      yb = (T)0.5 * v.x;
-    }
-    auto gh = [&](long long q) {
-      const int cx = (int)(q % P), cy = (int)(q / P);
-      return cx >= a.n || (a.dim == 3 && cy >= a.n);
-    };
-    x[sbase + col_base(qa) + (long long)k * a.stride] = gh(qa) ? (T)0 : ya;
-    x[sbase + col_base(qa + 1) + (long long)k * a.stride] = gh(qa + 1) ? (T)0 : yb;
+  // every warp's result sits in the same one of its two buffers
+  const int off = (int)(O - A);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 2 * C * M; idx += blockDim.x) {
+    const int pos = idx / (2 * C), c = idx - pos * 2 * C;
+    const int xc = x0 + c;
+    const bool gh = xc == M - 1 || ghost_o || pos == M - 1;
+    const T v = ((const T*)(bufA(c >> 1) + off + pd(pos)))[c & 1];
+    x[base + pos * stride + c] = gh ? (T)0 : v;
   }
 }
 
 template <typename T>
-int lines_per_block(int M, int max_bytes) {
-  const long long bytes = (long long)(2 * M + 1) * 2 * sizeof(T);
-  long long C = max_bytes / bytes;
-  if (C < 1) C = 1;
-  if (C > 16) C = 16;
-  long long pw = 1;
-  while (pw * 2 <= C) pw *= 2;
-  return (int)pw;
+int warps_for(int M) {
+  const size_t per = (size_t)(2 * padded_len(M) + 1) * 2 * sizeof(T);
+  int w = (int)((200u * 1024u) / per);
+  if (w > kWarpsMax) w = kWarpsMax;
+  return w < 1 ? 1 : w;
+}
+
+template <typename T>
+DstiTabs<T> tabs(const void* tw, const void* sn, const void* lam, const void* mu) {
+  DstiTabs<T> t;
+  t.tw = (const typename Vec2<T>::type*)tw;
+  t.sn = (const T*)sn;
+  t.lam = (const T*)lam;
+  t.mu = (const T*)mu;
+  return t;
 }
 
 }  // namespace
 
 template <typename T>
-void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const T* tw, cudaStream_t st) {
+void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const void* tw, const void* sn,
+                      cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
-  DstIArgs a;
-  a.n = n;
-  a.M = n + 1;
-  a.logM2 = logP + 1;
-  a.dim = dim;
-  a.S = S;
-  a.stride = 1;
-  a.nlines_slice = (int)(S / a.M);
-  const long long nlines = (long long)B * a.nlines_slice;
-  const int C = lines_per_block<T>(a.M, 64 * 1024);
-  const size_t smem = (size_t)C * (2 * a.M + 1) * sizeof(T2);
+  const int M = n + 1;
+  const int wpb = warps_for<T>(M);
+  const size_t smem = (size_t)wpb * (2 * padded_len(M) + 1) * sizeof(T2);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_dsti_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dsti_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     attr = true;
   }
-  const long long blocks = (nlines + 2 * C - 1) / (2 * C);
+  const long long npairs = (long long)B * (S / M) / 2;
+  long long blocks = (npairs + wpb - 1) / wpb;
+  if (blocks > (1LL << 30)) blocks = 1LL << 30;
   double d = B;
   for (int k = 0; k < dim; ++k) d *= n;
   LaunchScope ls("dsti_rows", st, 2.0 * sizeof(T) * d);
-  k_dsti_rows<T><<<(unsigned)blocks, kThreads, smem, st>>>(x, a, (const T2*)tw, C, nlines);
+  k_dsti_rows<T><<<(unsigned)blocks, wpb * 32, smem, st>>>(x, logP, dim, npairs,
+                                                           tabs<T>(tw, sn, nullptr, nullptr));
 }
 
 template <typename T>
-void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const T* tw,
-                      const double* lam, const double* mu, double tau, double c0, bool scale, cudaStream_t st) {
+void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
+                      const void* sn, const void* lam, const void* mu, double tau, double c0, bool scale,
+                      cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
-  DstIArgs a;
-  a.n = n;
-  a.M = n + 1;
-  a.logM2 = logP + 1;
-  a.dim = dim;
-  a.S = S;
-  a.stride = axis == 1 ? (long long)a.M : (long long)a.M * a.M;
-  a.nlines_slice = (int)(S / a.M);
-  ScaleArgs sc;
-  sc.enabled = scale ? 1 : 0;
-  sc.lam = lam;
-  sc.mu = mu;
-  sc.tau = tau;
-  sc.c0 = c0;
-  const long long cols = S / a.M;  // columns of one slice orthogonal to this axis (incl. ghosts)
-  int C = lines_per_block<T>(a.M, scale ? 48 * 1024 : 64 * 1024);
-  while (2LL * C > cols && C > 1) C >>= 1;
-  const size_t smem = (size_t)C * (2 * a.M + 1) * sizeof(T2) * (scale ? 2 : 1);
+  const int M = n + 1;
+  int C = warps_for<T>(M);
+  while (2 * C > M && C > 1) C >>= 1;
+  const size_t smem = (size_t)C * (2 * padded_len(M) + 1) * sizeof(T2);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_dsti_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dsti_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     attr = true;
   }
-  const dim3 grid((unsigned)((cols + 2 * C - 1) / (2 * C)), (unsigned)B);
+  const long long planes = dim == 3 ? M : 1;
+  const dim3 grid((unsigned)((M / (2 * C)) * planes), (unsigned)B);
   double d = B;
   for (int k = 0; k < dim; ++k) d *= n;
   LaunchScope ls(scale ? "dsti_cols_scale" : "dsti_cols", st, 2.0 * sizeof(T) * d);
-  k_dsti_cols<T><<<grid, kThreads, smem, st>>>(x, a, sc, (const T2*)tw, C);
+  k_dsti_cols<T><<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, (T)tau, (T)c0,
+                                             tabs<T>(tw, sn, lam, mu));
 }
 
-template void launch_dsti_rows<float>(float*, int, int, int, long long, int, const float*, cudaStream_t);
-template void launch_dsti_rows<double>(double*, int, int, int, long long, int, const double*, cudaStream_t);
-template void launch_dsti_cols<float>(float*, int, int, int, long long, int, int, const float*, const double*,
-                                      const double*, double, double, bool, cudaStream_t);
-template void launch_dsti_cols<double>(double*, int, int, int, long long, int, int, const double*, const double*,
-                                       const double*, double, double, bool, cudaStream_t);
+template void launch_dsti_rows<float>(float*, int, int, int, long long, int, const void*, const void*,
+                                      cudaStream_t);
+template void launch_dsti_rows<double>(double*, int, int, int, long long, int, const void*, const void*,
+                                       cudaStream_t);
+template void launch_dsti_cols<float>(float*, int, int, int, long long, int, int, const void*, const void*,
+                                      const void*, const void*, double, double, bool, cudaStream_t);
+template void launch_dsti_cols<double>(double*, int, int, int, long long, int, int, const void*, const void*,
+                                       const void*, const void*, double, double, bool, cudaStream_t);
 
 }  // namespace pt

@@ -232,15 +232,19 @@ template <typename T>
 void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
                         int logP, DstPlan<T> plan, const int* done, cudaStream_t st);
 
-// Spatial sine transforms of type I (kernels_dsti.cu), in place on padded slices:
+// Spatial sine transforms of type I (kernels_dsti.cu), in place on padded slices, n + 1 <= 4096:
 //   rows:  every x-line v <- S v;  cols: every line along axis 1 (y) or 2 (z) v <- S v, or with
 //   `scale`, v <- S diag(g) S v with g the exact block-solve factor c0 l / (mu_k + tau l)^2.
-// tw: e^{2 pi i k / (2(n+1))}, k < n + 1; lam: (4 a0 / h^2) sin^2(pi k h / 2), k = 1..n; mu: [B].
+// Tables (type T): tw [n+1] complex e^{-2 pi i e/(n+1)}; sn [(n+1)/2 + 1] sin(pi j/(n+1)) / 2;
+// lam [n+1] (4 a0/h^2) sin^2(pi k h/2) at position k-1 (0 at the ghost position); mu [B].
+constexpr int kDstiMaxM = 4096;
 template <typename T>
-void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const T* tw, cudaStream_t st);
+void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const void* tw, const void* sn,
+                      cudaStream_t st);
 template <typename T>
-void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const T* tw,
-                      const double* lam, const double* mu, double tau, double c0, bool scale, cudaStream_t st);
+void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
+                      const void* sn, const void* lam, const void* mu, double tau, double c0, bool scale,
+                      cudaStream_t st);
 
 // Problem hooks for the serving loop (defined in capi.cu).
 pt_status problem_begin(pt_problem* p, double tol, int max_it);   // reset + captured iteration graph
