@@ -95,6 +95,7 @@ struct pt_problem {
   void* dst_tw = nullptr;                       // [N/2] complex
   void* dst_pre = nullptr;                      // [N] complex
   int blueM = 0, blueLogM = 0;                  // Bluestein length (N not a power of two)
+  void* dst_twS = nullptr;                      // [N] complex e^{-2 pi i e / N} (power-of-two N)
   void* blue_chirp = nullptr;                   // [N] complex
   void* blue_gfwd = nullptr;                    // [M] complex
   void* blue_ginv = nullptr;                    // [M] complex
@@ -245,6 +246,7 @@ DstPlan<T> dst_plan(const pt_problem* p) {
   d.ginv = (const T*)p->blue_ginv;
   d.twM = (const T*)p->blue_tw;
   d.C = p->dstC;
+  d.twS = (const T*)p->dst_twS;
   return d;
 }
 
@@ -781,6 +783,15 @@ pt_status setup_precision(pt_problem* p) {
   if (!(p->dst_pre = alloc_bytes(p, sizeof(T) * pre.size(), &st))) return st;
   if ((st = upload<T>(p, p->dst_tw, tw)) != PT_OK) return st;
   if ((st = upload<T>(p, p->dst_pre, pre)) != PT_OK) return st;
+  if (is_pow2(p->N)) {
+    std::vector<double> tws(2 * p->N);
+    for (int e = 0; e < p->N; ++e) {
+      tws[2 * e] = std::cos(2.0 * M_PI * e / p->N);  // e^{-2 pi i e / N}
+      tws[2 * e + 1] = -std::sin(2.0 * M_PI * e / p->N);
+    }
+    if (!(p->dst_twS = alloc_bytes(p, sizeof(T) * tws.size(), &st))) return st;
+    if ((st = upload<T>(p, p->dst_twS, tws)) != PT_OK) return st;
+  }
   if (!is_pow2(p->N)) {
     // Bluestein: chirp c_m = e^{i pi m^2 / N} (phase reduced mod 2N), filters g with g_m = g_{M-m}
     // = c_m (e^{-} DFT) or conj(c_m) (e^{+} DFT), their M-point spectra in bit-reversed order / M

@@ -14,6 +14,7 @@
 //
 // A CTA owns W = 2C consecutive padded spatial columns for all N time slots, so the transform
 // is done in place with no inter-CTA dependency.  N must be a power of two.
+#include <algorithm>
 #include <cmath>
 
 #include "fft_common.cuh"
@@ -251,6 +252,176 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
   }
 }
 
+// ---- power-of-two N, 2 <= N <= 2048: the same transforms with radix-8 Stockham passes ----
+// A CTA owns F complex columns (2F real columns) for all N slots; each column's FFT is done by
+// nthr = max(1, N/8) threads, in place in a padded shared-memory array.  The e^{+} transform of
+// the forward direction is taken as the conjugate of the e^{-} transform of the conjugate.
+
+constexpr int kStockMaxN = 2048;
+constexpr int kStockThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kStockThreads, 2) k_dst_forward_s(T* x, long long S, ColGeom cg, DstPlan<T> plan,
+                                                                 int F, const int* done) {
+  using T2 = typename Vec2<T>::type;
+  if (stop_requested(done)) return;
+  const int N = plan.N, logN = plan.logN;
+  const int nthr = N >= 8 ? N >> 3 : 1;
+  const int Lp = padded_len(N);
+  const T2* __restrict__ pre = (const T2*)plan.pre;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* sm = (T2*)smem_raw;
+  const long long c0 = (long long)blockIdx.x * 2 * F;
+  // load: slot m = N-1-t holds (w_a, w_b); the m = 0 entry is doubled
+  for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
+    const int f = idx % F, t = idx / F;
+    T2 v = *(const T2*)(x + (long long)t * S + c0 + 2 * f);
+    const int m = N - 1 - t;
+    if (m == 0) {
+      v.x *= (T)2;
+      v.y *= (T)2;
+    }
+    sm[(size_t)f * Lp + pd(m)] = v;
+  }
+  __syncthreads();
+  // pre-twiddle in pairs (m, N-m): V[m] = e^{i pi m/(2N)} (w_m - i w_{N-m}), Z = V_a + i V_b,
+  // stored conjugated
+  const int halfp = (N >> 1) + 1;
+  for (int idx = threadIdx.x; idx < F * halfp; idx += blockDim.x) {
+    const int f = idx % F, m = idx / F;
+    T2* col = sm + (size_t)f * Lp;
+    if (m == 0) {
+      col[0].y = -col[0].y;
+      continue;
+    }
+    const int q = N - m;
+    const T2 A = col[pd(m)], Bq = col[pd(q)];
+    const T2 em = pre[m], eq = pre[q];
+    const T vam_r = A.x * em.x + Bq.x * em.y, vam_i = A.x * em.y - Bq.x * em.x;
+    const T vbm_r = A.y * em.x + Bq.y * em.y, vbm_i = A.y * em.y - Bq.y * em.x;
+    if (q != m) {
+      const T vaq_r = Bq.x * eq.x + A.x * eq.y, vaq_i = Bq.x * eq.y - A.x * eq.x;
+      const T vbq_r = Bq.y * eq.x + A.y * eq.y, vbq_i = Bq.y * eq.y - A.y * eq.x;
+      col[pd(q)] = mk<T2>(vaq_r - vbq_i, -(vaq_i + vbq_r));
+    }
+    col[pd(m)] = mk<T2>(vam_r - vbm_i, -(vam_i + vbm_r));
+  }
+  __syncthreads();
+  {
+    const int f = threadIdx.x / nthr, tid = threadIdx.x - f * nthr;
+    block_fft<T2>(sm + (size_t)f * Lp, logN, (const T2*)plan.twS, tid, nthr);
+  }
+  // output: rhat_{j+1} = (-1)^j C3_j / 2, C3_{2i} = v_i, C3_{2i+1} = v_{N-1-i}; v = conj(spectrum)
+  for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
+    const int f = idx % F, j = idx / F;
+    const int vi = (j & 1) ? (N - 1 - (j >> 1)) : (j >> 1);
+    const T2 r = sm[(size_t)f * Lp + pd(vi)];
+    const T sc = (j & 1) ? (T)-0.5 : (T)0.5;
+    T2 v;
+    v.x = ghost_col(cg, c0 + 2 * f) ? (T)0 : r.x * sc;
+    v.y = ghost_col(cg, c0 + 2 * f + 1) ? (T)0 : -r.y * sc;
+    *(T2*)(x + (long long)j * S + c0 + 2 * f) = v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStockThreads, 2) k_dst_inverse_s(const T* __restrict__ y, void* out, int mode,
+                                                                 double omega, long long S, ColGeom cg,
+                                                                 DstPlan<T> plan, int F, const int* done) {
+  using T2 = typename Vec2<T>::type;
+  if (stop_requested(done)) return;
+  const int N = plan.N, logN = plan.logN;
+  const int nthr = N >= 8 ? N >> 3 : 1;
+  const int Lp = padded_len(N);
+  const T2* __restrict__ pre = (const T2*)plan.pre;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* sm = (T2*)smem_raw;
+  const long long c0 = (long long)blockIdx.x * 2 * F;
+  // load: z_j = (-1)^j y_{j+1};  v_{j/2} = z_j (j even), v_{N-1-(j-1)/2} = z_j (j odd)
+  for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
+    const int f = idx % F, j = idx / F;
+    T2 v = *(const T2*)(y + (long long)j * S + c0 + 2 * f);
+    int s;
+    if (j & 1) {
+      s = N - 1 - (j >> 1);
+      v.x = -v.x;
+      v.y = -v.y;
+    } else {
+      s = j >> 1;
+    }
+    sm[(size_t)f * Lp + pd(s)] = v;
+  }
+  __syncthreads();
+  {
+    const int f = threadIdx.x / nthr, tid = threadIdx.x - f * nthr;
+    block_fft<T2>(sm + (size_t)f * Lp, logN, (const T2*)plan.twS, tid, nthr);
+  }
+  // post: V_a[m] = (C_m + conj C_{N-m})/2, V_b[m] = (C_m - conj C_{N-m})/(2i);
+  //       X[m] = Re(e^{-i pi m/(2N)} V[m]);  u_{N-m} = X[m]  (time slot N-1-m)
+  const int halfp = (N >> 1) + 1;
+  for (int idx = threadIdx.x; idx < F * halfp; idx += blockDim.x) {
+    const int f = idx % F, m = idx / F;
+    const bool ga = ghost_col(cg, c0 + 2 * f), gb = ghost_col(cg, c0 + 2 * f + 1);
+    const int q = m == 0 ? 0 : N - m;
+    const T2* col = sm + (size_t)f * Lp;
+    const T2 Cm = col[pd(m)], Cq = col[pd(q)];
+    const T2 em = pre[m];
+    const T var = (T)0.5 * (Cm.x + Cq.x), vai = (T)0.5 * (Cm.y - Cq.y);
+    const T vbr = (T)0.5 * (Cm.y + Cq.y), vbi = (T)0.5 * (Cq.x - Cm.x);
+    const T Xa = ga ? (T)0 : var * em.x + vai * em.y;
+    const T Xb = gb ? (T)0 : vbr * em.x + vbi * em.y;
+    const long long o1 = (long long)(N - 1 - m) * S + c0 + 2 * f;
+    if (mode == 1) {
+      double2* u = (double2*)((double*)out + o1);
+      double2 cur = *u;
+      cur.x += omega * (double)Xa;
+      cur.y += omega * (double)Xb;
+      *u = cur;
+    } else {
+      *(T2*)((T*)out + o1) = mk<T2>(Xa, Xb);
+    }
+    if (m != 0 && q != m) {
+      // X[q] with the roles of m and q exchanged -> time slot N-1-q = m-1
+      const T2 eq = pre[q];
+      const T var2 = (T)0.5 * (Cq.x + Cm.x), vai2 = (T)0.5 * (Cq.y - Cm.y);
+      const T vbr2 = (T)0.5 * (Cq.y + Cm.y), vbi2 = (T)0.5 * (Cm.x - Cq.x);
+      const T Xa2 = ga ? (T)0 : var2 * eq.x + vai2 * eq.y;
+      const T Xb2 = gb ? (T)0 : vbr2 * eq.x + vbi2 * eq.y;
+      const long long o2 = (long long)(m - 1) * S + c0 + 2 * f;
+      if (mode == 1) {
+        double2* u = (double2*)((double*)out + o2);
+        double2 cur = *u;
+        cur.x += omega * (double)Xa2;
+        cur.y += omega * (double)Xb2;
+        *u = cur;
+      } else {
+        *(T2*)((T*)out + o2) = mk<T2>(Xa2, Xb2);
+      }
+    }
+  }
+}
+
+template <typename T>
+bool stockham_ok(const DstPlan<T>& plan) {
+  return plan.M == 0 && plan.twS != nullptr && plan.N >= 2 && plan.N <= kStockMaxN;
+}
+
+// complex columns per CTA for the Stockham kernels: a power of two within the thread, shared-
+// memory and slice limits (C from the plan or the autotuner is an upper bound)
+template <typename T>
+int stockham_cols(const DstPlan<T>& plan, long long S) {
+  const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
+  const long long per = (long long)padded_len(plan.N) * 2 * sizeof(T);
+  long long F = plan.C > 0 ? plan.C : kStockThreads / nthr;
+  F = std::min<long long>(F, std::max(1, kStockThreads / nthr));
+  F = std::min<long long>(F, std::max<long long>(1, (200 * 1024) / per));
+  long long pw = 1;
+  while (pw * 2 <= F) pw *= 2;
+  F = pw;
+  while (F > 1 && (S % (2 * F)) != 0) F >>= 1;
+  return (int)F;
+}
+
 template <typename T>
 int dst_cols(int L, long long S) {
   // complex columns (stride L) per CTA: a power of two, <= 16, using at most ~100 KB of shared memory
@@ -291,7 +462,17 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
   double interior = plan.N;
   for (int d = 0; d < dim; ++d) interior *= n;
   LaunchScope ls("dst_forward", st, 2.0 * sizeof(T) * interior);
-  if (plan.M > 0)
+  if (stockham_ok(plan)) {
+    static bool attr_s = false;
+    if (!attr_s) {
+      cudaFuncSetAttribute(k_dst_forward_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_s = true;
+    }
+    const int F = stockham_cols(plan, S);
+    const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
+    const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2);
+    k_dst_forward_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(x, S, cg, plan, F, done);
+  } else if (plan.M > 0)
     k_dst_forward<T, true><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
   else
     k_dst_forward<T, false><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
@@ -315,7 +496,17 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
   double interior = plan.N;
   for (int d = 0; d < dim; ++d) interior *= n;
   LaunchScope ls("dst_inverse", st, (sizeof(T) + (mode == 1 ? 16.0 : (double)sizeof(T))) * interior);
-  if (plan.M > 0)
+  if (stockham_ok(plan)) {
+    static bool attr_s = false;
+    if (!attr_s) {
+      cudaFuncSetAttribute(k_dst_inverse_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_s = true;
+    }
+    const int F = stockham_cols(plan, S);
+    const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
+    const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2);
+    k_dst_inverse_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(y, out, mode, omega, S, cg, plan, F, done);
+  } else if (plan.M > 0)
     k_dst_inverse<T, true><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);
   else
     k_dst_inverse<T, false><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);

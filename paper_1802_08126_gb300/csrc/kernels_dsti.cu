@@ -24,121 +24,6 @@ namespace {
 
 constexpr int kWarpsMax = 8;
 
-// padded shared-memory index: one spare element per 8 keeps radix-8 strided writes conflict-free
-__device__ __forceinline__ int pd(int e) { return e + (e >> 3); }
-__host__ __device__ constexpr int padded_len(int M) { return M + (M >> 3) + 1; }
-
-template <typename T2>
-__device__ __forceinline__ T2 mk(decltype(T2::x) x, decltype(T2::x) y) {
-  T2 r;
-  r.x = x;
-  r.y = y;
-  return r;
-}
-template <typename T2>
-__device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
-template <typename T2>
-__device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
-template <typename T2>
-__device__ __forceinline__ T2 cmul(T2 a, T2 w) {
-  return mk<T2>(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
-}
-template <typename T2>
-__device__ __forceinline__ T2 mul_mi(T2 a) { return mk<T2>(a.y, -a.x); }  // a * (-i)
-
-// forward DFTs of length 2, 4, 8 in registers, natural order in and out (omega_R = e^{-2 pi i/R})
-template <typename T2>
-__device__ __forceinline__ void dft2(T2* u) {
-  const T2 a = u[0];
-  u[0] = cadd(a, u[1]);
-  u[1] = csub(a, u[1]);
-}
-template <typename T2>
-__device__ __forceinline__ void dft4(T2& u0, T2& u1, T2& u2, T2& u3) {
-  const T2 s02 = cadd(u0, u2), d02 = csub(u0, u2), s13 = cadd(u1, u3), d13 = mul_mi(csub(u1, u3));
-  u0 = cadd(s02, s13);
-  u2 = csub(s02, s13);
-  u1 = cadd(d02, d13);
-  u3 = csub(d02, d13);
-}
-template <typename T2>
-__device__ __forceinline__ void dft8(T2* u) {
-  using T = decltype(T2::x);
-  const T r = (T)0.70710678118654752440;  // 1/sqrt(2)
-  T2 e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
-  T2 o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
-  dft4(e0, e1, e2, e3);
-  dft4(o0, o1, o2, o3);
-  o1 = mk<T2>((o1.x + o1.y) * r, (o1.y - o1.x) * r);   // * e^{-i pi/4}
-  o2 = mul_mi(o2);                                       // * e^{-i pi/2}
-  o3 = mk<T2>((o3.y - o3.x) * r, -(o3.x + o3.y) * r);  // * e^{-3 i pi/4}
-  u[0] = cadd(e0, o0);
-  u[4] = csub(e0, o0);
-  u[1] = cadd(e1, o1);
-  u[5] = csub(e1, o1);
-  u[2] = cadd(e2, o2);
-  u[6] = csub(e2, o2);
-  u[3] = cadd(e3, o3);
-  u[7] = csub(e3, o3);
-}
-template <int LR, typename T2>
-__device__ __forceinline__ void dftR(T2* u) {
-  if (LR == 1) dft2(u);
-  if (LR == 2) dft4(u[0], u[1], u[2], u[3]);
-  if (LR == 3) dft8(u);
-}
-
-// One Stockham (autosort) radix-2^LR pass of a length-M = 2^logM FFT, after passes of total
-// radix p = 2^s: butterfly i reads in[i + m M/R], twiddles input m by omega_{pR}^{m k}
-// (k = i mod p), and writes out[(i - k) R + k + m p].  tw[e] = e^{-2 pi i e / M}.
-template <int LR, typename T2>
-__device__ __forceinline__ void stockham_pass(const T2* __restrict__ in, T2* __restrict__ out, int logM, int s,
-                                              const T2* __restrict__ tw, int lane) {
-  constexpr int R = 1 << LR;
-  const int nb = 1 << (logM - LR);
-  const int p = 1 << s;
-  const int tsh = logM - s - LR;
-  for (int i = lane; i < nb; i += 32) {
-    const int k = i & (p - 1);
-    T2 u[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) u[m] = in[pd(i + m * nb)];
-    if (s > 0) {
-#pragma unroll
-      for (int m = 1; m < R; ++m) u[m] = cmul(u[m], __ldg(&tw[(m * k) << tsh]));
-    }
-    dftR<LR>(u);
-    const int j = ((i - k) << LR) + k;
-#pragma unroll
-    for (int m = 0; m < R; ++m) out[pd(j + m * p)] = u[m];
-  }
-}
-
-// FFT of the warp's sequence in `a` (padded, natural order); `b` is scratch.  Returns the buffer
-// holding the spectrum (natural order).
-template <typename T2>
-__device__ __forceinline__ T2* warp_fft(T2* a, T2* b, int logM, const T2* __restrict__ tw, int lane) {
-  int s = 0;
-  while (s < logM) {
-    const int rem = logM - s;
-    if (rem >= 5 || rem == 3) {
-      stockham_pass<3>(a, b, logM, s, tw, lane);
-      s += 3;
-    } else if (rem == 4 || rem == 2) {
-      stockham_pass<2>(a, b, logM, s, tw, lane);
-      s += 2;
-    } else {
-      stockham_pass<1>(a, b, logM, s, tw, lane);
-      s += 1;
-    }
-    __syncwarp();
-    T2* t = a;
-    a = b;
-    b = t;
-  }
-  return a;
-}
-
 // z_j = (y^a_j + i y^b_j) / 2 from x_j = read(j - 1) (position j-1 holds x_j, x_0 = x_M = 0);
 // sn[j] = sin(pi j / M) / 2 for j <= M/2.
 template <typename T, typename T2, typename Read>

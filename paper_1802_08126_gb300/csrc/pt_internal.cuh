@@ -218,6 +218,7 @@ struct DstPlan {
   const T* ginv = nullptr;   // [M] same for the e^{+} transform
   const T* twM = nullptr;    // [M/2] e^{2 pi i k / M}
   int C = 0;                 // complex columns per CTA (0: chosen from shared-memory size)
+  const T* twS = nullptr;    // [N] e^{-2 pi i e / N} (power-of-two N: radix-8 Stockham kernels)
 };
 
 // in-place forward transform: x_k <- sum_n x_n sin((2k-1) n pi/(2N)) for every interior column
