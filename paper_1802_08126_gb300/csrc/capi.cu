@@ -74,7 +74,7 @@ struct pt_problem {
   double *u = nullptr, *p = nullptr, *F = nullptr;
   void *W1 = nullptr, *W2 = nullptr;            // preconditioner precision, fine level
   void* W3 = nullptr;                           // residual between V-cycles of an H_k solve
-  double* bres = nullptr;                       // F - B u of the current iterate (mixed precision)
+  double* bres = nullptr;                       // F - B u of the current iterate (FP64, 2-D)
   bool hdst = false;                            // exact H_k solves by spatial sine transforms
   void* dsti_tw = nullptr;                      // [n+1] complex e^{-2 pi i e / (n+1)}   (type T)
   void* dsti_sn = nullptr;                      // [(n+1)/2 + 1] sin(pi j / (n+1)) / 2
@@ -96,6 +96,11 @@ struct pt_problem {
   void* dst_pre = nullptr;                      // [N] complex
   int blueM = 0, blueLogM = 0;                  // Bluestein length (N not a power of two)
   void* dst_twS = nullptr;                      // [N] complex e^{-2 pi i e / N} (power-of-two N)
+  float* ir_du = nullptr;                       // mixed: FP32 corrections of u and p, residuals
+  float* ir_dp = nullptr;
+  float* ir_R1 = nullptr;
+  float* ir_R2 = nullptr;
+  float* ir_bp = nullptr;
   void* blue_chirp = nullptr;                   // [N] complex
   void* blue_gfwd = nullptr;                    // [M] complex
   void* blue_ginv = nullptr;                    // [M] complex
@@ -353,6 +358,25 @@ void enqueue_iteration(pt_problem* p) {
   T* W1 = (T*)p->W1;
   T* W2 = (T*)p->W2;
   const DstPlan<T> dp = dst_plan<T>(p);
+  if (p->mixed) {
+    // iterative refinement: FP64 step (fold + residual) or FP32 step on the corrections
+    const Level& L0 = p->lev[0];
+    const long long total = L0.S * p->N;
+    const StencilGeom<float> gf = geom<float>(p, 0);
+    launch_ir_begin(p->state, kOuter, p->st);
+    launch_ir_fold(p->u, p->p, p->ir_du, p->ir_dp, total, p->state, p->st);
+    launch_ir_outer(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, g, p->cth_d, p->tau, p->N,
+                    p->state, p->st);
+    launch_ir_inner(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials, gf,
+                    (const float*)p->cthA, (float)p->tau, p->N, p->state, p->st);
+    launch_ir_finalize(p->partials, p->state, p->hist, p->st);
+    apply_precond_A<T>(p, W1, p->ir_dp, 1, 0, done);
+    launch_ir_resid_u(p->ir_bp, p->ir_R2, p->ir_du, p->ir_dp, (float*)W1, L0.S, p->N, p->state, p->st);
+    launch_dst_forward<T>(W1, L0.S, p->dim, p->n, L0.logP, dp, done, p->st);
+    T* yhat = block_solve<T>(p, done);
+    launch_dst_inverse<T>(yhat, p->ir_du, 2, p->omega, L0.S, p->dim, p->n, L0.logP, dp, done, p->st);
+    return;
+  }
   if (p->bres && p->dim == 2 && p->lev[0].P >= 32) {
     // outer residual first (and the convergence test), then the p-update and the stencil-free r_u
     const Level& L0 = p->lev[0];
@@ -393,6 +417,10 @@ pt_status enqueue_reset(pt_problem* p, double tol, int max_it) {
   const long long total = p->lev[0].S * p->N;
   PT_CUDA(cudaMemsetAsync(p->u, 0, sizeof(double) * total, p->st));
   PT_CUDA(cudaMemsetAsync(p->p, 0, sizeof(double) * total, p->st));
+  if (p->mixed) {
+    PT_CUDA(cudaMemsetAsync(p->ir_du, 0, sizeof(float) * total, p->st));
+    PT_CUDA(cudaMemsetAsync(p->ir_dp, 0, sizeof(float) * total, p->st));
+  }
   launch_norm2_partials(p->F, total, p->partials, p->st);
   launch_finalize_fnorm(p->partials, p->state, tol, max_it, p->st);
   PT_CHECK_LAUNCH();
@@ -457,7 +485,7 @@ pt_status finish_solve(pt_problem* p, int* iters_out, double* res_hist) {
   SolveState hs;
   pt_status st = read_state(p, &hs);
   if (st != PT_OK) return st;
-  if (!hs.done) return fail(PT_ECUDA, "solver state not finalised");
+  if (hs.done != 1) return fail(PT_ECUDA, "solver state not finalised");
   if (iters_out) *iters_out = hs.iters;
   if (res_hist) {
     PT_CUDA(cudaMemcpyAsync(res_hist, p->hist, sizeof(double) * (hs.iters + 1), cudaMemcpyDeviceToHost, p->st));
@@ -499,8 +527,9 @@ pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* r
       since_poll = 0;
       SolveState hs;
       if ((st = read_state(p, &hs)) != PT_OK) return st;
-      if (hs.done) break;
-      if (launched > (long long)max_it + per_launch + 1) return fail(PT_ECUDA, "solver did not stop at max_it");
+      if (hs.done == 1) break;
+      // (the mixed form may take one extra launch: the FP64 step that confirms the last estimate)
+      if (launched > (long long)max_it + 2 * per_launch + 2) return fail(PT_ECUDA, "solver did not stop at max_it");
     }
   }
   return finish_solve(p, iters_out, res_hist);
@@ -951,8 +980,12 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   if (!(p->u = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->p = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->F = alloc_padded<double>(p, L0, p->N, &st))) return st;
-  if ((p->mixed || (p->dim == 2 && L0.P >= 32)) && !(p->bres = alloc_padded<double>(p, L0, p->N, &st)))
-    return st;
+  if (!p->mixed && p->dim == 2 && L0.P >= 32 && !(p->bres = alloc_padded<double>(p, L0, p->N, &st))) return st;
+  if (p->mixed) {
+    float** ir[5] = {&p->ir_du, &p->ir_dp, &p->ir_R1, &p->ir_R2, &p->ir_bp};
+    for (float** b : ir)
+      if (!(*b = alloc_padded<float>(p, L0, p->N, &st))) return st;
+  }
   st = p->mixed ? setup_precision<float>(p) : setup_precision<double>(p);
   if (st != PT_OK) return st;
   if (!(p->partials = (double*)alloc_bytes(p, sizeof(double) * kReduceBlocks, &st))) return st;
@@ -1071,7 +1104,8 @@ size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o) {
   const double s = mixed ? 4.0 : 8.0;
   const double lev = 1.0 / ((1 << d) - 1);  // levels below the finest, relative to it
   double per = 24.0 + 3.0 * s;              // u, p, F and three work vectors
-  if (mixed || d == 2) per += 8.0;          // stored outer residual
+  if (mixed) per += 20.0;                   // FP32 corrections and residuals of the refinement
+  if (!mixed && d == 2) per += 8.0;         // stored outer residual
   per += (d == 2 ? 2.0 : 3.0) * s * lev;    // multigrid right-hand sides, iterates (and residuals)
   if (d != 2) per += 2.0 * s;               // generic path: level-0 iterate and residual
   if (d == 2 && !mixed) per += 8.0 * (1.0 + lev);  // cached Jacobi factors
@@ -1272,7 +1306,7 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
         if (!hdone[i]) still.push_back(i);
       const size_t finished = active.size() - still.size();
       if (still.empty()) break;
-      if (rounds > max_rounds + 1) {
+      if (rounds > max_rounds + 2) {
         cleanup();
         return fail(PT_ECUDA, "batch did not stop at max_it");
       }

@@ -222,6 +222,12 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
       cur.x += omega * (double)Xa;
       cur.y += omega * (double)Xb;
       *u = cur;
+    } else if (mode == 2) {
+      T2* o = (T2*)((T*)out + o1);
+      T2 cur = *o;
+      cur.x += (T)omega * Xa;
+      cur.y += (T)omega * Xb;
+      *o = cur;
     } else {
       T2 v;
       v.x = Xa;
@@ -242,6 +248,12 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
         cur.x += omega * (double)Xa2;
         cur.y += omega * (double)Xb2;
         *u = cur;
+      } else if (mode == 2) {
+        T2* o = (T2*)((T*)out + o2);
+        T2 cur = *o;
+        cur.x += (T)omega * Xa2;
+        cur.y += (T)omega * Xb2;
+        *o = cur;
       } else {
         T2 v;
         v.x = Xa2;
@@ -377,6 +389,10 @@ __global__ void __launch_bounds__(kStockThreads, 2) k_dst_inverse_s(const T* __r
       cur.x += omega * (double)Xa;
       cur.y += omega * (double)Xb;
       *u = cur;
+    } else if (mode == 2) {
+      T2* o = (T2*)((T*)out + o1);
+      const T2 cur = *o;
+      *o = mk<T2>(cur.x + (T)omega * Xa, cur.y + (T)omega * Xb);
     } else {
       *(T2*)((T*)out + o1) = mk<T2>(Xa, Xb);
     }
@@ -394,6 +410,10 @@ __global__ void __launch_bounds__(kStockThreads, 2) k_dst_inverse_s(const T* __r
         cur.x += omega * (double)Xa2;
         cur.y += omega * (double)Xb2;
         *u = cur;
+      } else if (mode == 2) {
+        T2* o = (T2*)((T*)out + o2);
+        const T2 cur = *o;
+        *o = mk<T2>(cur.x + (T)omega * Xa2, cur.y + (T)omega * Xb2);
       } else {
         *(T2*)((T*)out + o2) = mk<T2>(Xa2, Xb2);
       }
@@ -495,7 +515,8 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
   const ColGeom cg{dim, n, logP};
   double interior = plan.N;
   for (int d = 0; d < dim; ++d) interior *= n;
-  LaunchScope ls("dst_inverse", st, (sizeof(T) + (mode == 1 ? 16.0 : (double)sizeof(T))) * interior);
+  LaunchScope ls("dst_inverse", st,
+                 (sizeof(T) + (mode == 1 ? 16.0 : mode == 2 ? 2.0 * sizeof(T) : (double)sizeof(T))) * interior);
   if (stockham_ok(plan)) {
     static bool attr_s = false;
     if (!attr_s) {

@@ -295,7 +295,7 @@ __global__ void k_finalize_fnorm(const double* __restrict__ partials, SolveState
 
 __global__ void k_gather_done(SolveState* const* __restrict__ states, int count, int* __restrict__ out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
-    out[i] = states[i]->done;
+    out[i] = states[i]->done == 1;
 }
 
 template <typename Tp>

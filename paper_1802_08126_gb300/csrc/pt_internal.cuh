@@ -141,8 +141,24 @@ struct SolveState {
   double last_res;
   double tol;
   int max_it;
-  int pad;
+  int outer;     // mixed precision: this iteration starts with the FP64 refinement step
 };
+
+// Mixed precision as iterative refinement (kernels_ir.cu): FP64 step every kOuter iterations
+// (and on request of the FP32 residual estimate), FP32 iterations on the corrections between.
+constexpr int kOuter = 8;
+void launch_ir_begin(SolveState* st, int kouter, cudaStream_t s);
+void launch_ir_fold(double* u, double* p, float* du, float* dp, long long total, const SolveState* st,
+                    cudaStream_t s);
+void launch_ir_outer(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
+                     double* partials, StencilGeom<double> g, const double* cth, double tau, int N,
+                     const SolveState* st, cudaStream_t s);
+void launch_ir_inner(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
+                     double* partials, StencilGeom<float> g, const float* cth, float tau, int N,
+                     const SolveState* st, cudaStream_t s);
+void launch_ir_resid_u(const float* bp, const float* R2, const float* du, const float* dp, float* ru, long long S,
+                       int N, const SolveState* st, cudaStream_t s);
+void launch_ir_finalize(const double* partials, SolveState* state, double* hist, cudaStream_t s);
 
 // sum partials in fixed order; residual of iterate state->j -> hist[j], sets flags, advances j.
 void launch_finalize_residual(const double* partials, SolveState* state, double* hist, cudaStream_t st);
@@ -227,8 +243,8 @@ template <typename T>
 void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> plan, const int* done,
                         cudaStream_t st);
 
-// inverse + update: u_n += omega * sum_k y_k sin((2k-1) n pi/(2N)); u in FP64 (mode 1) or
-// out = transform (mode 0, out of type T)
+// inverse + update: u_n += omega * sum_k y_k sin((2k-1) n pi/(2N)); u in FP64 (mode 1), u of
+// type T (mode 2), or out = transform (mode 0, out of type T)
 template <typename T>
 void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long S, int dim, int n,
                         int logP, DstPlan<T> plan, const int* done, cudaStream_t st);
