@@ -367,8 +367,13 @@ void enqueue_iteration(pt_problem* p) {
     launch_ir_fold(p->u, p->p, p->ir_du, p->ir_dp, total, p->state, p->st);
     launch_ir_outer(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, g, p->cth_d, p->tau, p->N,
                     p->state, p->st);
-    launch_ir_inner(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials, gf,
-                    (const float*)p->cthA, (float)p->tau, p->N, p->state, p->st);
+    if (p->dim == 2 && L0.P >= 32)
+      launch_ir_inner_2d(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials,
+                         p->tab_f + L0.tab, (const float*)p->cthA, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S,
+                         p->N, p->state, p->st);
+    else
+      launch_ir_inner(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials, gf,
+                      (const float*)p->cthA, (float)p->tau, p->N, p->state, p->st);
     launch_ir_finalize(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->ir_dp, 1, 0, done);
     launch_ir_resid_u(p->ir_bp, p->ir_R2, p->ir_du, p->ir_dp, (float*)W1, L0.S, p->N, p->state, p->st);

@@ -101,7 +101,7 @@ __global__ void k_ir_inner(const float* __restrict__ du, const float* __restrict
                            float* __restrict__ rp, double* __restrict__ partials, StencilGeom<float> g,
                            const float* __restrict__ cth, float tau, long long total, const SolveState* st) {
   if (vload(&st->done) != 0 || vload(&st->outer)) return;
-  double acc = 0.0;
+  float acc = 0.f;  // per-thread sum in FP32 (an estimate), block sum in FP64
   const float sc = tau * g.h2inv;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -118,13 +118,13 @@ __global__ void k_ir_inner(const float* __restrict__ du, const float* __restrict
       const float Ap = stencil_sum<DIM, float>(dp, i, pc, am, ap, g.P);
       b = R2[i] - Kd - sc * Ad;
       r = Kd - sc * Ap - R1[i];
-      acc += (double)b * (double)b;
+      acc = fmaf(b, b, acc);
     }
     bp[i] = b;
     rp[i] = r;
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  const double sum = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = sum;
 }
 
 // r_u' = b' - K^T (dp + du); b' is R2 on the FP64-step iteration (du = 0 there)

@@ -139,3 +139,102 @@ template void launch_resid_bres_2d<double>(const double*, const double*, const d
                                            int, long long, int, const int*, cudaStream_t);
 
 }  // namespace pt
+
+// ---- FP32 inner step of the mixed-precision refinement, 2-D (n + 1 >= 32) ----
+//   b'   = R2 - K du - tau A du,    r_p' = K du - tau A dp - R1,    partials of ||b'||^2
+// with the same warp-strip sweep; the per-thread norm is accumulated in FP32 (it only decides
+// when the FP64 step is due) and summed in FP64 across the block.
+namespace pt {
+namespace {
+
+__global__ void __launch_bounds__(256) k_ir_inner_2d(
+    const float* __restrict__ du, const float* __restrict__ dp, const float* __restrict__ R1,
+    const float* __restrict__ R2, float* __restrict__ bp, float* __restrict__ rp, double* __restrict__ partials,
+    const float* __restrict__ tabf, const float* __restrict__ cthf, float a0s, float s_h2, int n, int logP,
+    long long S, long long nwarps, const SolveState* st) {
+  if (*((volatile const int*)&st->done) != 0 || *((volatile const int*)&st->outer) != 0) return;
+  const int P = 1 << logP;
+  const int lane = threadIdx.x & 31;
+  float acc = 0.f;
+  for (long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wg < nwarps;
+       wg += (long long)gridDim.x * (blockDim.x >> 5)) {
+    const int wx_count = P >> 5, strips = P / kRows;
+    const int wx = (int)(wg % wx_count);
+    const long long rest = wg / wx_count;
+    const int strip = (int)(rest % strips);
+    const int t = (int)(rest / strips);
+    const int x = (wx << 5) + lane;
+    const int y0 = strip * kRows;
+    const float* nx = tabf;
+    const float* fx = tabf + P;
+    const float* ny = tabf + 2 * P;
+    const float* fy = tabf + 3 * P;
+    const float ct = s_h2 * cthf[t];
+    const bool xin = x < n;
+    const float fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
+    const float gxc = ct * nx[x];
+    const long long base = (long long)t * S + x;
+    auto at = [&](int y) { return base + (long long)y * P; };
+    float d_m = du[at(y0) - P], d_c = du[at(y0)];
+    float q_m = dp[at(y0) - P], q_c = dp[at(y0)];
+    float ayl = fmaf(gxc, fy[y0], a0s);
+    for (int k = 0; k < kRows; ++k) {
+      const int y = y0 + k;
+      const bool yin = y < n;
+      float d_p = 0.f, q_p = 0.f;
+      if (y + 1 < P) {
+        d_p = du[at(y + 1)];
+        q_p = dp[at(y + 1)];
+      }
+      float dW = __shfl_up_sync(0xffffffffu, d_c, 1), dE = __shfl_down_sync(0xffffffffu, d_c, 1);
+      float qW = __shfl_up_sync(0xffffffffu, q_c, 1), qE = __shfl_down_sync(0xffffffffu, q_c, 1);
+      if (lane == 0 && yin) {
+        dW = du[at(y) - 1];
+        qW = dp[at(y) - 1];
+      }
+      if (lane == 31 && yin && x + 1 < P) {
+        dE = du[at(y) + 1];
+        qE = dp[at(y) + 1];
+      }
+      const float ayu = fmaf(gxc, fy[y + 1 < P ? y + 1 : y], a0s);
+      float b = 0.f, r = 0.f;
+      if (xin && yin) {
+        const long long i = at(y);
+        const float gy = ct * ny[y];
+        const float axl = fmaf(gy, fxl, a0s), axr = fmaf(gy, fxr, a0s);
+        const float Kd = d_c - (t > 0 ? du[i - S] : 0.f);
+        const float sd = axl * (d_c - dW) + axr * (d_c - dE) + ayl * (d_c - d_m) + ayu * (d_c - d_p);
+        const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - q_m) + ayu * (q_c - q_p);
+        b = R2[i] - Kd - sd;
+        r = Kd - sq - R1[i];
+        acc = fmaf(b, b, acc);
+      }
+      if (y < P) {
+        bp[at(y)] = b;
+        rp[at(y)] = r;
+      }
+      d_m = d_c;
+      d_c = d_p;
+      q_m = q_c;
+      q_c = q_p;
+      ayl = ayu;
+    }
+  }
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+}  // namespace
+
+void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
+                        double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
+                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s) {
+  const int P = 1 << logP;
+  const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
+  const double s_h2 = tau / (h * h);
+  LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * N);
+  k_ir_inner_2d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
+                                              (float)s_h2, n, logP, S, nwarps, st);
+}
+
+}  // namespace pt

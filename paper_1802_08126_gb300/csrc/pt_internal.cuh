@@ -146,7 +146,7 @@ struct SolveState {
 
 // Mixed precision as iterative refinement (kernels_ir.cu): FP64 step every kOuter iterations
 // (and on request of the FP32 residual estimate), FP32 iterations on the corrections between.
-constexpr int kOuter = 8;
+constexpr int kOuter = 16;
 void launch_ir_begin(SolveState* st, int kouter, cudaStream_t s);
 void launch_ir_fold(double* u, double* p, float* du, float* dp, long long total, const SolveState* st,
                     cudaStream_t s);
@@ -156,6 +156,10 @@ void launch_ir_outer(const double* u, const double* p, const double* F, float* R
 void launch_ir_inner(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                      double* partials, StencilGeom<float> g, const float* cth, float tau, int N,
                      const SolveState* st, cudaStream_t s);
+// 2-D (n + 1 >= 32) warp-strip form of launch_ir_inner (kernels_resid2d.cu); tabf: level-0 FP32 tables
+void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
+                        double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
+                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s);
 void launch_ir_resid_u(const float* bp, const float* R2, const float* du, const float* dp, float* ru, long long S,
                        int N, const SolveState* st, cudaStream_t s);
 void launch_ir_finalize(const double* partials, SolveState* state, double* hist, cudaStream_t s);
