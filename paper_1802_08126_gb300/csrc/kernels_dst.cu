@@ -270,10 +270,10 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
 // the forward direction is taken as the conjugate of the e^{-} transform of the conjugate.
 
 constexpr int kStockMaxN = 2048;
-constexpr int kStockThreads = 256;
+constexpr int kStockThreads = 256;  // (FP32: 4 CTAs per SM, FP64: 2 -- the register budget)
 
 template <typename T>
-__global__ void __launch_bounds__(kStockThreads, 2) k_dst_forward_s(T* x, long long S, ColGeom cg, DstPlan<T> plan,
+__global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_forward_s(T* x, long long S, ColGeom cg, DstPlan<T> plan,
                                                                  int F, const int* done) {
   using T2 = typename Vec2<T>::type;
   if (stop_requested(done)) return;
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kStockThreads, 2) k_dst_forward_s(T* x, long l
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kStockThreads, 2) k_dst_inverse_s(const T* __restrict__ y, void* out, int mode,
+__global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_inverse_s(const T* __restrict__ y, void* out, int mode,
                                                                  double omega, long long S, ColGeom cg,
                                                                  DstPlan<T> plan, int F, const int* done) {
   using T2 = typename Vec2<T>::type;

@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kDownTX = 16, kDownTY = 8;  // coarse points per down tile
 constexpr int kUpTX = 32, kUpTY = 16;     // fine points per up tile
+constexpr int kStripMinP = 64;            // fine levels at least this wide use the warp-strip kernels
 
 template <typename T>
 struct Mg2Args {
@@ -223,6 +224,251 @@ __global__ void __launch_bounds__(256) k_mg2_up(const T* __restrict__ bf, const 
   }
 }
 
+// ---- warp-strip forms of the two level kernels (fine levels with P >= 64) ----
+// A warp owns a band of consecutive fine columns, one per lane, and sweeps a strip of fine rows
+// keeping the rows above and below in registers; x-neighbours come from warp shuffles.  The
+// bands overlap by the halo so that no lane needs a value from outside its warp.
+
+constexpr int kStripDownCols = 14;  // coarse columns per down warp (fine columns 2X0-1 .. 2X0+29)
+constexpr int kStripDownRows = 16;  // coarse rows per down warp
+constexpr int kStripUpCols = 30;    // fine output columns per up warp (lanes 1..30)
+constexpr int kStripUpRows = 32;    // fine rows per up warp
+
+// Face coefficients (scaled by s/h^2) of the lane's point (y, x).  FP64: formed once per face --
+// the lane computes its lower x-face and upper y-face; the upper x-face is the lower x-face of
+// the lane to the right (shuffle) and the lower y-face is the upper y-face of the row before.
+template <typename T, bool VAR>
+struct Faces {
+  T xl, xr, yl, yu;
+};
+template <typename T, bool VAR>
+struct FaceSweep {
+  T gx;       // (s/h^2) c g_t g_x(x)
+  T yu_last;  // upper y-face of the previous row (= lower y-face of the next)
+  bool xok;   // 0 <= x <= n: the lane's lower x-face exists
+  __device__ __forceinline__ void init(const Mg2Args<T>& a, const T* nx, const T* fy, T cths, int x, int y) {
+    xok = x >= 0 && x <= a.nf;
+    gx = (VAR && x >= 0 && x < a.nf) ? cths * nx[x] : (T)0;
+    yu_last = (VAR && y >= 0 && y <= a.nf) ? fma(gx, fy[y], a.a0s) : a.a0s;
+  }
+  // faces of row y (every lane calls it, rows in increasing order).  Sharing saves FP64
+  // instructions; in FP32 the shuffle costs more than the two multiply-adds it replaces.
+  __device__ __forceinline__ Faces<T, VAR> row(const Mg2Args<T>& a, const T* fx, const T* ny, const T* fy, T cths,
+                                               int x, int y) {
+    Faces<T, VAR> f;
+    if (VAR && sizeof(T) == 4) {
+      f.xl = f.xr = f.yl = f.yu = (T)0;
+      if (y >= 0 && y < a.nf && x >= 0 && x < a.nf) {
+        const T gy = cths * ny[y];
+        f.xl = fma(gy, fx[x], a.a0s);
+        f.xr = fma(gy, fx[x + 1], a.a0s);
+        f.yl = fma(gx, fy[y], a.a0s);
+        f.yu = fma(gx, fy[y + 1], a.a0s);
+      }
+    } else if (VAR) {
+      const bool yok = y >= 0 && y < a.nf;
+      const T xl = (yok && xok) ? fma(cths * ny[y], fx[x], a.a0s) : (T)0;
+      f.xl = xl;
+      f.xr = __shfl_down_sync(0xffffffffu, xl, 1);
+      if ((threadIdx.x & 31) == 31) f.xr = (yok && x + 1 <= a.nf) ? fma(cths * ny[y], fx[x + 1], a.a0s) : (T)0;
+      f.yl = yu_last;
+      f.yu = (y + 1 >= 0 && y + 1 <= a.nf) ? fma(gx, fy[y + 1], a.a0s) : a.a0s;
+      yu_last = f.yu;
+    } else {
+      f.xl = f.xr = f.yl = f.yu = a.a0s;
+    }
+    return f;
+  }
+};
+
+template <typename T, bool VAR, int DM>
+__device__ __forceinline__ T jacobi_at(const Mg2Args<T>& a, int b, long long gi, const Faces<T, VAR>& f, T sig) {
+  if (DM == 0) return a.dinv[b];
+  if (DM == 1) return a.jinv[gi];
+  return a.omega / (sig + ((f.xl + f.xr) + (f.yl + f.yu)));
+}
+
+template <typename T, bool VAR, int DM>
+__global__ void __launch_bounds__(256) k_mg2s_down(const T* __restrict__ bf, T* __restrict__ bc, Mg2Args<T> a,
+                                                   int wpr, int strips, long long nwarps, const int* done) {
+  if (stop_requested(done)) return;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (wg >= nwarps) return;  // warp-uniform; no block-level barrier in this kernel
+  const int lane = threadIdx.x & 31;
+  const int wx = (int)(wg % wpr);
+  const long long rest = wg / wpr;
+  const int strip = (int)(rest % strips);
+  const int b = (int)(rest / strips);
+  const int X0 = kStripDownCols * wx, Y0 = kStripDownRows * strip;
+  const int x = 2 * X0 - 1 + lane;  // fine column of this lane
+  const int nf = a.nf, Pf = 1 << a.logPf, Pc = 1 << a.logPc;
+  const bool xin = x >= 0 && x < nf;
+  const long long base = (long long)b * a.Sf;
+  const T sig = a.sig[b];
+  const T cths = a.s_h2 * a.cth[b];
+  const T* nx = a.tab;
+  const T* fx = a.tab + Pf;
+  const T* ny = a.tab + 2 * Pf;
+  const T* fy = a.tab + 3 * Pf;
+  const int yfirst = 2 * Y0 - 1, ylast = 2 * (Y0 + kStripDownRows);  // x1 rows needed: yfirst .. ylast + 1
+  FaceSweep<T, VAR> fs;
+  fs.init(a, nx, fy, cths, x, yfirst);
+  // x1 = w D^-1 b and everything the residual at that row needs
+  auto row = [&](int y, T& bv, T& x1, Faces<T, VAR>& f) {
+    f = fs.row(a, fx, ny, fy, cths, x, y);
+    bv = (T)0;
+    x1 = (T)0;
+    if (xin && y >= 0 && y < nf) {
+      const long long gi = base + (long long)y * Pf + x;
+      bv = bf[gi];
+      x1 = bv * jacobi_at<T, VAR, DM>(a, b, gi, f, sig);
+    }
+  };
+  T bm, xm, bc_, xc, bn, xn;
+  Faces<T, VAR> fm, fc, fn;
+  row(yfirst, bm, xm, fm);
+  row(yfirst + 1, bc_, xc, fc);
+  T h1 = (T)0, h2 = (T)0;  // horizontal restrictions of the two previous rows
+  const bool out_lane = (lane & 1) == 0 && lane >= 2 && lane <= 28;
+  const int X = X0 + (lane >> 1) - 1;  // coarse column of an output lane (x = 2X + 1)
+  for (int y = yfirst + 1; y <= ylast; ++y) {
+    row(y + 1, bn, xn, fn);
+    // residual of x1 at row y
+    const T xW = __shfl_up_sync(0xffffffffu, xc, 1);
+    const T xE = __shfl_down_sync(0xffffffffu, xc, 1);
+    T r = (T)0;
+    if (xin && y >= 0 && y < nf) {
+      T Lx;
+      if (VAR)
+        Lx = sig * xc + fc.xl * (xc - xW) + fc.xr * (xc - xE) + fc.yl * (xc - xm) + fc.yu * (xc - xn);
+      else
+        Lx = (sig + (T)4 * a.a0s) * xc - a.a0s * ((xW + xE) + (xm + xn));
+      r = bc_ - Lx;
+    }
+    const T rW = __shfl_up_sync(0xffffffffu, r, 1);
+    const T rE = __shfl_down_sync(0xffffffffu, r, 1);
+    const T h = (T)0.25 * (rW + rE) + (T)0.5 * r;
+    // coarse row Y = (y - 2)/2 - ... : rows 2Y, 2Y+1, 2Y+2 are complete when y = 2Y + 2
+    if (y >= 2 * Y0 + 2 && ((y - 2 * Y0) & 1) == 0) {
+      const int Y = (y >> 1) - 1;
+      if (out_lane && X < a.nc && Y < a.nc)
+        bc[(long long)b * a.Sc + (long long)Y * Pc + X] = (T)0.25 * (h2 + h) + (T)0.5 * h1;
+    }
+    h2 = h1;
+    h1 = h;
+    bm = bc_;
+    xm = xc;
+    fm = fc;
+    bc_ = bn;
+    xc = xn;
+    fc = fn;
+  }
+  (void)bm;
+  (void)fm;
+}
+
+template <typename T, bool VAR, int DM>
+__global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const T* __restrict__ ec, void* out,
+                                                 int mode, int out_fp64, Mg2Args<T> a, int wpr, int strips,
+                                                 long long nwarps, const int* done) {
+  if (stop_requested(done)) return;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (wg >= nwarps) return;
+  const int lane = threadIdx.x & 31;
+  const int wx = (int)(wg % wpr);
+  const long long rest = wg / wpr;
+  const int strip = (int)(rest % strips);
+  const int b = (int)(rest / strips);
+  const int x = kStripUpCols * wx - 1 + lane;  // fine column; lanes 1..30 write
+  const int y0 = kStripUpRows * strip;
+  const int nf = a.nf, nc = a.nc, Pf = 1 << a.logPf, Pc = 1 << a.logPc;
+  const bool xin = x >= 0 && x < nf;
+  const long long base = (long long)b * a.Sf;
+  const long long cbase = (long long)b * a.Sc;
+  const T sig = a.sig[b];
+  const T cths = a.s_h2 * a.cth[b];
+  const T* nx = a.tab;
+  const T* fx = a.tab + Pf;
+  const T* ny = a.tab + 2 * Pf;
+  const T* fy = a.tab + 3 * Pf;
+  // x-interpolated coarse row Yc at this lane's column (0 outside the coarse interior)
+  const int cxa = (x & 1) ? (x - 1) >> 1 : (x >> 1) - 1;  // first coarse column used
+  auto crow = [&](int Yc) -> T {
+    if (Yc < 0 || Yc >= nc || !xin) return (T)0;
+    const T* er = ec + cbase + (long long)Yc * Pc;
+    if (x & 1) return er[cxa];
+    const T e0 = cxa >= 0 ? er[cxa] : (T)0;
+    const T e1 = cxa + 1 < nc ? er[cxa + 1] : (T)0;
+    return (T)0.5 * (e0 + e1);
+  };
+  // x2 = w D^-1 b + P e at row y, with b, faces and the Jacobi factor for the smoothing step
+  T ex_lo = (T)0;  // crow(k - 1) for the current even row 2k (cached from the odd row before)
+  int k_lo = -1000;
+  FaceSweep<T, VAR> fs;
+  fs.init(a, nx, fy, cths, x, y0 - 1);
+  auto row = [&](int y, T& bv, T& x2, T& jf, Faces<T, VAR>& f) {
+    f = fs.row(a, fx, ny, fy, cths, x, y);
+    bv = (T)0;
+    x2 = (T)0;
+    jf = (T)0;
+    // prolongation of the coarse correction (rows: odd y -> (y-1)/2, even y -> y/2 - 1 and y/2)
+    T pe;
+    if (y & 1) {
+      const int k = (y - 1) >> 1;
+      ex_lo = (k_lo == k) ? ex_lo : crow(k);
+      k_lo = k;
+      pe = ex_lo;
+    } else {
+      const int k = y >> 1;
+      const T lo = (k_lo == k - 1) ? ex_lo : crow(k - 1);
+      const T hi = crow(k);
+      pe = (T)0.5 * (lo + hi);
+      ex_lo = hi;
+      k_lo = k;
+    }
+    if (xin && y >= 0 && y < nf) {
+      const long long gi = base + (long long)y * Pf + x;
+      bv = bf[gi];
+      jf = jacobi_at<T, VAR, DM>(a, b, gi, f, sig);
+      x2 = fma(bv, jf, pe);
+    }
+  };
+  T bm, xm, jm, bcv, xc, jc, bn, xn, jn;
+  Faces<T, VAR> fm, fc, fn;
+  row(y0 - 1, bm, xm, jm, fm);
+  row(y0, bcv, xc, jc, fc);
+  const bool wlane = lane >= 1 && lane <= 30 && x < Pf;
+  for (int y = y0; y < y0 + kStripUpRows && y < Pf; ++y) {
+    row(y + 1, bn, xn, jn, fn);
+    const T xW = __shfl_up_sync(0xffffffffu, xc, 1);
+    const T xE = __shfl_down_sync(0xffffffffu, xc, 1);
+    if (wlane) {
+      const long long gi = base + (long long)y * Pf + x;
+      if (xin && y < nf) {
+        T Lx;
+        if (VAR)
+          Lx = sig * xc + fc.xl * (xc - xW) + fc.xr * (xc - xE) + fc.yl * (xc - xm) + fc.yu * (xc - xn);
+        else
+          Lx = (sig + (T)4 * a.a0s) * xc - a.a0s * ((xW + xE) + (xm + xn));
+        store_out<T>(out, gi, mode, out_fp64, xc + jc * (bcv - Lx));
+      } else if (mode == 0) {
+        store_out<T>(out, gi, 0, out_fp64, (T)0);
+      }
+    }
+    bm = bcv;
+    xm = xc;
+    jm = jc;
+    fm = fc;
+    bcv = bn;
+    xc = xn;
+    jc = jn;
+    fc = fn;
+  }
+  (void)bm;
+  (void)jm;
+  (void)fm;
+}
+
 // w D^-1 for every interior point of one level (FP64 variable-coefficient cache)
 template <typename T>
 __global__ void k_make_jinv(T* __restrict__ jinv, StencilGeom<T> g, OpBatch<T> op, long long total) {
@@ -276,7 +522,19 @@ void vcycle2d(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int 
     const double df = (double)B * a.nf * a.nf, dc = (double)B * a.nc * a.nc;
     LaunchScope ls("mg2_down", st, sizeof(T) * (df + dc) + (dm == 1 ? sizeof(T) * df : 0.0));
     T* bc = (T*)plan.buf[l + 1].b;
-    if (dm == 0)
+    // (FP64: the tile kernel spends fewer FP64 instructions per point on this level)
+    if (sizeof(T) == 4 && (1 << a.logPf) >= kStripMinP) {
+      const int wpr = (a.nc + kStripDownCols - 1) / kStripDownCols;
+      const int strips = (a.nc + kStripDownRows - 1) / kStripDownRows;
+      const long long nw = (long long)wpr * strips * B;
+      const unsigned blocks = (unsigned)((nw + 7) / 8);
+      if (dm == 0)
+        k_mg2s_down<T, false, 0><<<blocks, 256, 0, st>>>(bl, bc, a, wpr, strips, nw, done);
+      else if (dm == 1)
+        k_mg2s_down<T, true, 1><<<blocks, 256, 0, st>>>(bl, bc, a, wpr, strips, nw, done);
+      else
+        k_mg2s_down<T, true, 2><<<blocks, 256, 0, st>>>(bl, bc, a, wpr, strips, nw, done);
+    } else if (dm == 0)
       k_mg2_down<T, false, 0><<<grid, 256, 0, st>>>(bl, bc, a, done);
     else if (dm == 1)
       k_mg2_down<T, true, 1><<<grid, 256, 0, st>>>(bl, bc, a, done);
@@ -297,7 +555,18 @@ void vcycle2d(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int 
     const double ob = of ? (om == 1 ? 16.0 : 8.0) : (om == 1 ? 2.0 * sizeof(T) : (double)sizeof(T));
     LaunchScope ls("mg2_up", st, sizeof(T) * (df + dc) + ob * df + (dm == 1 ? sizeof(T) * df : 0.0));
     const T* e = (const T*)plan.buf[l + 1].x;
-    if (dm == 0)
+    if (Pf >= kStripMinP) {
+      const int wpr = (Pf + kStripUpCols - 1) / kStripUpCols;
+      const int strips = (Pf + kStripUpRows - 1) / kStripUpRows;
+      const long long nw = (long long)wpr * strips * B;
+      const unsigned blocks = (unsigned)((nw + 7) / 8);
+      if (dm == 0)
+        k_mg2s_up<T, false, 0><<<blocks, 256, 0, st>>>(bf, e, o, om, of, a, wpr, strips, nw, done);
+      else if (dm == 1)
+        k_mg2s_up<T, true, 1><<<blocks, 256, 0, st>>>(bf, e, o, om, of, a, wpr, strips, nw, done);
+      else
+        k_mg2s_up<T, true, 2><<<blocks, 256, 0, st>>>(bf, e, o, om, of, a, wpr, strips, nw, done);
+    } else if (dm == 0)
       k_mg2_up<T, false, 0><<<grid, 256, 0, st>>>(bf, e, o, om, of, a, done);
     else if (dm == 1)
       k_mg2_up<T, true, 1><<<grid, 256, 0, st>>>(bf, e, o, om, of, a, done);

@@ -101,7 +101,9 @@ def test_apply_B_matches_oracle(prob):
     assert np.abs(host(out) - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("prob", SMALL[:4], ids=lambda p: p.name)
+# 63^2 and 127^2 reach the warp-strip level kernels (fine levels of width >= 64)
+@pytest.mark.parametrize("prob", SMALL[:4] + [S.heat2d_uniform(63, 3), S.heat2d_uniform(127, 2)],
+                         ids=lambda p: p.name)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("cycles", [1, 2, 3])
 def test_vcycle_preconditioners_match_oracle_vcycle(prob, precision, cycles):
