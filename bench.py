@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -141,6 +142,61 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def fp64_peak_tflops(peaks):
+    """FP64 pipe peak of the GB300: 152 SMs x 2 FP64 FMA lanes per clock x 2 flop x max SM clock."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
+
+
+def fp64_flops_per_launch(name, dim, n, N):
+    """Algorithmic FP64 flops of one launch of a kernel of the FP64 path (2-D workloads).
+
+    Transforms use the standard count for a real-input FFT of length L, 2.5 L log2 L per line; a
+    DST-I of n points is one such FFT of length M = n + 1, the temporal DST one of length N.
+    Stencil kernels count the flops of the formulas they evaluate per interior point (face
+    coefficients a0 + c g g: 2 each; 5-point variable-coefficient stencil: 11)."""
+    if dim != 2:
+        return None
+    M = n + 1
+    pts = float(N) * n * n
+    fft_M = 2.5 * M * math.log2(M)
+    if name == "dsti_cols_scale":   # two y-transforms of every x-column + the scale factor
+        return N * n * 2 * fft_M + 10.0 * pts
+    if name == "dsti_rows":
+        return N * n * fft_M
+    if name in ("dst_forward", "dst_inverse"):  # N-point transform of every spatial point + twiddles
+        return n * n * (2.5 * N * math.log2(N) + 6.0 * N)
+    if name == "resid_bres":        # bres (faces 8, stencil 11, K and F 3, norm 2) + r_p (13)
+        return 37.0 * pts
+    if name == "mg2_up":            # 3 launches (levels 0, 1, 2): prolong 5, stencil 19, smoothing 4
+        return 28.0 * pts * (1 + 0.25 + 0.0625) / 3
+    if name == "mg2_down":          # x1 1, stencil 19, residual 1, restriction 9/4
+        return 23.25 * pts * (1 + 0.25 + 0.0625) / 3
+    return None
+
+
+def roofline_of(prof, name, bound_fp64, dims, peaks, peak_src, tr):
+    d = prof[name]
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    share = d["ms"] / sum(v["ms"] for v in prof.values())
+    base = {"kernel": name, "traffic": tr.get((name, WORKLOAD)),
+            "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+            "avg_launch_ms": per_launch_ms, "share": share}
+    fl = fp64_flops_per_launch(name, *dims) if bound_fp64 else None
+    if fl is not None:
+        tf = fl / (per_launch_ms / 1e3) / 1e12
+        pk = fp64_peak_tflops(peaks)
+        base.update({"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk,
+                     "algorithmic_flops_per_launch": fl, "hbm_GBps": gbs,
+                     "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz (%s clock)"
+                                    % (float(peaks.get("sm_max_mhz", 2070.0)), peak_src)})
+    else:
+        base.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_src})
+    return base
 
 
 def traffic_table():
@@ -448,21 +504,13 @@ def main():
         ms = t.item()
     value = ws * dofs * args.steps / (ms / 1e3)
 
-    # roofline of the dominant kernel (largest share of the timed region)
+    # roofline of the dominant kernel (largest share of the timed region): FP64-pipe bound for the
+    # FP64 kernels of the FP64 path, HBM bound otherwise
     peaks, peak_src = load_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
-    roof = None
-    if dom is not None:
-        name, d = dom
-        per_launch_ms = d["ms"] / max(d["launches"], 1)
-        gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        tr = traffic_table()
-        traffic = tr.get((name, WORKLOAD))
-        roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
-                "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
-                "avg_launch_ms": per_launch_ms, "share": d["ms"] / sum(v["ms"] for v in prof.values()),
-                "peak_source": peak_src}
+    tr = traffic_table()
+    dims = (prob.dim, prob.n[0], prob.N)
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
+    roof = roofline_of(prof, dom, base_prec == "fp64", dims, peaks, peak_src, tr) if dom else None
     phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                   "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
@@ -523,7 +571,10 @@ def main():
             t = torch.tensor([mms], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             mms = t.item()
+        vdom = max(vprof.items(), key=lambda kv: kv[1]["ms"])[0] if vprof else None
         mixed = {"precision": variant, "value": ws * dofs * vsteps / (mms / 1e3), "unit": "DOF/s",
+                 "roofline": roofline_of(vprof, vdom, variant == "fp64", dims, peaks, peak_src, tr)
+                 if vdom else None,
                  "ms_per_step": mms / vsteps, "iterations": mits[-1],
                  "rel_l2_mixed_vs_fp64_path": float(np.linalg.norm(um - u64) / np.linalg.norm(u64)),
                  "kernels": {k: {"ms_per_step": v["ms"] / vsteps, "launches_per_step": v["launches"] / vsteps,
