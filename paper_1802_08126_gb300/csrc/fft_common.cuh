@@ -194,6 +194,48 @@ __device__ __forceinline__ T2* warp_fft(T2* a, T2* b, int logM, const T2* __rest
   return a;
 }
 
+// Compile-time length (LOGM > 0): the same passes with every trip count, stride and shift a
+// constant, fully unrolled.
+template <int LR, int LOGM, int S, typename T2>
+__device__ __forceinline__ void stockham_pass_c(const T2* __restrict__ in, T2* __restrict__ out,
+                                                const T2* __restrict__ tw, int lane) {
+  constexpr int R = 1 << LR;
+  constexpr int NB = 1 << (LOGM - LR);
+  constexpr int P = 1 << S;
+  constexpr int TSH = LOGM - S - LR;
+#pragma unroll
+  for (int i0 = 0; i0 < NB; i0 += 32) {
+    const int i = i0 + lane;
+    if (NB >= 32 || i < NB) {
+      const int k = i & (P - 1);
+      T2 u[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) u[m] = in[pd(i + m * NB)];
+      if (S > 0) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) u[m] = cmul(u[m], __ldg(&tw[(m * k) << TSH]));
+      }
+      dftR<LR>(u);
+      const int j = ((i - k) << LR) + k;
+#pragma unroll
+      for (int m = 0; m < R; ++m) out[pd(j + m * P)] = u[m];
+    }
+  }
+}
+
+template <int LOGM, int S, typename T2>
+__device__ __forceinline__ T2* warp_fft_c(T2* a, T2* b, const T2* __restrict__ tw, int lane) {
+  if constexpr (S >= LOGM) {
+    return a;
+  } else {
+    constexpr int REM = LOGM - S;
+    constexpr int LR = (REM >= 5 || REM == 3) ? 3 : (REM == 4 || REM == 2) ? 2 : 1;
+    stockham_pass_c<LR, LOGM, S>(a, b, tw, lane);
+    __syncwarp();
+    return warp_fft_c<LOGM, S + LR>(b, a, tw, lane);
+  }
+}
+
 // Block-cooperative Stockham pass: the FFTs of a CTA each own `nthr` threads (tid = thread index
 // within its FFT) and every thread holds 8 values (N >= 8); read all, barrier, write all, barrier,
 // so the pass is done in place.  Every thread of the CTA must call it.

@@ -284,16 +284,27 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* sm = (T2*)smem_raw;
   const long long c0 = (long long)blockIdx.x * 2 * F;
-  // load: slot m = N-1-t holds (w_a, w_b); the m = 0 entry is doubled
-  for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
-    const int f = idx % F, t = idx / F;
-    T2 v = *(const T2*)(x + (long long)t * S + c0 + 2 * f);
-    const int m = N - 1 - t;
-    if (m == 0) {
-      v.x *= (T)2;
-      v.y *= (T)2;
+  // load: slot m = N-1-t holds (w_a, w_b); the m = 0 entry is doubled.  Four loads in flight
+  // per thread (the loads are latency-bound at this occupancy).
+  for (int idx0 = threadIdx.x; idx0 < N * F; idx0 += 4 * blockDim.x) {
+    T2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = idx0 + q * blockDim.x;
+      if (idx < N * F) v[q] = *(const T2*)(x + (long long)(idx / F) * S + c0 + 2 * (idx % F));
     }
-    sm[(size_t)f * Lp + pd(m)] = v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = idx0 + q * blockDim.x;
+      if (idx < N * F) {
+        const int f = idx % F, m = N - 1 - idx / F;
+        if (m == 0) {
+          v[q].x *= (T)2;
+          v[q].y *= (T)2;
+        }
+        sm[(size_t)f * Lp + pd(m)] = v[q];
+      }
+    }
   }
   __syncthreads();
   // pre-twiddle in pairs (m, N-m): V[m] = e^{i pi m/(2N)} (w_m - i w_{N-m}), Z = V_a + i V_b,
@@ -350,18 +361,29 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
   T2* sm = (T2*)smem_raw;
   const long long c0 = (long long)blockIdx.x * 2 * F;
   // load: z_j = (-1)^j y_{j+1};  v_{j/2} = z_j (j even), v_{N-1-(j-1)/2} = z_j (j odd)
-  for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
-    const int f = idx % F, j = idx / F;
-    T2 v = *(const T2*)(y + (long long)j * S + c0 + 2 * f);
-    int s;
-    if (j & 1) {
-      s = N - 1 - (j >> 1);
-      v.x = -v.x;
-      v.y = -v.y;
-    } else {
-      s = j >> 1;
+  for (int idx0 = threadIdx.x; idx0 < N * F; idx0 += 4 * blockDim.x) {
+    T2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = idx0 + q * blockDim.x;
+      if (idx < N * F) v[q] = *(const T2*)(y + (long long)(idx / F) * S + c0 + 2 * (idx % F));
     }
-    sm[(size_t)f * Lp + pd(s)] = v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = idx0 + q * blockDim.x;
+      if (idx < N * F) {
+        const int f = idx % F, j = idx / F;
+        int s;
+        if (j & 1) {
+          s = N - 1 - (j >> 1);
+          v[q].x = -v[q].x;
+          v[q].y = -v[q].y;
+        } else {
+          s = j >> 1;
+        }
+        sm[(size_t)f * Lp + pd(s)] = v[q];
+      }
+    }
   }
   __syncthreads();
   {

@@ -26,9 +26,11 @@ constexpr int kWarpsMax = 8;
 
 // z_j = (y^a_j + i y^b_j) / 2 from x_j = read(j - 1) (position j-1 holds x_j, x_0 = x_M = 0);
 // sn[j] = sin(pi j / M) / 2 for j <= M/2.
-template <typename T, typename T2, typename Read>
-__device__ __forceinline__ void dsti_pre(T2* z, int M, const T* __restrict__ sn, int lane, Read read) {
+template <int LOGMC, typename T, typename T2, typename Read>
+__device__ __forceinline__ void dsti_pre(T2* z, int M_rt, const T* __restrict__ sn, int lane, Read read) {
+  const int M = LOGMC > 0 ? (1 << LOGMC) : M_rt;
   const int H = M >> 1;
+#pragma unroll
   for (int j = lane; j <= H; j += 32) {
     if (j == 0) {
       z[0] = mk<T2>((T)0, (T)0);
@@ -45,8 +47,9 @@ __device__ __forceinline__ void dsti_pre(T2* z, int M, const T* __restrict__ sn,
 
 // From the spectrum Z of the packed pair: write(pos, (S^a, S^b)) for every position 0 .. M-1
 // (S_q at position q-1, the ghost position M-1 gets 0).
-template <typename T, typename T2, typename Write>
-__device__ __forceinline__ void dsti_post(const T2* Z, int M, int lane, Write write) {
+template <int LOGMC, typename T, typename T2, typename Write>
+__device__ __forceinline__ void dsti_post(const T2* Z, int M_rt, int lane, Write write) {
+  const int M = LOGMC > 0 ? (1 << LOGMC) : M_rt;
   const int H = M >> 1;
   const int K = H >= 32 ? H >> 5 : 1;  // k's per lane, contiguous
   const int k0 = lane * K;
@@ -60,6 +63,7 @@ __device__ __forceinline__ void dsti_post(const T2* Z, int M, int lane, Write wr
   };
   T ta = (T)0, tb = (T)0;
   if (act) {
+#pragma unroll
     for (int q = 0; q < K; ++q) {
       const T2 c = contrib(k0 + q);
       ta += c.x;
@@ -79,6 +83,7 @@ __device__ __forceinline__ void dsti_post(const T2* Z, int M, int lane, Write wr
   }
   if (!act) return;
   T pa = ia - ta, pb = ib - tb;
+#pragma unroll
   for (int q = 0; q < K; ++q) {
     const int k = k0 + q;
     const T2 c = contrib(k);
@@ -92,6 +97,14 @@ __device__ __forceinline__ void dsti_post(const T2* Z, int M, int lane, Write wr
       write(2 * k - 1, mk<T2>(zm.y - zk.y, zk.x - zm.x));  // S_{2k} = -I_k
     }
   }
+}
+
+template <int LOGMC, typename T2>
+__device__ __forceinline__ T2* fft_any(T2* a, T2* b, int logM, const T2* __restrict__ tw, int lane) {
+  if constexpr (LOGMC > 0)
+    return warp_fft_c<LOGMC, 0>(a, b, tw, lane);
+  else
+    return warp_fft<T2>(a, b, logM, tw, lane);
 }
 
 // 1 / d for d > 0 in FP64: single-precision reciprocal and one Newton-Raphson step
@@ -111,11 +124,12 @@ struct DstiTabs {
 };
 
 // Rows (x, contiguous): every line pair of every slice, in place.  Lines 2q and 2q+1.
-template <typename T>
-__global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x, int logM, int dim,
+template <typename T, int LOGMC>
+__global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x, int logM_rt, int dim,
                                                               long long npairs, DstiTabs<T> tb) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int logM = LOGMC > 0 ? LOGMC : logM_rt;
   const int M = 1 << logM;
   const int W = padded_len(M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -126,11 +140,11 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x,
     const long long la = 2 * pr;
     T* xa = x + la * M;
     T* xb = xa + M;
-    dsti_pre<T, T2>(A, M, tb.sn, lane, [&](int pos) { return mk<T2>(xa[pos], xb[pos]); });
+    dsti_pre<LOGMC, T, T2>(A, M, tb.sn, lane, [&](int pos) { return mk<T2>(xa[pos], xb[pos]); });
     __syncwarp();
-    T2* Z = warp_fft<T2>(A, B, logM, tb.tw, lane);
+    T2* Z = fft_any<LOGMC>(A, B, logM, tb.tw, lane);
     T2* O = Z == A ? B : A;
-    dsti_post<T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
+    dsti_post<LOGMC, T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
     __syncwarp();
     // ghost lines: y == n (2-D and 3-D) or z == n (3-D)
     auto ghost = [&](long long l) {
@@ -138,6 +152,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x,
       return y == M - 1 || (dim == 3 && ((l >> logM) & (M - 1)) == M - 1);
     };
     const bool ga = ghost(la), gb = ghost(la + 1);
+#pragma unroll
     for (int pos = lane; pos < M; pos += 32) {
       const T2 v = O[pd(pos)];
       xa[pos] = ga ? (T)0 : v.x;
@@ -150,12 +165,13 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x,
 // Columns along a strided axis (1: y, stride M; 2: z, stride M^2), in place.  A block takes 2C
 // consecutive columns (x .. x + 2C - 1) of one plane of one slice; warp w transforms columns
 // 2w, 2w+1.  With `scale`, the column pair gets S diag(g) S, g the exact block-solve factor.
-template <typename T>
-__global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x, int logM, int dim, int axis,
+template <typename T, int LOGMC>
+__global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x, int logM_rt, int dim, int axis,
                                                               long long S, int scale, T tau, T c0,
                                                               DstiTabs<T> tb) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int logM = LOGMC > 0 ? LOGMC : logM_rt;
   const int M = 1 << logM;
   const int W = padded_len(M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -180,9 +196,9 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x,
   T2* B = A + W;
   const int xa = x0 + 2 * warp;
   const bool ghost_o = dim == 3 && o == M - 1;
-  dsti_pre<T, T2>(B, M, tb.sn, lane, [&](int pos) { return A[pd(pos)]; });
+  dsti_pre<LOGMC, T, T2>(B, M, tb.sn, lane, [&](int pos) { return A[pd(pos)]; });
   __syncwarp();
-  T2* Z = warp_fft<T2>(B, A, logM, tb.tw, lane);
+  T2* Z = fft_any<LOGMC>(B, A, logM, tb.tw, lane);
   T2* O = Z == A ? B : A;
   if (scale) {
     // g = c0 l / (mu + tau l)^2, l = lam_x + lam_axis (+ lam_y in 3-D); 0 on ghost columns
@@ -190,7 +206,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x,
     const T lo = dim == 3 ? tb.lam[o] : (T)0;
     const T la = tb.lam[xa] + lo, lb = tb.lam[xa + 1] + lo;
     const bool za = xa == M - 1 || ghost_o, zb = xa + 1 == M - 1 || ghost_o;
-    dsti_post<T, T2>(Z, M, lane, [&](int pos, T2 v) {
+    dsti_post<LOGMC, T, T2>(Z, M, lane, [&](int pos, T2 v) {
       const T ly = tb.lam[pos];
       const T l1 = la + ly, l2 = lb + ly;
       const T r1 = recip_pos(fma(tau, l1, mu)), r2 = recip_pos(fma(tau, l2, mu));
@@ -199,14 +215,14 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x,
     });
     __syncwarp();
     T2* P2 = O == A ? B : A;
-    dsti_pre<T, T2>(P2, M, tb.sn, lane, [&](int pos) { return O[pd(pos)]; });
+    dsti_pre<LOGMC, T, T2>(P2, M, tb.sn, lane, [&](int pos) { return O[pd(pos)]; });
     __syncwarp();
-    T2* Z2 = warp_fft<T2>(P2, O, logM, tb.tw, lane);
+    T2* Z2 = fft_any<LOGMC>(P2, O, logM, tb.tw, lane);
     T2* O2 = Z2 == A ? B : A;
-    dsti_post<T, T2>(Z2, M, lane, [&](int pos, T2 v) { O2[pd(pos)] = v; });
+    dsti_post<LOGMC, T, T2>(Z2, M, lane, [&](int pos, T2 v) { O2[pd(pos)] = v; });
     O = O2;
   } else {
-    dsti_post<T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
+    dsti_post<LOGMC, T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
   }
   // every warp's result sits in the same one of its two buffers
   const int off = (int)(O - A);
@@ -247,19 +263,24 @@ void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const 
   const int M = n + 1;
   const int wpb = warps_for<T>(M);
   const size_t smem = (size_t)wpb * (2 * padded_len(M) + 1) * sizeof(T2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_dsti_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    attr = true;
-  }
   const long long npairs = (long long)B * (S / M) / 2;
   long long blocks = (npairs + wpb - 1) / wpb;
   if (blocks > (1LL << 30)) blocks = 1LL << 30;
   double d = B;
   for (int k = 0; k < dim; ++k) d *= n;
   LaunchScope ls("dsti_rows", st, 2.0 * sizeof(T) * d);
-  k_dsti_rows<T><<<(unsigned)blocks, wpb * 32, smem, st>>>(x, logP, dim, npairs,
-                                                           tabs<T>(tw, sn, nullptr, nullptr));
+  // (every length's kernel has the same pointer type: the attribute flag is kept per length)
+  static bool attr[32] = {};
+  auto go = [&](auto kern) {
+    if (!attr[logP]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+      attr[logP] = true;
+    }
+    kern<<<(unsigned)blocks, wpb * 32, smem, st>>>(x, logP, dim, npairs, tabs<T>(tw, sn, nullptr, nullptr));
+  };
+  // (the run-time-length kernel: unrolling the row transform raises its register count past
+  // what its occupancy can afford, measured slower in both precisions)
+  go(k_dsti_rows<T, 0>);
 }
 
 template <typename T>
@@ -271,18 +292,33 @@ void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int ax
   int C = warps_for<T>(M);
   while (2 * C > M && C > 1) C >>= 1;
   const size_t smem = (size_t)C * (2 * padded_len(M) + 1) * sizeof(T2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_dsti_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    attr = true;
-  }
   const long long planes = dim == 3 ? M : 1;
   const dim3 grid((unsigned)((M / (2 * C)) * planes), (unsigned)B);
   double d = B;
   for (int k = 0; k < dim; ++k) d *= n;
   LaunchScope ls(scale ? "dsti_cols_scale" : "dsti_cols", st, 2.0 * sizeof(T) * d);
-  k_dsti_cols<T><<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, (T)tau, (T)c0,
-                                             tabs<T>(tw, sn, lam, mu));
+  static bool attr[32] = {};
+  auto go = [&](auto kern) {
+    if (!attr[logP]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+      attr[logP] = true;
+    }
+    kern<<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, (T)tau, (T)c0, tabs<T>(tw, sn, lam, mu));
+  };
+  // FP32: compile-time lengths (instruction-bound, the unrolled form measured 11 % faster);
+  // FP64: bound by the FP64 pipe either way, the run-time-length kernel (fewer registers)
+  if (sizeof(T) == 4) {
+    switch (logP) {
+      case 5: go(k_dsti_cols<T, 5>); break;
+      case 6: go(k_dsti_cols<T, 6>); break;
+      case 7: go(k_dsti_cols<T, 7>); break;
+      case 8: go(k_dsti_cols<T, 8>); break;
+      case 9: go(k_dsti_cols<T, 9>); break;
+      default: go(k_dsti_cols<T, 0>); break;
+    }
+  } else {
+    go(k_dsti_cols<T, 0>);
+  }
 }
 
 template void launch_dsti_rows<float>(float*, int, int, int, long long, int, const void*, const void*,

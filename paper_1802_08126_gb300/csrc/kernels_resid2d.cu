@@ -18,13 +18,21 @@ namespace {
 
 constexpr int kRows = 16;
 
-template <typename W>
+// IR = true: the FP64 step of the mixed-precision refinement -- instead of bres and r_p it writes
+// the FP32 right-hand sides R1 = bres + tau A w, R2 = bres - K^T w and r_p' = -R1, and runs only
+// on refinement iterations (state flags).
+template <typename W, bool IR>
 __global__ void __launch_bounds__(256) k_resid_bres_2d(
     const double* __restrict__ u, const double* __restrict__ p, const double* __restrict__ F,
     double* __restrict__ bres, W* __restrict__ rp, double* __restrict__ partials,
     const double* __restrict__ tab, const float* __restrict__ tabf, const double* __restrict__ cth,
-    double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, const int* done) {
-  if (stop_requested(done)) return;
+    double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, const int* done,
+    float* __restrict__ R1, float* __restrict__ R2, const SolveState* st) {
+  if (IR) {
+    if (*((volatile const int*)&st->done) != 0 || !*((volatile const int*)&st->outer)) return;
+  } else if (stop_requested(done)) {
+    return;
+  }
   const int P = 1 << logP;
   const int lane = threadIdx.x & 31;
   double acc = 0.0;
@@ -79,6 +87,7 @@ __global__ void __launch_bounds__(256) k_resid_bres_2d(
       const float ayuf = fmaf(gxcf, fyf[y + 1 < P ? y + 1 : y], a0f);
       double b = 0.0;
       W r = (W)0;
+      float r1 = 0.f, r2 = 0.f;
       if (xin && yin) {
         const long long i = at(y);
         const double gy = ct * ny[y];
@@ -98,11 +107,25 @@ __global__ void __launch_bounds__(256) k_resid_bres_2d(
           sw = (W)(axl * ((double)w_c - (double)wW) + axr * ((double)w_c - (double)wE) +
                    ayl * ((double)w_c - (double)w_m) + ayu * ((double)w_c - (double)w_p));
         }
-        r = (W)(-b) - sw;
+        if (IR) {
+          const long long in = i + S;
+          const double wn = t + 1 < N ? p[in] + u[in] : 0.0;
+          const double wc = p[i] + u_c;
+          r1 = (float)b + (float)sw;
+          r2 = (float)(b - (wc - wn));
+        } else {
+          r = (W)(-b) - sw;
+        }
       }
       if (y < P) {
-        bres[at(y)] = b;
-        rp[at(y)] = r;
+        if (IR) {
+          R1[at(y)] = r1;
+          R2[at(y)] = r2;
+          rp[at(y)] = (W)(-r1);
+        } else {
+          bres[at(y)] = b;
+          rp[at(y)] = r;
+        }
       }
       u_m = u_c;
       u_c = u_p;
@@ -127,8 +150,22 @@ void launch_resid_bres_2d(const double* u, const double* p, const double* F, dou
   const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("resid_bres", st, (24.0 + 8.0 + sizeof(W)) * (double)n * n * N);
-  k_resid_bres_2d<W><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth, s_h2 * a0,
-                                                       s_h2, n, logP, S, N, nwarps, done);
+  k_resid_bres_2d<W, false><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth, s_h2 * a0,
+                                                              s_h2, n, logP, S, N, nwarps, done, nullptr, nullptr,
+                                                              nullptr);
+}
+
+void launch_ir_outer_2d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
+                        double* partials, const double* tab, const float* tabf, const double* cth, double a0,
+                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
+                        cudaStream_t s) {
+  const int P = 1 << logP;
+  const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
+  const double s_h2 = tau / (h * h);
+  LaunchScope ls("ir_outer", s, (24.0 + 12.0) * (double)n * n * N);
+  k_resid_bres_2d<float, true><<<kReduceBlocks, 256, 0, s>>>(u, p, F, nullptr, rp, partials, tab, tabf, cth,
+                                                               s_h2 * a0, s_h2, n, logP, S, N, nwarps, nullptr, R1,
+                                                               R2, st);
 }
 
 template void launch_resid_bres_2d<float>(const double*, const double*, const double*, double*, float*, double*,

@@ -156,7 +156,12 @@ void launch_ir_outer(const double* u, const double* p, const double* F, float* R
 void launch_ir_inner(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                      double* partials, StencilGeom<float> g, const float* cth, float tau, int N,
                      const SolveState* st, cudaStream_t s);
-// 2-D (n + 1 >= 32) warp-strip form of launch_ir_inner (kernels_resid2d.cu); tabf: level-0 FP32 tables
+// 2-D (n + 1 >= 32) warp-strip forms of launch_ir_outer / launch_ir_inner (kernels_resid2d.cu);
+// tab / tabf: level-0 FP64 / FP32 tables
+void launch_ir_outer_2d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
+                        double* partials, const double* tab, const float* tabf, const double* cth, double a0,
+                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
+                        cudaStream_t s);
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
                         int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s);

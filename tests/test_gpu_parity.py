@@ -126,7 +126,7 @@ def test_vcycle_preconditioners_match_oracle_vcycle(prob, precision, cycles):
 
 @pytest.mark.parametrize("prob", [S.heat2d_uniform(15, 8), S.heat2d_uniform(31, 12), S.heat2d_uniform(7, 2),
                                   S.heat2d_uniform(63, 5), S.heat2d_uniform(1, 4), S.heat2d_uniform(3, 3),
-                                  S.heat2d_uniform(127, 2)], ids=lambda p: p.name)
+                                  S.heat2d_uniform(127, 2), S.heat2d_uniform(255, 2)], ids=lambda p: p.name)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_exact_transform_H_matches_oracle_direct_solves(prob, precision):
     """H~^-1 with exact H_k solves done by spatial sine transforms equals Phi^-1 Hhat^-1 Phi^-T
