@@ -98,8 +98,9 @@ typedef struct {
   int no_graphs;         /* 1: launch kernels one by one instead of replaying a captured CUDA
                             graph of the iteration (kernel timing via pt_profile_* also does) */
   int h_solver;          /* H_k solves of the Schur preconditioner: 0 = automatic (exact, by spatial
-                            sine transforms, when the reference coefficient is constant and
-                            dim == 2; else V-cycles), 1 = V-cycles, 2 = exact (error if unavailable) */
+                            sine transforms, when the reference coefficient is constant in space,
+                            dim is 2 or 3 and n + 1 <= 4096; else V-cycles), 1 = V-cycles,
+                            2 = exact (PT_EINVAL if unavailable) */
   int reserved[2];       /* must be zero */
 } pt_options;
 

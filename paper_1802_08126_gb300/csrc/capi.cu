@@ -335,9 +335,17 @@ T* block_solve(pt_problem* p, const int* done) {
   if (p->hdst) {
     const Level& L = p->lev[0];
     const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
+    // x, (y,) the last axis forward-scale-inverse, (y,) x: S_x S_y S_z diag(g) S_z S_y S_x
+    const int last = p->dim - 1;
     launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
-    launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_lam, p->dsti_mu,
-                        p->tau, c0, true, p->st);
+    if (p->dim == 3)
+      launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_lam,
+                          p->dsti_mu, p->tau, c0, false, p->st);
+    launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, last, p->dsti_tw, p->dsti_sn, p->dsti_lam,
+                        p->dsti_mu, p->tau, c0, true, p->st);
+    if (p->dim == 3)
+      launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_lam,
+                          p->dsti_mu, p->tau, c0, false, p->st);
     launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
     return W1;
   }
@@ -768,8 +776,8 @@ pt_status setup_precision(pt_problem* p) {
       if ((st = upload<T>(p, p->dinvH[l], dv)) != PT_OK) return st;
     }
   }
-  // exact H_k solves by spatial sine transforms (constant reference coefficient, 2-D)
-  p->hdst = !p->exact1d && p->dim == 2 && !p->hvar && p->opt.h_solver != 1 && p->n + 1 <= kDstiMaxM;
+  // exact H_k solves by spatial sine transforms (constant reference coefficient, 2-D and 3-D)
+  p->hdst = !p->exact1d && p->dim >= 2 && !p->hvar && p->opt.h_solver != 1 && p->n + 1 <= kDstiMaxM;
   if (p->hdst) {
     const int M = p->n + 1;
     std::vector<double> tw(2 * M), sn(M / 2 + 1), lam(M, 0.0), mud(mu.begin(), mu.end());
@@ -793,7 +801,7 @@ pt_status setup_precision(pt_problem* p) {
     if ((st = upload<T>(p, p->dsti_mu, mud)) != PT_OK) return st;
   } else if (p->opt.h_solver == 2) {
     return fail(PT_EINVAL,
-                "exact H_k solves need dim == 2, n + 1 <= 4096 and a reference coefficient constant in space");
+                "exact H_k solves need dim >= 2, n + 1 <= 4096 and a reference coefficient constant in space");
   }
   // FP64 2-D: cache w / D of every tau A_n (a division per point per smoothing step otherwise)
   if (!p->exact1d && p->dim == 2 && sizeof(T) == 8) {

@@ -126,7 +126,8 @@ def test_vcycle_preconditioners_match_oracle_vcycle(prob, precision, cycles):
 
 @pytest.mark.parametrize("prob", [S.heat2d_uniform(15, 8), S.heat2d_uniform(31, 12), S.heat2d_uniform(7, 2),
                                   S.heat2d_uniform(63, 5), S.heat2d_uniform(1, 4), S.heat2d_uniform(3, 3),
-                                  S.heat2d_uniform(127, 2), S.heat2d_uniform(255, 2)], ids=lambda p: p.name)
+                                  S.heat2d_uniform(127, 2), S.heat2d_uniform(255, 2), S.heat3d_bumps(7, 4),
+                                  S.heat3d_bumps(15, 3), S.heat3d_bumps(31, 2)], ids=lambda p: p.name)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_exact_transform_H_matches_oracle_direct_solves(prob, precision):
     """H~^-1 with exact H_k solves done by spatial sine transforms equals Phi^-1 Hhat^-1 Phi^-T
@@ -184,8 +185,8 @@ def test_heat1d_exact_solves_matches_oracle_and_mirror_history():
                          ids=lambda p: p.name)
 @pytest.mark.parametrize("hsol", ["vcycle", "exact"])
 def test_multigrid_solve_history_and_solution(prob, hsol):
-    if hsol == "exact" and prob.dim != 2:
-        pytest.skip("transform H_k solves are 2-D")
+    if hsol == "exact" and prob.dim == 1:
+        pytest.skip("transform H_k solves are 2-D and 3-D (1-D has its own exact solves)")
     f, u0 = S.source(prob), S.initial(prob)
     T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
     F = T.rhs(f, u0)
