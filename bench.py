@@ -162,8 +162,8 @@ def fp64_flops_per_launch(name, dim, n, N):
     M = n + 1
     pts = float(N) * n * n
     fft_M = 2.5 * M * math.log2(M)
-    if name == "dsti_cols_scale":   # two y-transforms of every x-column + the scale factor
-        return N * n * 2 * fft_M + 10.0 * pts
+    if name == "dsti_cols_scale":   # two y-transforms of every x-column + the product with the
+        return N * n * 2 * fft_M + 1.0 * pts  # precomputed block-solve factor
     if name == "dsti_rows":
         return N * n * fft_M
     if name in ("dst_forward", "dst_inverse"):  # N-point transform of every spatial point + twiddles
@@ -479,8 +479,6 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    ptu.profile_reset()
-    ptu.profile_enable(True)
     launches0 = ptu.launch_count()
     barrier()
     torch.cuda.synchronize()
@@ -495,9 +493,21 @@ def main():
     barrier()
     ms = ev0.elapsed_time(ev1)
     launches = ptu.launch_count() - launches0
+    clk = clocks.stop()
+    # the same steps again with a CUDA event pair around every kernel (graphs off): per-kernel
+    # times for the breakdown and the roofline (the value above is measured without them)
+    ptu.profile_reset()
+    ptu.profile_enable(True)
+    torch.cuda.synchronize()
+    e0p, e1p = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0p.record()
+    for _ in range(args.steps):
+        solve_once(P)
+    e1p.record()
+    torch.cuda.synchronize()
+    ms_prof = e0p.elapsed_time(e1p)
     ptu.profile_enable(False)
     prof = ptu.profile_totals()
-    clk = clocks.stop()
     if dist is not None:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -549,8 +559,6 @@ def main():
         vsteps = args.steps if variant == "mixed" else 1
         if variant == "mixed":
             solve_once(Pm)
-        ptu.profile_reset()
-        ptu.profile_enable(True)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -562,6 +570,11 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         mms = e0.elapsed_time(e1)
+        # per-kernel breakdown from one more solve with kernel events
+        ptu.profile_reset()
+        ptu.profile_enable(True)
+        solve_once(Pm)
+        torch.cuda.synchronize()
         ptu.profile_enable(False)
         vprof = ptu.profile_totals()
         um = np.zeros((prob.N, prob.ns))
@@ -577,7 +590,7 @@ def main():
                  if vdom else None,
                  "ms_per_step": mms / vsteps, "iterations": mits[-1],
                  "rel_l2_mixed_vs_fp64_path": float(np.linalg.norm(um - u64) / np.linalg.norm(u64)),
-                 "kernels": {k: {"ms_per_step": v["ms"] / vsteps, "launches_per_step": v["launches"] / vsteps,
+                 "kernels": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
                                  "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
                              for k, v in sorted(vprof.items(), key=lambda kv: -kv[1]["ms"])}}
     P.close()
@@ -603,6 +616,7 @@ def main():
                        "l2": "inputs larger than L2 (533 MB per space-time vector)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "ms_per_step_with_kernel_events": ms_prof / args.steps,
             "clocks": clk, ("fp64_path" if variant == "fp64" else "mixed"): mixed, "kernels": phases,
         }
         print(json.dumps(line), flush=True)

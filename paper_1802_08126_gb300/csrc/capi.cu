@@ -78,8 +78,9 @@ struct pt_problem {
   bool hdst = false;                            // exact H_k solves by spatial sine transforms
   void* dsti_tw = nullptr;                      // [n+1] complex e^{-2 pi i e / (n+1)}   (type T)
   void* dsti_sn = nullptr;                      // [(n+1)/2 + 1] sin(pi j / (n+1)) / 2
-  void* dsti_lam = nullptr;                     // [n+1] (4 a0/h^2) sin^2(pi k h / 2) at k-1, 0 at n
-  void* dsti_mu = nullptr;                      // [N] mu_k
+  double* dsti_lam = nullptr;                   // [n+1] (4 a0/h^2) sin^2(pi k h / 2) at k-1, 0 at n
+  double* dsti_mu = nullptr;                    // [N] mu_k
+  void* dsti_g = nullptr;                       // padded, type T: block-solve factor of each point
   int nv_h = 2;                                 // V-cycles per H_k solve
   void* mg_b[kMaxLevels] = {};
   void* mg_x[kMaxLevels] = {};
@@ -334,18 +335,17 @@ T* block_solve(pt_problem* p, const int* done) {
   T* W2 = (T*)p->W2;
   if (p->hdst) {
     const Level& L = p->lev[0];
-    const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
     // x, (y,) the last axis forward-scale-inverse, (y,) x: S_x S_y S_z diag(g) S_z S_y S_x
     const int last = p->dim - 1;
     launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
     if (p->dim == 3)
-      launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_lam,
-                          p->dsti_mu, p->tau, c0, false, p->st);
-    launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, last, p->dsti_tw, p->dsti_sn, p->dsti_lam,
-                        p->dsti_mu, p->tau, c0, true, p->st);
+      launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_g, false,
+                          p->st);
+    launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, last, p->dsti_tw, p->dsti_sn, p->dsti_g, true,
+                        p->st);
     if (p->dim == 3)
-      launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_lam,
-                          p->dsti_mu, p->tau, c0, false, p->st);
+      launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_g, false,
+                          p->st);
     launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
     return W1;
   }
@@ -793,12 +793,19 @@ pt_status setup_precision(pt_problem* p) {
     }
     if (!(p->dsti_tw = alloc_bytes(p, sizeof(T) * tw.size(), &st))) return st;
     if (!(p->dsti_sn = alloc_bytes(p, sizeof(T) * sn.size(), &st))) return st;
-    if (!(p->dsti_lam = alloc_bytes(p, sizeof(T) * lam.size(), &st))) return st;
-    if (!(p->dsti_mu = alloc_bytes(p, sizeof(T) * mud.size(), &st))) return st;
+    if (!(p->dsti_lam = (double*)alloc_bytes(p, sizeof(double) * lam.size(), &st))) return st;
+    if (!(p->dsti_mu = (double*)alloc_bytes(p, sizeof(double) * mud.size(), &st))) return st;
     if ((st = upload<T>(p, p->dsti_tw, tw)) != PT_OK) return st;
     if ((st = upload<T>(p, p->dsti_sn, sn)) != PT_OK) return st;
-    if ((st = upload<T>(p, p->dsti_lam, lam)) != PT_OK) return st;
-    if ((st = upload<T>(p, p->dsti_mu, mud)) != PT_OK) return st;
+    if ((st = upload<double>(p, p->dsti_lam, lam)) != PT_OK) return st;
+    if ((st = upload<double>(p, p->dsti_mu, mud)) != PT_OK) return st;
+    // the point-wise block-solve factor, computed once in FP64 (c0 as in block_solve)
+    const Level& L = p->lev[0];
+    const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
+    T* g = alloc_padded<T>(p, L, p->N, &st);
+    if (!g) return st;
+    p->dsti_g = g;
+    launch_dsti_scale_table<T>(g, p->dsti_lam, p->dsti_mu, p->tau, c0, p->dim, L.logP, L.S, p->N, p->st);
   } else if (p->opt.h_solver == 2) {
     return fail(PT_EINVAL,
                 "exact H_k solves need dim >= 2, n + 1 <= 4096 and a reference coefficient constant in space");
@@ -1124,6 +1131,7 @@ size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o) {
   double per = 24.0 + 3.0 * s;              // u, p, F and three work vectors
   if (mixed) per += 20.0;                   // FP32 corrections and residuals of the refinement
   if (!mixed && d == 2) per += 8.0;         // stored outer residual
+  if (d >= 2) per += s;                     // block-solve factor table (exact H_k solves)
   per += (d == 2 ? 2.0 : 3.0) * s * lev;    // multigrid right-hand sides, iterates (and residuals)
   if (d != 2) per += 2.0 * s;               // generic path: level-0 iterate and residual
   if (d == 2 && !mixed) per += 8.0 * (1.0 + lev);  // cached Jacobi factors

@@ -107,20 +107,11 @@ __device__ __forceinline__ T2* fft_any(T2* a, T2* b, int logM, const T2* __restr
     return warp_fft<T2>(a, b, logM, tw, lane);
 }
 
-// 1 / d for d > 0 in FP64: single-precision reciprocal and one Newton-Raphson step
-// r <- r (2 - d r), relative error about 1e-14 (the square of the single-precision error).
-__device__ __forceinline__ double recip_pos(double d) {
-  const double r = (double)__frcp_rn((float)d);
-  return fma(r, fma(-d, r, 1.0), r);
-}
-__device__ __forceinline__ float recip_pos(float d) { return __frcp_rn(d); }
-
 template <typename T>
 struct DstiTabs {
   const typename Vec2<T>::type* tw;  // [M]   e^{-2 pi i e / M}
   const T* sn;                       // [M/2 + 1] sin(pi j / M) / 2
-  const T* lam;                      // [M]   (4 a0 / h^2) sin^2(pi (pos+1) h / 2), 0 at the ghost
-  const T* mu;                       // [N]   mu_k
+  const T* g;                        // padded like the data: the block-solve factor, 0 at ghosts
 };
 
 // Rows (x, contiguous): every line pair of every slice, in place.  Lines 2q and 2q+1.
@@ -167,8 +158,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x,
 // 2w, 2w+1.  With `scale`, the column pair gets S diag(g) S, g the exact block-solve factor.
 template <typename T, int LOGMC>
 __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x, int logM_rt, int dim, int axis,
-                                                              long long S, int scale, T tau, T c0,
-                                                              DstiTabs<T> tb) {
+                                                              long long S, int scale, DstiTabs<T> tb) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int logM = LOGMC > 0 ? LOGMC : logM_rt;
@@ -201,20 +191,14 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x,
   T2* Z = fft_any<LOGMC>(B, A, logM, tb.tw, lane);
   T2* O = Z == A ? B : A;
   if (scale) {
-    // g = c0 l / (mu + tau l)^2, l = lam_x + lam_axis (+ lam_y in 3-D); 0 on ghost columns
-    const T mu = tb.mu[slice];
-    const T lo = dim == 3 ? tb.lam[o] : (T)0;
-    const T la = tb.lam[xa] + lo, lb = tb.lam[xa + 1] + lo;
-    const bool za = xa == M - 1 || ghost_o, zb = xa + 1 == M - 1 || ghost_o;
+    // g from the precomputed table (same padded layout as the data, zero on ghosts)
+    const T* gcol = tb.g + base + 2 * warp;
     dsti_post<LOGMC, T, T2>(Z, M, lane, [&](int pos, T2 v) {
-      const T ly = tb.lam[pos];
-      const T l1 = la + ly, l2 = lb + ly;
-      const T r1 = recip_pos(fma(tau, l1, mu)), r2 = recip_pos(fma(tau, l2, mu));
-      const T g1 = za ? (T)0 : c0 * l1 * r1 * r1, g2 = zb ? (T)0 : c0 * l2 * r2 * r2;
-      O[pd(pos)] = mk<T2>(v.x * g1, v.y * g2);
+      const T2 g = *(const T2*)(gcol + pos * stride);
+      O[pd(pos)] = mk<T2>(v.x * g.x, v.y * g.y);
     });
     __syncwarp();
-    T2* P2 = O == A ? B : A;
+    T2* P2 = O == A ? B : A;  // second transform of the scaled spectrum
     dsti_pre<LOGMC, T, T2>(P2, M, tb.sn, lane, [&](int pos) { return O[pd(pos)]; });
     __syncwarp();
     T2* Z2 = fft_any<LOGMC>(P2, O, logM, tb.tw, lane);
@@ -236,6 +220,28 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x,
   }
 }
 
+// g = c0 l / (mu_k + tau l)^2 at every padded point (0 at ghosts), l = sum of the axes' lam
+template <typename T>
+__global__ void k_dsti_scale_table(T* __restrict__ g, const double* __restrict__ lam, const double* __restrict__ mu,
+                                   double tau, double c0, int dim, int logM, long long total) {
+  const int M = 1 << logM;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long t = i >> (dim * logM);
+    const long long rem = i & ((1LL << (dim * logM)) - 1);
+    const int x = (int)(rem & (M - 1));
+    const int y = (int)((rem >> logM) & (M - 1));
+    const int z = dim == 3 ? (int)(rem >> (2 * logM)) : 0;
+    double v = 0.0;
+    if (x < M - 1 && y < M - 1 && z < M - 1) {
+      const double l = lam[x] + lam[y] + (dim == 3 ? lam[z] : 0.0);
+      const double d = mu[t] + tau * l;
+      v = c0 * l / (d * d);
+    }
+    g[i] = (T)v;
+  }
+}
+
 template <typename T>
 int warps_for(int M) {
   const size_t per = (size_t)(2 * padded_len(M) + 1) * 2 * sizeof(T);
@@ -245,16 +251,27 @@ int warps_for(int M) {
 }
 
 template <typename T>
-DstiTabs<T> tabs(const void* tw, const void* sn, const void* lam, const void* mu) {
+DstiTabs<T> tabs(const void* tw, const void* sn, const void* g) {
   DstiTabs<T> t;
   t.tw = (const typename Vec2<T>::type*)tw;
   t.sn = (const T*)sn;
-  t.lam = (const T*)lam;
-  t.mu = (const T*)mu;
+  t.g = (const T*)g;
   return t;
 }
 
 }  // namespace
+
+template <typename T>
+void launch_dsti_scale_table(T* g, const double* lam, const double* mu, double tau, double c0, int dim, int logP,
+                             long long S, int B, cudaStream_t st) {
+  const long long total = S * B;
+  LaunchScope ls("dsti_table", st, sizeof(T) * (double)total);
+  k_dsti_scale_table<T><<<grid_for(total), kThreads, 0, st>>>(g, lam, mu, tau, c0, dim, logP, total);
+}
+template void launch_dsti_scale_table<float>(float*, const double*, const double*, double, double, int, int,
+                                             long long, int, cudaStream_t);
+template void launch_dsti_scale_table<double>(double*, const double*, const double*, double, double, int, int,
+                                              long long, int, cudaStream_t);
 
 template <typename T>
 void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const void* tw, const void* sn,
@@ -276,7 +293,7 @@ void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const 
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
       attr[logP] = true;
     }
-    kern<<<(unsigned)blocks, wpb * 32, smem, st>>>(x, logP, dim, npairs, tabs<T>(tw, sn, nullptr, nullptr));
+    kern<<<(unsigned)blocks, wpb * 32, smem, st>>>(x, logP, dim, npairs, tabs<T>(tw, sn, nullptr));
   };
   // (the run-time-length kernel: unrolling the row transform raises its register count past
   // what its occupancy can afford, measured slower in both precisions)
@@ -285,8 +302,7 @@ void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const 
 
 template <typename T>
 void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
-                      const void* sn, const void* lam, const void* mu, double tau, double c0, bool scale,
-                      cudaStream_t st) {
+                      const void* sn, const void* gtab, bool scale, cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
   const int M = n + 1;
   int C = warps_for<T>(M);
@@ -303,7 +319,7 @@ void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int ax
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
       attr[logP] = true;
     }
-    kern<<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, (T)tau, (T)c0, tabs<T>(tw, sn, lam, mu));
+    kern<<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, tabs<T>(tw, sn, gtab));
   };
   // FP32: compile-time lengths (instruction-bound, the unrolled form measured 11 % faster);
   // FP64: bound by the FP64 pipe either way, the run-time-length kernel (fewer registers)
@@ -326,8 +342,8 @@ template void launch_dsti_rows<float>(float*, int, int, int, long long, int, con
 template void launch_dsti_rows<double>(double*, int, int, int, long long, int, const void*, const void*,
                                        cudaStream_t);
 template void launch_dsti_cols<float>(float*, int, int, int, long long, int, int, const void*, const void*,
-                                      const void*, const void*, double, double, bool, cudaStream_t);
+                                      const void*, bool, cudaStream_t);
 template void launch_dsti_cols<double>(double*, int, int, int, long long, int, int, const void*, const void*,
-                                       const void*, const void*, double, double, bool, cudaStream_t);
+                                       const void*, bool, cudaStream_t);
 
 }  // namespace pt

@@ -393,6 +393,70 @@ __global__ void k_tridiag(const T* __restrict__ r, void* out, int mode, int out_
   if (mode == 0) store_out<T>(out, base + n, 0, out_fp64, (T)0);  // ghost
 }
 
+// The same solves by parallel cyclic reduction (n + 1 <= 1024): one CTA per slice, thread i owns
+// equation i (a_i x_{i-1} + b_i x_i + c_i x_{i+1} = r_i).  Step s eliminates the couplings at
+// distance s by combining equation i with i - s and i + s, so after ceil(log2 n) steps every
+// equation stands alone.  The matrices are diagonally dominant (sigma >= 0, a > 0), for which
+// the reduction is stable.
+template <typename T>
+__global__ void k_tridiag_pcr(const T* __restrict__ r, void* out, int mode, int out_fp64, StencilGeom<T> g,
+                              OpBatch<T> op, const int* done) {
+  if (stop_requested(done)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = g.P, n = g.n, L = blockDim.x;  // L = max(P, 32) rows; rows >= n are identities
+  T* sa = (T*)smem_raw;
+  T* sb = sa + L;
+  T* sc = sb + L;
+  T* sr = sc + L;
+  const int b = blockIdx.x, i = threadIdx.x;
+  const long long base = (long long)b * g.S;
+  T ai = (T)0, bi = (T)1, ci = (T)0, ri = (T)0;
+  if (i < n) {
+    T am[1], ap[1];
+    const T sh = op.s * g.h2inv;
+    face_coefs<1, T>(g.tab, P, i, 0, 0, op.cth[b], g.a0, am, ap);
+    ai = i > 0 ? -sh * am[0] : (T)0;
+    ci = i < n - 1 ? -sh * ap[0] : (T)0;
+    bi = op.sig[b] + sh * (am[0] + ap[0]);
+    ri = r[base + i];
+  }
+  sa[i] = ai;
+  sb[i] = bi;
+  sc[i] = ci;
+  sr[i] = ri;
+  __syncthreads();
+  for (int s = 1; s < n; s <<= 1) {
+    const int im = i - s, ip = i + s;
+    T alpha = (T)0, gamma = (T)0, na = (T)0, nc = (T)0, nb = bi, nr = ri;
+    if (i < n && im >= 0) {
+      alpha = -ai / sb[im];
+      na = alpha * sa[im];
+      nb = fma(alpha, sc[im], nb);
+      nr = fma(alpha, sr[im], nr);
+    }
+    if (i < n && ip < n) {
+      gamma = -ci / sb[ip];
+      nc = gamma * sc[ip];
+      nb = fma(gamma, sa[ip], nb);
+      nr = fma(gamma, sr[ip], nr);
+    }
+    __syncthreads();
+    ai = na;
+    bi = nb;
+    ci = nc;
+    ri = nr;
+    sa[i] = ai;
+    sb[i] = bi;
+    sc[i] = ci;
+    sr[i] = ri;
+    __syncthreads();
+  }
+  if (i < n)
+    store_out<T>(out, base + i, mode, out_fp64, ri / bi);
+  else if (i < P && mode == 0)
+    store_out<T>(out, base + i, 0, out_fp64, (T)0);  // ghost
+}
+
 template <int DIM>
 double level_dofs(int n, int B) {
   double d = B;
@@ -552,7 +616,11 @@ void launch_tridiag(const T* r, void* out, int mode, int out_fp64, StencilGeom<T
                     int B, T* work, const int* done, cudaStream_t st) {
   const double d = (double)B * g.n, ob = out_fp64 ? (mode == 1 ? 16.0 : 8.0) : (double)sizeof(T);
   LaunchScope ls("tridiag", st, d * (sizeof(T) + ob));
-  k_tridiag<T><<<(B + 63) / 64, 64, 0, st>>>(r, out, mode, out_fp64, g, op, B, work, done);
+  if (g.P <= 1024)
+    k_tridiag_pcr<T><<<B, g.P < 32 ? 32 : g.P, 4 * sizeof(T) * (g.P < 32 ? 32 : g.P), st>>>(r, out, mode, out_fp64,
+                                                                                         g, op, done);
+  else
+    k_tridiag<T><<<(B + 63) / 64, 64, 0, st>>>(r, out, mode, out_fp64, g, op, B, work, done);
 }
 
 template void vcycle<float>(const MGPlan<float>&, OpBatch<float>, const float*, void*, int, int, const int*, cudaStream_t);

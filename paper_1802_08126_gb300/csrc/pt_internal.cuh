@@ -260,17 +260,20 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
 
 // Spatial sine transforms of type I (kernels_dsti.cu), in place on padded slices, n + 1 <= 4096:
 //   rows:  every x-line v <- S v;  cols: every line along axis 1 (y) or 2 (z) v <- S v, or with
-//   `scale`, v <- S diag(g) S v with g the exact block-solve factor c0 l / (mu_k + tau l)^2.
+//   `scale`, v <- S diag(g) S v with g the exact block-solve factor from the table `gtab`.
 // Tables (type T): tw [n+1] complex e^{-2 pi i e/(n+1)}; sn [(n+1)/2 + 1] sin(pi j/(n+1)) / 2;
-// lam [n+1] (4 a0/h^2) sin^2(pi k h/2) at position k-1 (0 at the ghost position); mu [B].
+// gtab padded like the data (B slots): c0 l / (mu_k + tau l)^2, l = sum over the axes of
+// lam[pos] = (4 a0/h^2) sin^2(pi (pos+1) h/2) (FP64 tables lam [n+1], mu [B]), 0 at ghosts.
 constexpr int kDstiMaxM = 4096;
 template <typename T>
 void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const void* tw, const void* sn,
                       cudaStream_t st);
 template <typename T>
 void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
-                      const void* sn, const void* lam, const void* mu, double tau, double c0, bool scale,
-                      cudaStream_t st);
+                      const void* sn, const void* gtab, bool scale, cudaStream_t st);
+template <typename T>
+void launch_dsti_scale_table(T* g, const double* lam, const double* mu, double tau, double c0, int dim, int logP,
+                             long long S, int B, cudaStream_t st);
 
 // Problem hooks for the serving loop (defined in capi.cu).
 pt_status problem_begin(pt_problem* p, double tol, int max_it);   // reset + captured iteration graph

@@ -144,12 +144,16 @@ def test_exact_transform_H_matches_oracle_direct_solves(prob, precision):
     assert rel_err(host(out), T.apply_Hinv(r, T.exact_H_solver())) <= tol
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_exact_1d_preconditioners_match_oracle(precision):
-    prob = S.heat1d_mms(63, 64)
-    # FP32 Thomas elimination: relative error up to ~kappa * eps32 with kappa(tau A_n) ~ 4/(pi h)^2
-    # ~ 1.7e3 at h = 1/64, i.e. ~1e-4; FP64 needs the same bound with eps64.
-    tol = 1e-12 if precision == "fp64" else 1e-4
+# n + 1 <= 1024: parallel cyclic reduction; 2047: the sequential elimination
+@pytest.mark.parametrize("prob,precision", [(S.heat1d_mms(63, 64), "fp64"), (S.heat1d_mms(63, 64), "mixed"),
+                                            (S.heat1d_mms(1, 4), "fp64"), (S.heat1d_mms(1, 4), "mixed"),
+                                            (S.heat1d_mms(15, 5), "fp64"), (S.heat1d_mms(1023, 6), "fp64"),
+                                            (S.heat1d_mms(2047, 3), "fp64")], ids=lambda v: getattr(v, "name", v))
+def test_exact_1d_preconditioners_match_oracle(prob, precision):
+    # Elimination in precision eps: relative error up to ~kappa * eps with kappa(tau A_n) ~
+    # 4/(pi h)^2 (1.7e3 at h = 1/64): FP32 ~1e-4; FP64 1e-12 up to h = 1/64, kappa * 1e-15 beyond.
+    kappa = 4.0 / (np.pi / (prob.n[0] + 1)) ** 2
+    tol = max(1e-12, kappa * 1e-15) if precision == "fp64" else 1e-4
     T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
     rng = np.random.default_rng(6)
     r = rng.standard_normal((prob.N, prob.ns))
