@@ -313,7 +313,7 @@ def run_batch(args, rank, ws, dist):
         budget = free - (24 << 30)
         Ps, used = [], 0
         while i < len(probs):
-            est = probs[i].dofs * 1.05 * 40  # bytes per DOF in mixed precision, padded, with margin
+            est = ptu.estimate_bytes(probs[i].dim, probs[i].n, probs[i].N, "mixed")
             if Ps and used + est > budget:
                 break
             Ps.append(make_batch_problem(ptu, probs[i]))

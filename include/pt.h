@@ -190,6 +190,12 @@ void pt_server_destroy(pt_server* sv);
  * Either output may be NULL; on_device selects device (1) or host (0) memory for both. */
 pt_status pt_problem_get_state(pt_problem* p, double* u_out, double* p_out, int on_device);
 
+/* Device memory: *bytes_out = an upper estimate of what pt_problem_create allocates for this
+ * grid, N_t and options (the serving loop's admission rule; no device work, no allocation), or
+ * the bytes a created problem holds.  PT_EINVAL on NULL arguments. */
+pt_status pt_problem_estimate_bytes(const pt_grid* grid, int N_t, const pt_options* opts, size_t* bytes_out);
+pt_status pt_problem_device_bytes(const pt_problem* p, size_t* bytes_out);
+
 /* Release all device memory of the problem; NULL is ignored. */
 void pt_problem_destroy(pt_problem* p);
 

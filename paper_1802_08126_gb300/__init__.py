@@ -79,6 +79,19 @@ def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=
     return o
 
 
+def estimate_bytes(dim: int, n: Sequence[int], N: int, precision: str = "mixed", solver: str = "mg") -> int:
+    """Upper estimate of the device memory a problem of this size takes (no allocation)."""
+    L = _lib.load()
+    g = _lib.Grid()
+    g.dim = dim
+    for d in range(3):
+        g.n[d] = int(n[d]) if d < dim else 1
+    o = _options(precision=precision, solver=solver)
+    out = ctypes.c_size_t()
+    _check(L.pt_problem_estimate_bytes(ctypes.byref(g), int(N), ctypes.byref(o), ctypes.byref(out)))
+    return int(out.value)
+
+
 class Server:
     """Continuous-batching solve server on the current device (wraps ``pt_server``)."""
 
@@ -260,6 +273,12 @@ class Problem:
         st = _check(self._lib.pt_solve(self._h, float(tol), int(max_it), up, udev, hp, ctypes.byref(it)),
                     allowed=(PT_OK, PT_ENOTCONV, PT_EDIVERGED))
         return st, it.value, (hist[: it.value + 1] if hist is not None else None)
+
+    def device_bytes(self) -> int:
+        """Device memory this problem holds."""
+        out = ctypes.c_size_t()
+        _check(self._lib.pt_problem_device_bytes(self._h, ctypes.byref(out)))
+        return int(out.value)
 
     def get_state(self, u_out=None, p_out=None):
         """Copy the current iterates (u_j, p_j) into the given arrays (both host or both device)."""

@@ -18,7 +18,7 @@ EXPORTED = (
     "pt_precond_H", "pt_kernel_launch_count", "pt_problem_get_state", "pt_profile_enable",
     "pt_profile_reset", "pt_profile_get", "pt_dst_forward_noalloc", "pt_solve_batch",
     "pt_problem_set_rhs_uniform", "pt_server_create", "pt_server_submit", "pt_server_wait",
-    "pt_server_stats", "pt_server_destroy",
+    "pt_server_stats", "pt_server_destroy", "pt_problem_estimate_bytes", "pt_problem_device_bytes",
 )
 
 
@@ -74,6 +74,11 @@ def load(path: str = LIB_PATH):
             fn.restype = i
         L.pt_problem_get_state.argtypes = [vp, vp, vp, i]
         L.pt_problem_get_state.restype = i
+        L.pt_problem_estimate_bytes.argtypes = [ctypes.POINTER(Grid), i, ctypes.POINTER(Options),
+                                                ctypes.POINTER(ctypes.c_size_t)]
+        L.pt_problem_estimate_bytes.restype = i
+        L.pt_problem_device_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.pt_problem_device_bytes.restype = i
         L.pt_profile_enable.argtypes = [i]
         L.pt_profile_enable.restype = None
         L.pt_profile_reset.argtypes = []

@@ -1354,6 +1354,21 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
   return PT_OK;
 }
 
+pt_status pt_problem_estimate_bytes(const pt_grid* grid, int N_t, const pt_options* opts, size_t* bytes_out) {
+  g_err.clear();
+  if (!grid || !bytes_out) return fail(PT_EINVAL, "grid and bytes_out are required");
+  if (grid->dim < 1 || grid->dim > 3 || N_t < 1) return fail(PT_EINVAL, "bad grid or N_t");
+  *bytes_out = pt::estimate_problem_bytes(grid, N_t, opts);
+  return PT_OK;
+}
+
+pt_status pt_problem_device_bytes(const pt_problem* p, size_t* bytes_out) {
+  g_err.clear();
+  if (!p || !bytes_out) return fail(PT_EINVAL, "problem and bytes_out are required");
+  *bytes_out = pt::problem_bytes(p);
+  return PT_OK;
+}
+
 pt_status pt_problem_get_state(pt_problem* p, double* u_out, double* p_out, int on_device) {
   g_err.clear();
   if (!p) return fail(PT_EINVAL, "problem is NULL");

@@ -77,3 +77,14 @@ def test_null_pointers_rejected(lib):
 def test_binding_rejects_wrong_dtype():
     with pytest.raises(ValueError):
         ptu._ptr(np.zeros(4, dtype=np.float32))
+
+
+def test_memory_estimate_is_host_only_and_monotone():
+    """pt_problem_estimate_bytes needs no device: it grows with N_t and the grid."""
+    import paper_1802_08126_gb300 as ptu
+    a = ptu.estimate_bytes(2, [255, 255], 64, "mixed")
+    b = ptu.estimate_bytes(2, [255, 255], 128, "mixed")
+    c = ptu.estimate_bytes(2, [511, 511], 64, "mixed")
+    assert 0 < a < b and a < c
+    assert ptu.estimate_bytes(3, [31, 31, 31], 16, "fp64") > 0
+    assert ptu.estimate_bytes(1, [63], 64, "fp64", solver="exact") > 0

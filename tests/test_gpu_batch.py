@@ -105,3 +105,21 @@ def test_default_omega_rule():
             st, it, hist = P.solve(1e-10, 500)
             out.append(hist.copy())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("dim,n,N,precision", [(2, 255, 64, "mixed"), (2, 255, 64, "fp64"), (2, 31, 300, "mixed"),
+                                               (3, 31, 16, "mixed"), (3, 15, 8, "fp64"), (1, 63, 64, "fp64")])
+def test_memory_estimate_covers_the_allocation(dim, n, N, precision):
+    """The admission estimate (serving loop, batch waves) is an upper bound of what a problem
+    actually allocates."""
+    import paper_1802_08126_gb300 as ptu
+    from synthetic import Coeff
+    coeff = Coeff(a0=1.0, c=0.5, fx=[S.TRIG_SIN] * 3, mx=[2.0] * 3, ft=S.TRIG_COS, mt=2.0)  # mean-zero in t
+    solver = "exact" if dim == 1 else "mg"
+    P = ptu.Problem(dim, [n] * dim, N, 1.0, coeff, None, None, precision=precision, solver=solver)
+    try:
+        held = P.device_bytes()
+    finally:
+        P.close()
+    est = ptu.estimate_bytes(dim, [n] * dim, N, precision, solver=solver)
+    assert held <= est, (held, est)
