@@ -347,6 +347,17 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
   }
 }
 
+// asynchronous global -> shared copies (sm_80+ cp.async): the target tile of the accumulating
+// inverse is fetched while the transform runs
+__device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_inverse_s(const T* __restrict__ y, void* out, int mode,
                                                                  double omega, long long S, ColGeom cg,
@@ -360,6 +371,14 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* sm = (T2*)smem_raw;
   const long long c0 = (long long)blockIdx.x * 2 * F;
+  // mode 2 (FP32 accumulate): prefetch the target tile [N][F] behind the transform tile
+  T2* tgt = sm + (size_t)F * Lp;
+  if (mode == 2 && sizeof(T2) == 8) {
+    for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
+      const int f = idx % F, t = idx / F;
+      cp_async_8(tgt + idx, (const T*)out + (long long)t * S + c0 + 2 * f);
+    }
+  }
   // load: z_j = (-1)^j y_{j+1};  v_{j/2} = z_j (j even), v_{N-1-(j-1)/2} = z_j (j odd)
   for (int idx0 = threadIdx.x; idx0 < N * F; idx0 += 4 * blockDim.x) {
     T2 v[4];
@@ -390,6 +409,11 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
     const int f = threadIdx.x / nthr, tid = threadIdx.x - f * nthr;
     block_fft<T2>(sm + (size_t)f * Lp, logN, (const T2*)plan.twS, tid, nthr);
   }
+  const bool pref = mode == 2 && sizeof(T2) == 8;
+  if (pref) {
+    cp_async_commit_wait_all();
+    __syncthreads();
+  }
   // post: V_a[m] = (C_m + conj C_{N-m})/2, V_b[m] = (C_m - conj C_{N-m})/(2i);
   //       X[m] = Re(e^{-i pi m/(2N)} V[m]);  u_{N-m} = X[m]  (time slot N-1-m)
   const int halfp = (N >> 1) + 1;
@@ -413,7 +437,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
       *u = cur;
     } else if (mode == 2) {
       T2* o = (T2*)((T*)out + o1);
-      const T2 cur = *o;
+      const T2 cur = pref ? tgt[(N - 1 - m) * F + f] : *o;
       *o = mk<T2>(cur.x + (T)omega * Xa, cur.y + (T)omega * Xb);
     } else {
       *(T2*)((T*)out + o1) = mk<T2>(Xa, Xb);
@@ -434,7 +458,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
         *u = cur;
       } else if (mode == 2) {
         T2* o = (T2*)((T*)out + o2);
-        const T2 cur = *o;
+        const T2 cur = pref ? tgt[(m - 1) * F + f] : *o;
         *o = mk<T2>(cur.x + (T)omega * Xa2, cur.y + (T)omega * Xb2);
       } else {
         *(T2*)((T*)out + o2) = mk<T2>(Xa2, Xb2);
@@ -547,7 +571,8 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
     }
     const int F = stockham_cols(plan, S);
     const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
-    const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2);
+    const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2) +
+                      (mode == 2 && sizeof(T2) == 8 ? (size_t)F * plan.N * sizeof(T2) : 0);
     k_dst_inverse_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(y, out, mode, omega, S, cg, plan, F, done);
   } else if (plan.M > 0)
     k_dst_inverse<T, true><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);

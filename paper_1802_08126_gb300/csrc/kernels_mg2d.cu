@@ -314,25 +314,29 @@ __global__ void __launch_bounds__(256) k_mg2s_down(const T* __restrict__ bf, T* 
   FaceSweep<T, VAR> fs;
   fs.init(a, nx, fy, cths, x, yfirst);
   // x1 = w D^-1 b and everything the residual at that row needs
-  auto row = [&](int y, T& bv, T& x1, Faces<T, VAR>& f) {
+  auto ld_b = [&](int y) -> T { return (xin && y >= 0 && y < nf) ? bf[base + (long long)y * Pf + x] : (T)0; };
+  auto row = [&](int y, T bload, T& bv, T& x1, Faces<T, VAR>& f) {
     f = fs.row(a, fx, ny, fy, cths, x, y);
     bv = (T)0;
     x1 = (T)0;
     if (xin && y >= 0 && y < nf) {
       const long long gi = base + (long long)y * Pf + x;
-      bv = bf[gi];
+      bv = bload;
       x1 = bv * jacobi_at<T, VAR, DM>(a, b, gi, f, sig);
     }
   };
   T bm, xm, bc_, xc, bn, xn;
   Faces<T, VAR> fm, fc, fn;
-  row(yfirst, bm, xm, fm);
-  row(yfirst + 1, bc_, xc, fc);
+  row(yfirst, ld_b(yfirst), bm, xm, fm);
+  row(yfirst + 1, ld_b(yfirst + 1), bc_, xc, fc);
+  T b_next = ld_b(yfirst + 2);  // b of the row after next, loaded one iteration ahead
   T h1 = (T)0, h2 = (T)0;  // horizontal restrictions of the two previous rows
   const bool out_lane = (lane & 1) == 0 && lane >= 2 && lane <= 28;
   const int X = X0 + (lane >> 1) - 1;  // coarse column of an output lane (x = 2X + 1)
   for (int y = yfirst + 1; y <= ylast; ++y) {
-    row(y + 1, bn, xn, fn);
+    const T b_after = ld_b(y + 2);
+    row(y + 1, b_next, bn, xn, fn);
+    b_next = b_after;
     // residual of x1 at row y
     const T xW = __shfl_up_sync(0xffffffffu, xc, 1);
     const T xE = __shfl_down_sync(0xffffffffu, xc, 1);
@@ -406,7 +410,16 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
   int k_lo = -1000;
   FaceSweep<T, VAR> fs;
   fs.init(a, nx, fy, cths, x, y0 - 1);
-  auto row = [&](int y, T& bv, T& x2, T& jf, Faces<T, VAR>& f) {
+  // global operands are loaded ahead of use (the kernel is latency-bound otherwise): b two rows
+  // ahead, the accumulation target one row ahead
+  auto ld_b = [&](int y) -> T { return (xin && y >= 0 && y < nf) ? bf[base + (long long)y * Pf + x] : (T)0; };
+  const bool wlane = lane >= 1 && lane <= 30 && x < Pf;
+  auto ld_o = [&](int y) -> double {
+    if (mode != 1 || !wlane || !xin || y >= nf) return 0.0;
+    const long long gi = base + (long long)y * Pf + x;
+    return out_fp64 ? ((const double*)out)[gi] : (double)((const T*)out)[gi];
+  };
+  auto row = [&](int y, T bload, T& bv, T& x2, T& jf, Faces<T, VAR>& f) {
     f = fs.row(a, fx, ny, fy, cths, x, y);
     bv = (T)0;
     x2 = (T)0;
@@ -428,18 +441,23 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
     }
     if (xin && y >= 0 && y < nf) {
       const long long gi = base + (long long)y * Pf + x;
-      bv = bf[gi];
+      bv = bload;
       jf = jacobi_at<T, VAR, DM>(a, b, gi, f, sig);
       x2 = fma(bv, jf, pe);
     }
   };
   T bm, xm, jm, bcv, xc, jc, bn, xn, jn;
   Faces<T, VAR> fm, fc, fn;
-  row(y0 - 1, bm, xm, jm, fm);
-  row(y0, bcv, xc, jc, fc);
-  const bool wlane = lane >= 1 && lane <= 30 && x < Pf;
+  row(y0 - 1, ld_b(y0 - 1), bm, xm, jm, fm);
+  row(y0, ld_b(y0), bcv, xc, jc, fc);
+  T b_next = ld_b(y0 + 1);
+  double o_next = ld_o(y0);
   for (int y = y0; y < y0 + kStripUpRows && y < Pf; ++y) {
-    row(y + 1, bn, xn, jn, fn);
+    const T b_after = ld_b(y + 2);
+    const double o_cur = o_next;
+    o_next = ld_o(y + 1);
+    row(y + 1, b_next, bn, xn, jn, fn);
+    b_next = b_after;
     const T xW = __shfl_up_sync(0xffffffffu, xc, 1);
     const T xE = __shfl_down_sync(0xffffffffu, xc, 1);
     if (wlane) {
@@ -450,7 +468,15 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
           Lx = sig * xc + fc.xl * (xc - xW) + fc.xr * (xc - xE) + fc.yl * (xc - xm) + fc.yu * (xc - xn);
         else
           Lx = (sig + (T)4 * a.a0s) * xc - a.a0s * ((xW + xE) + (xm + xn));
-        store_out<T>(out, gi, mode, out_fp64, xc + jc * (bcv - Lx));
+        const T v = xc + jc * (bcv - Lx);
+        if (mode == 1) {
+          if (out_fp64)
+            ((double*)out)[gi] = o_cur + (double)v;
+          else
+            ((T*)out)[gi] = (T)o_cur + v;
+        } else {
+          store_out<T>(out, gi, 0, out_fp64, v);
+        }
       } else if (mode == 0) {
         store_out<T>(out, gi, 0, out_fp64, (T)0);
       }

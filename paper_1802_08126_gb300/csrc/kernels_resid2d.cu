@@ -215,14 +215,34 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
     float d_m = du[at(y0) - P], d_c = du[at(y0)];
     float q_m = dp[at(y0) - P], q_c = dp[at(y0)];
     float ayl = fmaf(gxc, fy[y0], a0s);
+    // operands of the next row are loaded one iteration ahead (latency)
+    auto ld_row = [&](int y, float& dv, float& qv) {
+      dv = 0.f;
+      qv = 0.f;
+      if (y < P) {
+        dv = du[at(y)];
+        qv = dp[at(y)];
+      }
+    };
+    auto ld_ctr = [&](int y, float& r1, float& r2, float& dt) {
+      r1 = r2 = dt = 0.f;
+      if (xin && y < n) {
+        const long long i = at(y);
+        r1 = R1[i];
+        r2 = R2[i];
+        dt = t > 0 ? du[i - S] : 0.f;
+      }
+    };
+    float dpn, qpn, r1c, r2c, dtc;
+    ld_row(y0 + 1, dpn, qpn);
+    ld_ctr(y0, r1c, r2c, dtc);
     for (int k = 0; k < kRows; ++k) {
       const int y = y0 + k;
       const bool yin = y < n;
-      float d_p = 0.f, q_p = 0.f;
-      if (y + 1 < P) {
-        d_p = du[at(y + 1)];
-        q_p = dp[at(y + 1)];
-      }
+      const float d_p = dpn, q_p = qpn;
+      const float r1 = r1c, r2 = r2c, dtm = dtc;
+      ld_row(y + 2, dpn, qpn);
+      ld_ctr(y + 1, r1c, r2c, dtc);
       float dW = __shfl_up_sync(0xffffffffu, d_c, 1), dE = __shfl_down_sync(0xffffffffu, d_c, 1);
       float qW = __shfl_up_sync(0xffffffffu, q_c, 1), qE = __shfl_down_sync(0xffffffffu, q_c, 1);
       if (lane == 0 && yin) {
@@ -239,11 +259,12 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
         const long long i = at(y);
         const float gy = ct * ny[y];
         const float axl = fmaf(gy, fxl, a0s), axr = fmaf(gy, fxr, a0s);
-        const float Kd = d_c - (t > 0 ? du[i - S] : 0.f);
+        (void)i;
+        const float Kd = d_c - dtm;
         const float sd = axl * (d_c - dW) + axr * (d_c - dE) + ayl * (d_c - d_m) + ayu * (d_c - d_p);
         const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - q_m) + ayu * (q_c - q_p);
-        b = R2[i] - Kd - sd;
-        r = Kd - sq - R1[i];
+        b = r2 - Kd - sd;
+        r = Kd - sq - r1;
         acc = fmaf(b, b, acc);
       }
       if (y < P) {
