@@ -373,14 +373,22 @@ void enqueue_iteration(pt_problem* p) {
     const StencilGeom<float> gf = geom<float>(p, 0);
     launch_ir_begin(p->state, kOuter, p->st);
     launch_ir_fold(p->u, p->p, p->ir_du, p->ir_dp, total, p->state, p->st);
-    if (p->dim == 2 && L0.P >= 32)
+    if (p->dim == 3 && L0.P >= 32)
+      launch_ir_outer_3d(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, p->tab_d + L0.tab,
+                         p->tab_f + L0.tab, p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N,
+                         p->state, p->st);
+    else if (p->dim == 2 && L0.P >= 32)
       launch_ir_outer_2d(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, p->tab_d + L0.tab,
                          p->tab_f + L0.tab, p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N,
                          p->state, p->st);
     else
       launch_ir_outer(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, g, p->cth_d, p->tau, p->N,
                       p->state, p->st);
-    if (p->dim == 2 && L0.P >= 32)
+    if (p->dim == 3 && L0.P >= 32)
+      launch_ir_inner_3d(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials,
+                         p->tab_f + L0.tab, (const float*)p->cthA, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S,
+                         p->N, p->state, p->st);
+    else if (p->dim == 2 && L0.P >= 32)
       launch_ir_inner_2d(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials,
                          p->tab_f + L0.tab, (const float*)p->cthA, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S,
                          p->N, p->state, p->st);

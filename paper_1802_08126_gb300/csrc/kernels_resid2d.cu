@@ -296,3 +296,240 @@ void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const
 }
 
 }  // namespace pt
+
+// ---- 3-D forms (n + 1 >= 32) of the two refinement residuals ----
+// A warp owns 32 consecutive x of one (y, slot) line and sweeps a strip of kRows z-planes: the
+// planes z-1, z, z+1 stay in registers, x-neighbours come from shuffles, y-neighbours are loads
+// (the neighbouring warps read the same rows, so they hit in cache).
+namespace pt {
+namespace {
+
+struct Sweep3 {
+  int wx, y, z0, t;
+};
+__device__ __forceinline__ Sweep3 sweep3_decode(long long wg, int P) {
+  const int wx_count = P >> 5, strips = P / kRows;
+  Sweep3 s;
+  s.wx = (int)(wg % wx_count);
+  long long r = wg / wx_count;
+  s.y = (int)(r % P);
+  r /= P;
+  s.z0 = (int)(r % strips) * kRows;
+  s.t = (int)(r / strips);
+  return s;
+}
+
+// FP32 inner step: b' = R2 - K du - tau A du, r_p' = K du - tau A dp - R1
+__global__ void __launch_bounds__(256) k_ir_inner_3d(
+    const float* __restrict__ du, const float* __restrict__ dp, const float* __restrict__ R1,
+    const float* __restrict__ R2, float* __restrict__ bp, float* __restrict__ rp, double* __restrict__ partials,
+    const float* __restrict__ tabf, const float* __restrict__ cthf, float a0s, float s_h2, int n, int logP,
+    long long S, long long nwarps, const SolveState* st) {
+  if (*((volatile const int*)&st->done) != 0 || *((volatile const int*)&st->outer) != 0) return;
+  const int P = 1 << logP;
+  const long long P2 = (long long)P * P;
+  const int lane = threadIdx.x & 31;
+  float acc = 0.f;
+  const float* nx = tabf;
+  const float* fx = tabf + P;
+  const float* ny = tabf + 2 * P;
+  const float* fy = tabf + 3 * P;
+  const float* nz = tabf + 4 * P;
+  const float* fz = tabf + 5 * P;
+  for (long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wg < nwarps;
+       wg += (long long)gridDim.x * (blockDim.x >> 5)) {
+    const Sweep3 w = sweep3_decode(wg, P);
+    const int x = (w.wx << 5) + lane;
+    const bool xyin = x < n && w.y < n;
+    const float ct = s_h2 * cthf[w.t];
+    const float gx = nx[x], gy = ny[w.y];
+    const float fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
+    const float fyl = fy[w.y], fyu = fy[w.y + 1 < P ? w.y + 1 : w.y];
+    const float gxy = ct * gx * gy;
+    const long long base = (long long)w.t * S + (long long)w.y * P + x;
+    auto at = [&](int z) { return base + (long long)z * P2; };
+    float d_m = du[at(w.z0) - P2], d_c = du[at(w.z0)];
+    float q_m = dp[at(w.z0) - P2], q_c = dp[at(w.z0)];
+    float azl = fmaf(gxy, fz[w.z0], a0s);
+    for (int k = 0; k < kRows; ++k) {
+      const int z = w.z0 + k;
+      const bool in = xyin && z < n;
+      float d_p = 0.f, q_p = 0.f;
+      if (z + 1 < P) {
+        d_p = du[at(z + 1)];
+        q_p = dp[at(z + 1)];
+      }
+      float dW = __shfl_up_sync(0xffffffffu, d_c, 1), dE = __shfl_down_sync(0xffffffffu, d_c, 1);
+      float qW = __shfl_up_sync(0xffffffffu, q_c, 1), qE = __shfl_down_sync(0xffffffffu, q_c, 1);
+      const float azu = fmaf(gxy, fz[z + 1 < P ? z + 1 : z], a0s);
+      float b = 0.f, r = 0.f;
+      if (in) {
+        const long long i = at(z);
+        if (lane == 0) {
+          dW = du[i - 1];
+          qW = dp[i - 1];
+        }
+        if (lane == 31) {
+          dE = du[i + 1];
+          qE = dp[i + 1];
+        }
+        const float dS = du[i - P], dN = du[i + P], qS = dp[i - P], qN = dp[i + P];
+        const float gz = ct * nz[z];
+        const float gyz = gz * gy, gxz = gz * gx;
+        const float axl = fmaf(gyz, fxl, a0s), axr = fmaf(gyz, fxr, a0s);
+        const float ayl = fmaf(gxz, fyl, a0s), ayu = fmaf(gxz, fyu, a0s);
+        const float Kd = d_c - (w.t > 0 ? du[i - S] : 0.f);
+        const float sd = axl * (d_c - dW) + axr * (d_c - dE) + ayl * (d_c - dS) + ayu * (d_c - dN) +
+                         azl * (d_c - d_m) + azu * (d_c - d_p);
+        const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - qS) + ayu * (q_c - qN) +
+                         azl * (q_c - q_m) + azu * (q_c - q_p);
+        b = R2[i] - Kd - sd;
+        r = Kd - sq - R1[i];
+        acc = fmaf(b, b, acc);
+      }
+      if (z < P) {
+        bp[at(z)] = b;
+        rp[at(z)] = r;
+      }
+      d_m = d_c;
+      d_c = d_p;
+      q_m = q_c;
+      q_c = q_p;
+      azl = azu;
+    }
+  }
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// FP64 step: bres = F - K u - tau A u (FP64, norm), w = p + u; R1 = bres + tau A w (w-stencil in
+// FP32), R2 = bres - K^T w, r_p' = -R1
+__global__ void __launch_bounds__(256) k_ir_outer_3d(
+    const double* __restrict__ u, const double* __restrict__ p, const double* __restrict__ F,
+    float* __restrict__ R1, float* __restrict__ R2, float* __restrict__ rp, double* __restrict__ partials,
+    const double* __restrict__ tab, const float* __restrict__ tabf, const double* __restrict__ cth,
+    double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, const SolveState* st) {
+  if (*((volatile const int*)&st->done) != 0 || !*((volatile const int*)&st->outer)) return;
+  const int P = 1 << logP;
+  const long long P2 = (long long)P * P;
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  const double* nx = tab;
+  const double* fx = tab + P;
+  const double* ny = tab + 2 * P;
+  const double* fy = tab + 3 * P;
+  const double* nz = tab + 4 * P;
+  const double* fz = tab + 5 * P;
+  const float* fxf = tabf + P;
+  const float* fyf = tabf + 3 * P;
+  const float* nzf = tabf + 4 * P;
+  const float* fzf = tabf + 5 * P;
+  const float a0f = (float)a0s;
+  for (long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wg < nwarps;
+       wg += (long long)gridDim.x * (blockDim.x >> 5)) {
+    const Sweep3 w = sweep3_decode(wg, P);
+    const int x = (w.wx << 5) + lane;
+    const bool xyin = x < n && w.y < n;
+    const double ct = s_h2 * cth[w.t];
+    const float ctf = (float)ct;
+    const double gx = nx[x], gy = ny[w.y];
+    const int xr = x + 1 < P ? x + 1 : x, yu = w.y + 1 < P ? w.y + 1 : w.y;
+    const double gxy = ct * gx * gy;
+    const float gxf = (float)gx, gyf = (float)gy, gxyf = (float)gxy;
+    const long long base = (long long)w.t * S + (long long)w.y * P + x;
+    auto at = [&](int z) { return base + (long long)z * P2; };
+    auto wv = [&](long long i) { return p[i] + u[i]; };
+    double u_m = u[at(w.z0) - P2], u_c = u[at(w.z0)];
+    float w_m = (float)wv(at(w.z0) - P2), w_c = (float)wv(at(w.z0));
+    double azl = fma(gxy, fz[w.z0], a0s);
+    float azlf = fmaf(gxyf, fzf[w.z0], a0f);
+    for (int k = 0; k < kRows; ++k) {
+      const int z = w.z0 + k;
+      const bool in = xyin && z < n;
+      double u_p = 0.0;
+      float w_p = 0.f;
+      if (z + 1 < P) {
+        u_p = u[at(z + 1)];
+        w_p = (float)wv(at(z + 1));
+      }
+      double uW = __shfl_up_sync(0xffffffffu, u_c, 1), uE = __shfl_down_sync(0xffffffffu, u_c, 1);
+      float wW = __shfl_up_sync(0xffffffffu, w_c, 1), wE = __shfl_down_sync(0xffffffffu, w_c, 1);
+      const int zu = z + 1 < P ? z + 1 : z;
+      const double azu = fma(gxy, fz[zu], a0s);
+      const float azuf = fmaf(gxyf, fzf[zu], a0f);
+      float r1 = 0.f, r2 = 0.f;
+      if (in) {
+        const long long i = at(z);
+        if (lane == 0) {
+          uW = u[i - 1];
+          wW = (float)wv(i - 1);
+        }
+        if (lane == 31) {
+          uE = u[i + 1];
+          wE = (float)wv(i + 1);
+        }
+        const double uS = u[i - P], uN = u[i + P];
+        const float wS = (float)wv(i - P), wN = (float)wv(i + P);
+        const double gz = ct * nz[z];
+        const double gyz = gz * gy, gxz = gz * gx;
+        const double axl = fma(gyz, fx[x], a0s), axr = fma(gyz, fx[xr], a0s);
+        const double ayl = fma(gxz, fy[w.y], a0s), ayu = fma(gxz, fy[yu], a0s);
+        const double su = axl * (u_c - uW) + axr * (u_c - uE) + ayl * (u_c - uS) + ayu * (u_c - uN) +
+                          azl * (u_c - u_m) + azu * (u_c - u_p);
+        const double um = w.t > 0 ? u[i - S] : 0.0;
+        const double b = F[i] - (u_c - um) - su;
+        acc = fma(b, b, acc);
+        const float gzf = ctf * nzf[z];
+        const float gyzf = gzf * gyf, gxzf = gzf * gxf;
+        const float axlf = fmaf(gyzf, fxf[x], a0f), axrf = fmaf(gyzf, fxf[xr], a0f);
+        const float aylf = fmaf(gxzf, fyf[w.y], a0f), ayuf = fmaf(gxzf, fyf[yu], a0f);
+        const float sw = axlf * (w_c - wW) + axrf * (w_c - wE) + aylf * (w_c - wS) + ayuf * (w_c - wN) +
+                         azlf * (w_c - w_m) + azuf * (w_c - w_p);
+        const double wc = p[i] + u_c;
+        const double wn = w.t + 1 < N ? wv(i + S) : 0.0;
+        r1 = (float)b + sw;
+        r2 = (float)(b - (wc - wn));
+      }
+      if (z < P) {
+        R1[at(z)] = r1;
+        R2[at(z)] = r2;
+        rp[at(z)] = -r1;
+      }
+      u_m = u_c;
+      u_c = u_p;
+      w_m = w_c;
+      w_c = w_p;
+      azl = azu;
+      azlf = azuf;
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+}  // namespace
+
+void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
+                        double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
+                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s) {
+  const int P = 1 << logP;
+  const long long nwarps = (long long)(P / 32) * P * (P / kRows) * N;
+  const double s_h2 = tau / (h * h);
+  LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * n * N);
+  k_ir_inner_3d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
+                                              (float)s_h2, n, logP, S, nwarps, st);
+}
+
+void launch_ir_outer_3d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
+                        double* partials, const double* tab, const float* tabf, const double* cth, double a0,
+                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
+                        cudaStream_t s) {
+  const int P = 1 << logP;
+  const long long nwarps = (long long)(P / 32) * P * (P / kRows) * N;
+  const double s_h2 = tau / (h * h);
+  LaunchScope ls("ir_outer", s, 36.0 * (double)n * n * n * N);
+  k_ir_outer_3d<<<kReduceBlocks, 256, 0, s>>>(u, p, F, R1, R2, rp, partials, tab, tabf, cth, s_h2 * a0, s_h2, n,
+                                              logP, S, N, nwarps, st);
+}
+
+}  // namespace pt

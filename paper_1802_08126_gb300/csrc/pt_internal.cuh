@@ -165,6 +165,13 @@ void launch_ir_outer_2d(const double* u, const double* p, const double* F, float
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
                         int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s);
+void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
+                        double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
+                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s);
+void launch_ir_outer_3d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
+                        double* partials, const double* tab, const float* tabf, const double* cth, double a0,
+                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
+                        cudaStream_t s);
 void launch_ir_resid_u(const float* bp, const float* R2, const float* du, const float* dp, float* ru, long long S,
                        int N, const SolveState* st, cudaStream_t s);
 void launch_ir_finalize(const double* partials, SolveState* state, double* hist, cudaStream_t s);
