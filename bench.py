@@ -60,6 +60,9 @@ def parse():
                     help="override the workload's precision (profiling runs)")
     ap.add_argument("--workload", default="heat2d", choices=["heat2d", "heat1d", "heat3d", "batch", "serve"])
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
+    ap.add_argument("--batch-mode", default="waves", choices=["waves", "server"],
+                    help="batch: pt_solve_batch over memory waves, or all problems submitted at once "
+                         "to the continuous-batching server (finished solves replaced at once)")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per arrival rate")
     ap.add_argument("--rates", default="0.5,0.9,1.1", help="serve: arrival rates as fractions of capacity")
     return ap.parse_args()
@@ -308,6 +311,20 @@ def run_batch(args, rank, ws, dist):
     clocks.start()
     launches0 = ptu.launch_count()
     solve_s, waves, its, statuses, i = 0.0, 0, [], [], 0
+    if args.batch_mode == "server":
+        # every problem submitted at t = 0; the server admits by memory and refills as solves end
+        with ptu.Server() as sv:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tickets = [sv.submit(p.dim, p.n, p.N, p.T, p.coeff, None, seed=p.seed, tol=args.tol,
+                                 max_it=args.max_it, precision="mixed") for p in probs]
+            for t in tickets:
+                stt, it = sv.wait(t)
+                its.append(it)
+                statuses.append(stt)
+            solve_s = time.perf_counter() - t0
+        waves = 0
+        i = len(probs)
     while i < len(probs):
         free, _ = torch.cuda.mem_get_info()
         budget = free - (24 << 30)
@@ -343,7 +360,7 @@ def run_batch(args, rank, ws, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
             "config": {"workload": "batch%d_heat2d_mixed" % args.problems, "problems": len(probs),
-                       "dofs_per_gpu": total_dofs, "tol": args.tol, "waves": waves,
+                       "dofs_per_gpu": total_dofs, "tol": args.tol, "waves": waves, "mode": args.batch_mode,
                        "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
                        "converged": int(sum(1 for x in statuses if x == 0)), "precision": "mixed",
                        "l2": "inputs larger than L2 for most problems"},
