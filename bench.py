@@ -84,6 +84,17 @@ def dist_init(args):
     return rank, ws, local, None
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over the ranks (x itself without a process group): the timed region
+    of a multi-GPU run is the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -348,11 +359,7 @@ def run_batch(args, rank, ws, dist):
             P.close()
     launches = ptu.launch_count() - launches0
     clk = clocks.stop()
-    if dist is not None:
-        import torch.distributed as d
-        t = torch.tensor([solve_s], device="cuda", dtype=torch.float64)
-        d.all_reduce(t, op=d.ReduceOp.MAX)
-        solve_s = t.item()
+    solve_s = max_over_ranks(solve_s, dist)
     if rank == 0:
         line = {
             "metric": METRIC + " (batched)", "value": ws * total_dofs / solve_s, "unit": "DOF/s",
@@ -525,10 +532,7 @@ def main():
     ms_prof = e0p.elapsed_time(e1p)
     ptu.profile_enable(False)
     prof = ptu.profile_totals()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, dist)
     value = ws * dofs * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (largest share of the timed region): FP64-pipe bound for the
@@ -557,10 +561,7 @@ def main():
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         barrier()
-        if dist is not None:
-            t = torch.tensor([secs], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = t.item()
+        secs = max_over_ranks(secs, dist)
         e2e = {"value": ws * dofs * args.steps / secs, "unit": "DOF/s",
                "h2d_bytes_per_step": int(fh.nbytes), "d2h_bytes_per_step": int(uh.nbytes + 8 * (it + 1))}
         u64 = uh.copy()
@@ -597,10 +598,7 @@ def main():
         um = np.zeros((prob.N, prob.ns))
         Pm.solve(args.tol, args.max_it, u_out=um)
         Pm.close()
-        if dist is not None:
-            t = torch.tensor([mms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            mms = t.item()
+        mms = max_over_ranks(mms, dist)
         vdom = max(vprof.items(), key=lambda kv: kv[1]["ms"])[0] if vprof else None
         mixed = {"precision": variant, "value": ws * dofs * vsteps / (mms / 1e3), "unit": "DOF/s",
                  "roofline": roofline_of(vprof, vdom, variant == "fp64", dims, peaks, peak_src, tr)
