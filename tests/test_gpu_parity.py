@@ -266,3 +266,37 @@ def test_full_size_heat2d_first_steps_and_global_residual():
     F = prob.T / prob.N * f
     Bu = oracle.apply_B(prob.dim, prob.n, prob.N, prob.T, prob.coeff, u)
     assert np.linalg.norm(F - Bu) / np.linalg.norm(F) <= 1e-12 * 1.01
+
+
+def test_full_size_heat2d_mixed_first_steps_and_global_residual():
+    """The 2-D workload at full size in mixed precision (FP32 iterations, FP64 refinement): first
+    steps against the oracle's implicit Euler and the residual recomputed by the oracle's B."""
+    prob = S.heat2d_uniform(255, 1024)
+    f = S.source(prob)
+    with make(prob, precision="mixed", omega=0.5) as P:
+        u = np.zeros((prob.N, prob.ns))
+        stt, it, hist = P.solve(1e-11, 2000, u_out=u)
+    assert stt == 0
+    ref = oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, None, steps=3)
+    assert rel_err(u[:3], ref) <= MIXED_TOL
+    F = prob.T / prob.N * f
+    Bu = oracle.apply_B(prob.dim, prob.n, prob.N, prob.T, prob.coeff, u)
+    assert np.linalg.norm(F - Bu) / np.linalg.norm(F) <= 1e-11 * 1.01
+
+
+def test_full_grid_heat3d_mixed_global_residual():
+    """The 3-D workload's grid (127^3) in mixed precision with 16 steps: the residual of the
+    returned u recomputed by the oracle's B (which the CPU tests pin to implicit Euler; the
+    step-by-step comparison runs at 31^3 above -- the oracle's CG takes minutes at 127^3)."""
+    prob = S.heat3d_bumps(127, 16)
+    f, u0 = S.source(prob), S.initial(prob)
+    with make(prob, precision="mixed", omega=0.5) as P:
+        u = np.zeros((prob.N, prob.ns))
+        stt, it, hist = P.solve(1e-10, 2000, u_out=u)
+    assert stt == 0
+    F = prob.T / prob.N * f
+    if u0 is not None:
+        F = F.copy()
+        F[0] += u0.ravel()
+    Bu = oracle.apply_B(prob.dim, prob.n, prob.N, prob.T, prob.coeff, u)
+    assert np.linalg.norm(F - Bu) / np.linalg.norm(F) <= 1e-10 * 1.01
