@@ -81,6 +81,7 @@ struct pt_problem {
   double* dsti_lam = nullptr;                   // [n+1] (4 a0/h^2) sin^2(pi k h / 2) at k-1, 0 at n
   double* dsti_mu = nullptr;                    // [N] mu_k
   void* dsti_g = nullptr;                       // padded, type T: block-solve factor of each point
+  double* hy_w = nullptr;                       // FP64 2-D: padded LU pivots of the y-tridiagonal H_k
   int nv_h = 2;                                 // V-cycles per H_k solve
   void* mg_b[kMaxLevels] = {};
   void* mg_x[kMaxLevels] = {};
@@ -335,6 +336,14 @@ T* block_solve(pt_problem* p, const int* done) {
   T* W2 = (T*)p->W2;
   if (p->hdst) {
     const Level& L = p->lev[0];
+    if (p->hy_w) {
+      // FP64 2-D: S_x [T_k^-1 Z T_k^-1]_y S_x, the y-part by tridiagonal eliminations
+      launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
+      launch_hsolve_trid((double*)(void*)W1, p->hy_w, p->dsti_lam, p->tau, p->coeff.a0 / (L.h * L.h),
+                         (2.0 * p->tau / p->N) * (2.0 / L.P), p->n, L.logP, L.S, p->N, p->st);
+      launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
+      return W1;
+    }
     // x, (y,) the last axis forward-scale-inverse, (y,) x: S_x S_y S_z diag(g) S_z S_y S_x
     const int last = p->dim - 1;
     launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
@@ -807,13 +816,22 @@ pt_status setup_precision(pt_problem* p) {
     if ((st = upload<T>(p, p->dsti_sn, sn)) != PT_OK) return st;
     if ((st = upload<double>(p, p->dsti_lam, lam)) != PT_OK) return st;
     if ((st = upload<double>(p, p->dsti_mu, mud)) != PT_OK) return st;
-    // the point-wise block-solve factor, computed once in FP64 (c0 as in block_solve)
     const Level& L = p->lev[0];
-    const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
-    T* g = alloc_padded<T>(p, L, p->N, &st);
-    if (!g) return st;
-    p->dsti_g = g;
-    launch_dsti_scale_table<T>(g, p->dsti_lam, p->dsti_mu, p->tau, c0, p->dim, L.logP, L.S, p->N, p->st);
+    if (p->dim == 2 && sizeof(T) == 8) {
+      // FP64 2-D: x by transforms, y by tridiagonal eliminations (fewer FP64 operations)
+      double* w = alloc_padded<double>(p, L, p->N, &st);
+      if (!w) return st;
+      p->hy_w = w;
+      launch_hsolve_trid_table(w, p->dsti_lam, p->dsti_mu, p->tau, p->coeff.a0 / (L.h * L.h), p->n, L.logP, L.S,
+                               p->N, p->st);
+    } else {
+      // the point-wise block-solve factor, computed once in FP64 (c0 as in block_solve)
+      const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
+      T* g = alloc_padded<T>(p, L, p->N, &st);
+      if (!g) return st;
+      p->dsti_g = g;
+      launch_dsti_scale_table<T>(g, p->dsti_lam, p->dsti_mu, p->tau, c0, p->dim, L.logP, L.S, p->N, p->st);
+    }
   } else if (p->opt.h_solver == 2) {
     return fail(PT_EINVAL,
                 "exact H_k solves need dim >= 2, n + 1 <= 4096 and a reference coefficient constant in space");
