@@ -182,8 +182,8 @@ def fp64_flops_per_launch(name, dim, n, N):
         return N * n * fft_M
     if name in ("dst_forward", "dst_inverse"):  # N-point transform of every spatial point + twiddles
         return n * n * (2.5 * N * math.log2(N) + 6.0 * N)
-    if name == "hsolve_y":          # per (k, x-frequency) column: two Thomas solves (3 each) and
-        return 11.0 * pts            # the tridiagonal product (3), scaled (2 per point, FMAs count 1)
+    if name == "hsolve_y":          # per (k, x-frequency) column: two Thomas eliminations (6 flops
+        return 16.0 * pts            # each: multiply-add, multiply) and the tridiagonal product (4)
     if name == "resid_bres":        # bres (faces 8, stencil 11, K and F 3, norm 2) + r_p (13)
         return 37.0 * pts
     if name == "mg2_up":            # 3 launches (levels 0, 1, 2): prolong 5, stencil 19, smoothing 4

@@ -81,7 +81,7 @@ struct pt_problem {
   double* dsti_lam = nullptr;                   // [n+1] (4 a0/h^2) sin^2(pi k h / 2) at k-1, 0 at n
   double* dsti_mu = nullptr;                    // [N] mu_k
   void* dsti_g = nullptr;                       // padded, type T: block-solve factor of each point
-  double* hy_w = nullptr;                       // FP64 2-D: padded LU pivots of the y-tridiagonal H_k
+  void* hy_w = nullptr;                         // 2-D: padded LU pivots (type T) of the y-tridiagonal H_k
   int nv_h = 2;                                 // V-cycles per H_k solve
   void* mg_b[kMaxLevels] = {};
   void* mg_x[kMaxLevels] = {};
@@ -339,8 +339,8 @@ T* block_solve(pt_problem* p, const int* done) {
     if (p->hy_w) {
       // FP64 2-D: S_x [T_k^-1 Z T_k^-1]_y S_x, the y-part by tridiagonal eliminations
       launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
-      launch_hsolve_trid((double*)(void*)W1, p->hy_w, p->dsti_lam, p->tau, p->coeff.a0 / (L.h * L.h),
-                         (2.0 * p->tau / p->N) * (2.0 / L.P), p->n, L.logP, L.S, p->N, p->st);
+      launch_hsolve_trid<T>(W1, (const T*)p->hy_w, p->dsti_lam, p->tau, p->coeff.a0 / (L.h * L.h),
+                            (2.0 * p->tau / p->N) * (2.0 / L.P), p->n, L.logP, L.S, p->N, p->st);
       launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
       return W1;
     }
@@ -818,12 +818,14 @@ pt_status setup_precision(pt_problem* p) {
     if ((st = upload<double>(p, p->dsti_mu, mud)) != PT_OK) return st;
     const Level& L = p->lev[0];
     if (p->dim == 2 && sizeof(T) == 8) {
-      // FP64 2-D: x by transforms, y by tridiagonal eliminations (fewer FP64 operations)
-      double* w = alloc_padded<double>(p, L, p->N, &st);
+      // FP64 2-D: x by transforms, y by tridiagonal eliminations (fewer FP64 operations; their
+      // relative error ~ cond(T_k) eps64 <= 1e-9 for n + 1 <= 4096.  In FP32 cond(T_k) eps32 would
+      // reach 1e-3 at 255^2, so the FP32 form keeps the transforms, exact to ~eps32 log n.)
+      T* w = alloc_padded<T>(p, L, p->N, &st);
       if (!w) return st;
       p->hy_w = w;
-      launch_hsolve_trid_table(w, p->dsti_lam, p->dsti_mu, p->tau, p->coeff.a0 / (L.h * L.h), p->n, L.logP, L.S,
-                               p->N, p->st);
+      launch_hsolve_trid_table<T>(w, p->dsti_lam, p->dsti_mu, p->tau, p->coeff.a0 / (L.h * L.h), p->n, L.logP,
+                                  L.S, p->N, p->st);
     } else {
       // the point-wise block-solve factor, computed once in FP64 (c0 as in block_solve)
       const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);

@@ -360,11 +360,13 @@ template void launch_dsti_cols<double>(double*, int, int, int, long long, int, i
 //   up:   x_i = yh_i - a w_i x_{i+1};   z_{i+1} = cd x_{i+1} - co (x_i + x_{i+2});
 //         yh'_{i+1} = (z_{i+1} - a yh'_{i+2}) w_{n-2-i}
 //   down: v_j = yh'_j - a w_{n-1-j} v_{j-1}
-// 11 FP64 operations per point against 36 for two y-transforms and the factor.
+// 11 operations per point against 36 for two y-transforms and the factor.  Used in FP64 (the
+// elimination's error grows with cond(T), which FP32 cannot afford).
 namespace pt {
 namespace {
 
-__global__ void k_hsolve_trid_table(double* __restrict__ w, const double* __restrict__ lam,
+template <typename T>
+__global__ void k_hsolve_trid_table(T* __restrict__ w, const double* __restrict__ lam,
                                     const double* __restrict__ mu, double tau, double a0h2, int n, int logP,
                                     long long S, int N) {
   const int P = 1 << logP;
@@ -373,41 +375,42 @@ __global__ void k_hsolve_trid_table(double* __restrict__ w, const double* __rest
   const int k = (int)(col >> logP), x = (int)(col & (P - 1));
   if (x >= n) return;
   const double d = mu[k] + tau * (lam[x] + 2.0 * a0h2), a = -tau * a0h2;
-  double* wc = w + (long long)k * S + x;
-  double wi = 1.0 / d;
-  wc[0] = wi;
+  T* wc = w + (long long)k * S + x;
+  double wi = 1.0 / d;  // pivots in FP64, stored in T
+  wc[0] = (T)wi;
   for (int i = 1; i < n; ++i) {
     wi = 1.0 / (d - a * a * wi);
-    wc[(long long)i * P] = wi;
+    wc[(long long)i * P] = (T)wi;
   }
 }
 
-__global__ void __launch_bounds__(128) k_hsolve_trid(double* __restrict__ X, const double* __restrict__ w,
-                                                      const double* __restrict__ lam, double tau, double a0h2,
-                                                      double scale, int n, int logP, long long S) {
+template <typename T>
+__global__ void __launch_bounds__(128) k_hsolve_trid(T* __restrict__ X, const T* __restrict__ w,
+                                                      const double* __restrict__ lam, double tau_d, double a0h2_d,
+                                                      double scale_d, int n, int logP, long long S) {
   const int P = 1 << logP;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (x >= n) return;
-  const double a = -tau * a0h2;
-  const double cd = scale * (lam[x] + 2.0 * a0h2), co = scale * a0h2;
-  double* c = X + (long long)k * S + x;
-  const double* wc = w + (long long)k * S + x;
+  const T a = (T)(-tau_d * a0h2_d);
+  const T cd = (T)(scale_d * (lam[x] + 2.0 * a0h2_d)), co = (T)(scale_d * a0h2_d);
+  T* c = X + (long long)k * S + x;
+  const T* wc = w + (long long)k * S + x;
   auto at = [&](int i) { return (long long)i * P; };
   // down: forward elimination with T
-  double yh = 0.0;
+  T yh = (T)0;
 #pragma unroll 4
   for (int i = 0; i < n; ++i) {
     yh = (c[at(i)] - a * yh) * wc[at(i)];
     c[at(i)] = yh;
   }
   // up: back substitution -> x_i; z one row behind; forward elimination of the reversed system
-  double x2 = 0.0, x1 = 0.0, yr = 0.0;  // x_{i+2}, x_{i+1}, yh' of the row above
+  T x2 = (T)0, x1 = (T)0, yr = (T)0;  // x_{i+2}, x_{i+1}, yh' of the row above
 #pragma unroll 4
   for (int i = n - 1; i >= 0; --i) {
-    const double xi = c[at(i)] - a * wc[at(i)] * x1;
+    const T xi = c[at(i)] - a * wc[at(i)] * x1;
     if (i + 1 <= n - 1) {
-      const double z = cd * x1 - co * (xi + x2);  // row i+1
+      const T z = cd * x1 - co * (xi + x2);  // row i+1
       yr = (z - a * yr) * wc[at(n - 2 - i)];
       c[at(i + 1)] = yr;
     }
@@ -415,12 +418,12 @@ __global__ void __launch_bounds__(128) k_hsolve_trid(double* __restrict__ X, con
     x1 = xi;
   }
   {
-    const double z = cd * x1 - co * x2;  // row 0 (x_{-1} = 0)
+    const T z = cd * x1 - co * x2;  // row 0 (x_{-1} = 0)
     yr = (z - a * yr) * wc[at(n - 1)];
     c[at(0)] = yr;
   }
   // down: back substitution of the reversed system
-  double v = 0.0;
+  T v = (T)0;
 #pragma unroll 4
   for (int j = 0; j < n; ++j) {
     v = c[at(j)] - a * wc[at(n - 1 - j)] * v;
@@ -430,19 +433,29 @@ __global__ void __launch_bounds__(128) k_hsolve_trid(double* __restrict__ X, con
 
 }  // namespace
 
-void launch_hsolve_trid_table(double* w, const double* lam, const double* mu, double tau, double a0h2, int n,
-                              int logP, long long S, int N, cudaStream_t st) {
+template <typename T>
+void launch_hsolve_trid_table(T* w, const double* lam, const double* mu, double tau, double a0h2, int n, int logP,
+                              long long S, int N, cudaStream_t st) {
   const long long cols = (long long)N << logP;
-  LaunchScope ls("hsolve_table", st, 8.0 * (double)N * n * n);
-  k_hsolve_trid_table<<<(unsigned)((cols + 127) / 128), 128, 0, st>>>(w, lam, mu, tau, a0h2, n, logP, S, N);
+  LaunchScope ls("hsolve_table", st, sizeof(T) * (double)N * n * n);
+  k_hsolve_trid_table<T><<<(unsigned)((cols + 127) / 128), 128, 0, st>>>(w, lam, mu, tau, a0h2, n, logP, S, N);
 }
 
-void launch_hsolve_trid(double* X, const double* w, const double* lam, double tau, double a0h2, double scale,
-                        int n, int logP, long long S, int N, cudaStream_t st) {
+template <typename T>
+void launch_hsolve_trid(T* X, const T* w, const double* lam, double tau, double a0h2, double scale, int n,
+                        int logP, long long S, int N, cudaStream_t st) {
   const int P = 1 << logP;
-  LaunchScope ls("hsolve_y", st, 7.0 * 8.0 * (double)N * n * n);
+  LaunchScope ls("hsolve_y", st, 7.0 * sizeof(T) * (double)N * n * n);
   const dim3 grid((unsigned)((P + 127) / 128), (unsigned)N);
-  k_hsolve_trid<<<grid, 128, 0, st>>>(X, w, lam, tau, a0h2, scale, n, logP, S);
+  k_hsolve_trid<T><<<grid, 128, 0, st>>>(X, w, lam, tau, a0h2, scale, n, logP, S);
 }
+template void launch_hsolve_trid_table<float>(float*, const double*, const double*, double, double, int, int,
+                                              long long, int, cudaStream_t);
+template void launch_hsolve_trid_table<double>(double*, const double*, const double*, double, double, int, int,
+                                               long long, int, cudaStream_t);
+template void launch_hsolve_trid<float>(float*, const float*, const double*, double, double, double, int, int,
+                                        long long, int, cudaStream_t);
+template void launch_hsolve_trid<double>(double*, const double*, const double*, double, double, double, int, int,
+                                         long long, int, cudaStream_t);
 
 }  // namespace pt

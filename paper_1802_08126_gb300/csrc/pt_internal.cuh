@@ -280,10 +280,12 @@ void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int ax
                       const void* sn, const void* gtab, bool scale, cudaStream_t st);
 // FP64 2-D: y-part of the exact block solve by tridiagonal eliminations (kernels_dsti.cu);
 // w padded like the data: the LU pivots 1/d'_i of every (k, x-frequency) column.
-void launch_hsolve_trid_table(double* w, const double* lam, const double* mu, double tau, double a0h2, int n,
-                              int logP, long long S, int N, cudaStream_t st);
-void launch_hsolve_trid(double* X, const double* w, const double* lam, double tau, double a0h2, double scale,
-                        int n, int logP, long long S, int N, cudaStream_t st);
+template <typename T>
+void launch_hsolve_trid_table(T* w, const double* lam, const double* mu, double tau, double a0h2, int n, int logP,
+                              long long S, int N, cudaStream_t st);
+template <typename T>
+void launch_hsolve_trid(T* X, const T* w, const double* lam, double tau, double a0h2, double scale, int n,
+                        int logP, long long S, int N, cudaStream_t st);
 template <typename T>
 void launch_dsti_scale_table(T* g, const double* lam, const double* mu, double tau, double c0, int dim, int logP,
                              long long S, int B, cudaStream_t st);
