@@ -110,7 +110,7 @@ struct pt_problem {
   void* tri_work = nullptr;
   bool hvar = true;                             // Abar has a non-constant coefficient
   void* dinvH[kMaxLevels] = {};                 // [N] w / D of H_k per level (constant Abar)
-  void* jinvA[kMaxLevels] = {};                 // cached w / D of tau A_n per level (FP64, 2-D)
+  void* jinvA[kMaxLevels] = {};                 // cached (w / D, D) of tau A_n per level (FP64, 2-D)
   double* partials = nullptr;
   SolveState* state = nullptr;
   double* hist = nullptr;
@@ -838,10 +838,11 @@ pt_status setup_precision(pt_problem* p) {
     return fail(PT_EINVAL,
                 "exact H_k solves need dim >= 2, n + 1 <= 4096 and a reference coefficient constant in space");
   }
-  // FP64 2-D: cache w / D of every tau A_n (a division per point per smoothing step otherwise)
+  // FP64 2-D: cache (w / D, D) of every tau A_n (a division per point per smoothing step, and
+  // four FP64 operations per stencil, otherwise)
   if (!p->exact1d && p->dim == 2 && sizeof(T) == 8) {
     for (int l = 0; l < p->lc_max; ++l) {
-      T* j = alloc_padded<T>(p, p->lev[l], p->N, &st);
+      T* j = alloc_padded<T>(p, p->lev[l], 2 * p->N, &st);  // pairs (w / D, D)
       if (!j) return st;
       p->jinvA[l] = j;
       launch_make_jinv<T>(j, geom<T>(p, l), op_A<T>(p), p->N, p->st);
@@ -1162,7 +1163,7 @@ size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o) {
   if (d >= 2) per += s;                     // block-solve factor table (exact H_k solves)
   per += (d == 2 ? 2.0 : 3.0) * s * lev;    // multigrid right-hand sides, iterates (and residuals)
   if (d != 2) per += 2.0 * s;               // generic path: level-0 iterate and residual
-  if (d == 2 && !mixed) per += 8.0 * (1.0 + lev);  // cached Jacobi factors
+  if (d == 2 && !mixed) per += 16.0 * (1.0 + lev);  // cached (Jacobi factor, diagonal) pairs
   return (size_t)(padded * per * 1.05) + (size_t)(4u << 20);
 }
 

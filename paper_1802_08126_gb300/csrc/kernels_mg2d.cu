@@ -12,6 +12,8 @@
 // whose coefficient oscillates in time).  The Jacobi factor w D^-1 is a per-slice constant
 // (constant coefficient), read from a per-level cache (FP64 variable coefficient, where the
 // division would dominate the FP64 instruction budget), or computed (FP32).
+#include <type_traits>
+
 #include "stencil_common.cuh"
 
 namespace pt {
@@ -33,7 +35,7 @@ struct Mg2Args {
   const T* sig;       // [B]
   const T* cth;       // [B]
   const T* dinv;      // [B] w / D per slice (DM == 0)
-  const T* jinv;      // cached w / D, fine padded layout (DM == 1)
+  const T* jinv;      // cached pairs (w / D, D) per point, fine padded layout (DM == 1)
   T omega;
 };
 
@@ -69,7 +71,7 @@ template <typename T, bool VAR, int DM>
 __device__ __forceinline__ T jacobi_factor(const Mg2Args<T>& a, int b, long long gi, const T* fxs,
                                            const T* fys, int RW, int ry, int rx, T sig) {
   if (DM == 0) return a.dinv[b];
-  if (DM == 1) return a.jinv[gi];
+  if (DM == 1) return a.jinv[2 * gi];
   T dsum;
   if (VAR) {
     dsum = fxs[ry * (RW + 1) + rx] + fxs[ry * (RW + 1) + rx + 1] + fys[ry * RW + rx] + fys[(ry + 1) * RW + rx];
@@ -119,7 +121,17 @@ __global__ void __launch_bounds__(256) k_mg2_down(const T* __restrict__ bf, T* _
     const int c = ry * RW + rx;
     const T xc = sx[c];
     T Lx;
-    if (VAR) {
+    if (DM == 1) {
+      // cached diagonal D = sig + sum of faces: L x = D x_c - sum_f a_f x_f (fewer FP64 operations)
+      const int x = fx0 + rx, y = fy0 + ry;
+      Lx = (T)0;
+      if (x < a.nf && y < a.nf) {
+        const T D = a.jinv[2 * (base + (long long)y * Pf + x) + 1];
+        const T aw = sfx[ry * (RW + 1) + rx], ae = sfx[ry * (RW + 1) + rx + 1];
+        const T as = sfy[ry * RW + rx], an = sfy[(ry + 1) * RW + rx];
+        Lx = D * xc - (aw * sx[c - 1] + ae * sx[c + 1] + as * sx[c - RW] + an * sx[c + RW]);
+      }
+    } else if (VAR) {
       const T aw = sfx[ry * (RW + 1) + rx], ae = sfx[ry * (RW + 1) + rx + 1];
       const T as = sfy[ry * RW + rx], an = sfy[(ry + 1) * RW + rx];
       Lx = sig * xc + aw * (xc - sx[c - 1]) + ae * (xc - sx[c + 1]) + as * (xc - sx[c - RW]) +
@@ -284,7 +296,7 @@ struct FaceSweep {
 template <typename T, bool VAR, int DM>
 __device__ __forceinline__ T jacobi_at(const Mg2Args<T>& a, int b, long long gi, const Faces<T, VAR>& f, T sig) {
   if (DM == 0) return a.dinv[b];
-  if (DM == 1) return a.jinv[gi];
+  if (DM == 1) return a.jinv[2 * gi];
   return a.omega / (sig + ((f.xl + f.xr) + (f.yl + f.yu)));
 }
 
@@ -375,6 +387,7 @@ template <typename T, bool VAR, int DM>
 __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const T* __restrict__ ec, void* out,
                                                  int mode, int out_fp64, Mg2Args<T> a, int wpr, int strips,
                                                  long long nwarps, const int* done) {
+  using T2c = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
   if (stop_requested(done)) return;
   const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (wg >= nwarps) return;
@@ -419,11 +432,12 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
     const long long gi = base + (long long)y * Pf + x;
     return out_fp64 ? ((const double*)out)[gi] : (double)((const T*)out)[gi];
   };
-  auto row = [&](int y, T bload, T& bv, T& x2, T& jf, Faces<T, VAR>& f) {
+  auto row = [&](int y, T bload, T& bv, T& x2, T& jf, T& dg, Faces<T, VAR>& f) {
     f = fs.row(a, fx, ny, fy, cths, x, y);
     bv = (T)0;
     x2 = (T)0;
     jf = (T)0;
+    dg = (T)0;
     // prolongation of the coarse correction (rows: odd y -> (y-1)/2, even y -> y/2 - 1 and y/2)
     T pe;
     if (y & 1) {
@@ -442,21 +456,27 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
     if (xin && y >= 0 && y < nf) {
       const long long gi = base + (long long)y * Pf + x;
       bv = bload;
-      jf = jacobi_at<T, VAR, DM>(a, b, gi, f, sig);
+      if (DM == 1) {
+        const T2c jd = *(const T2c*)(a.jinv + 2 * gi);  // (w / D, D)
+        jf = jd.x;
+        dg = jd.y;
+      } else {
+        jf = jacobi_at<T, VAR, DM>(a, b, gi, f, sig);
+      }
       x2 = fma(bv, jf, pe);
     }
   };
-  T bm, xm, jm, bcv, xc, jc, bn, xn, jn;
+  T bm, xm, jm, bcv, xc, jc, bn, xn, jn, dm_, dc_, dn_;
   Faces<T, VAR> fm, fc, fn;
-  row(y0 - 1, ld_b(y0 - 1), bm, xm, jm, fm);
-  row(y0, ld_b(y0), bcv, xc, jc, fc);
+  row(y0 - 1, ld_b(y0 - 1), bm, xm, jm, dm_, fm);
+  row(y0, ld_b(y0), bcv, xc, jc, dc_, fc);
   T b_next = ld_b(y0 + 1);
   double o_next = ld_o(y0);
   for (int y = y0; y < y0 + kStripUpRows && y < Pf; ++y) {
     const T b_after = ld_b(y + 2);
     const double o_cur = o_next;
     o_next = ld_o(y + 1);
-    row(y + 1, b_next, bn, xn, jn, fn);
+    row(y + 1, b_next, bn, xn, jn, dn_, fn);
     b_next = b_after;
     const T xW = __shfl_up_sync(0xffffffffu, xc, 1);
     const T xE = __shfl_down_sync(0xffffffffu, xc, 1);
@@ -464,7 +484,9 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
       const long long gi = base + (long long)y * Pf + x;
       if (xin && y < nf) {
         T Lx;
-        if (VAR)
+        if (DM == 1)
+          Lx = dc_ * xc - (fc.xl * xW + fc.xr * xE + fc.yl * xm + fc.yu * xn);
+        else if (VAR)
           Lx = sig * xc + fc.xl * (xc - xW) + fc.xr * (xc - xE) + fc.yl * (xc - xm) + fc.yu * (xc - xn);
         else
           Lx = (sig + (T)4 * a.a0s) * xc - a.a0s * ((xW + xE) + (xm + xn));
@@ -484,31 +506,36 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
     bm = bcv;
     xm = xc;
     jm = jc;
+    dm_ = dc_;
     fm = fc;
     bcv = bn;
     xc = xn;
     jc = jn;
+    dc_ = dn_;
     fc = fn;
   }
   (void)bm;
   (void)jm;
+  (void)dm_;
   (void)fm;
 }
 
-// w D^-1 for every interior point of one level (FP64 variable-coefficient cache)
+// (w D^-1, D) for every interior point of one level (FP64 variable-coefficient cache)
 template <typename T>
 __global__ void k_make_jinv(T* __restrict__ jinv, StencilGeom<T> g, OpBatch<T> op, long long total) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     long long t;
     int x, y, z;
-    T v = (T)0;
+    T v = (T)0, d = (T)0;
     if (decode<2>(i, g.logP, g.n, t, x, y, z)) {
       T am[3], ap[3];
       face_coefs<2, T>(g.tab, g.P, x, y, z, op.cth[t], g.a0, am, ap);
-      v = op.omega / (op.sig[t] + op.s * g.h2inv * face_sum<2, T>(am, ap));
+      d = op.sig[t] + op.s * g.h2inv * face_sum<2, T>(am, ap);
+      v = op.omega / d;
     }
-    jinv[i] = v;
+    jinv[2 * i] = v;
+    jinv[2 * i + 1] = d;
   }
 }
 
