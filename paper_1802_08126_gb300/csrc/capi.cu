@@ -416,7 +416,8 @@ void enqueue_iteration(pt_problem* p) {
     // outer residual first (and the convergence test), then the p-update and the stencil-free r_u
     const Level& L0 = p->lev[0];
     launch_resid_bres_2d<T>(p->u, p->p, p->F, p->bres, W1, p->partials, p->tab_d + L0.tab, p->tab_f + L0.tab,
-                            p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N, done, p->st);
+                            p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N, done,
+                            (const double*)p->jinvA[0], p->st);
     launch_finalize_residual(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->p, 1, 1, done);
     launch_resid_u_from_bres<T>(p->bres, p->u, p->p, W1, L0.S, p->N, p->dim, p->n, done, p->st);

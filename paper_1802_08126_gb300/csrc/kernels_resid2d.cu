@@ -21,13 +21,15 @@ constexpr int kRows = 16;
 // IR = true: the FP64 step of the mixed-precision refinement -- instead of bres and r_p it writes
 // the FP32 right-hand sides R1 = bres + tau A w, R2 = bres - K^T w and r_p' = -R1, and runs only
 // on refinement iterations (state flags).
-template <typename W, bool IR>
+// DG = true (FP64 path): the cached pairs (w/D, D) of tau A_n give the diagonal, and both
+// stencils are D x_c - sum_f a_f x_f (six fewer FP64 operations per point).
+template <typename W, bool IR, bool DG = false>
 __global__ void __launch_bounds__(256) k_resid_bres_2d(
     const double* __restrict__ u, const double* __restrict__ p, const double* __restrict__ F,
     double* __restrict__ bres, W* __restrict__ rp, double* __restrict__ partials,
     const double* __restrict__ tab, const float* __restrict__ tabf, const double* __restrict__ cth,
     double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, const int* done,
-    float* __restrict__ R1, float* __restrict__ R2, const SolveState* st) {
+    float* __restrict__ R1, float* __restrict__ R2, const SolveState* st, const double* __restrict__ jd = nullptr) {
   if (IR) {
     if (*((volatile const int*)&st->done) != 0 || !*((volatile const int*)&st->outer)) return;
   } else if (stop_requested(done)) {
@@ -94,7 +96,10 @@ __global__ void __launch_bounds__(256) k_resid_bres_2d(
         const double axl = fma(gy, fxl, a0s), axr = fma(gy, fxr, a0s);
         const double uW = u[i - 1], uE = u[i + 1];
         const double um = t > 0 ? u[i - S] : 0.0;
-        const double su = axl * (u_c - uW) + axr * (u_c - uE) + ayl * (u_c - u_m) + ayu * (u_c - u_p);
+        double D = 0.0;
+        if constexpr (DG) D = ((const double2*)jd)[i].y;
+        const double su = DG ? D * u_c - (axl * uW + axr * uE + ayl * u_m + ayu * u_p)
+                             : axl * (u_c - uW) + axr * (u_c - uE) + ayl * (u_c - u_m) + ayu * (u_c - u_p);
         b = F[i] - (u_c - um) - su;
         acc = fma(b, b, acc);
         W sw;
@@ -103,6 +108,8 @@ __global__ void __launch_bounds__(256) k_resid_bres_2d(
           const float axlf = fmaf(gyf, fxlf, a0f), axrf = fmaf(gyf, fxrf, a0f);
           sw = (W)(axlf * ((float)w_c - (float)wW) + axrf * ((float)w_c - (float)wE) +
                    aylf * ((float)w_c - (float)w_m) + ayuf * ((float)w_c - (float)w_p));
+        } else if constexpr (DG) {
+          sw = (W)(D * (double)w_c - (axl * (double)wW + axr * (double)wE + ayl * (double)w_m + ayu * (double)w_p));
         } else {
           sw = (W)(axl * ((double)w_c - (double)wW) + axr * ((double)w_c - (double)wE) +
                    ayl * ((double)w_c - (double)w_m) + ayu * ((double)w_c - (double)w_p));
@@ -145,14 +152,19 @@ template <typename W>
 void launch_resid_bres_2d(const double* u, const double* p, const double* F, double* bres, W* rp,
                           double* partials, const double* tab, const float* tabf, const double* cth, double a0,
                           double tau, double h, int n, int logP, long long S, int N, const int* done,
-                          cudaStream_t st) {
+                          const double* jd, cudaStream_t st) {
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("resid_bres", st, (24.0 + 8.0 + sizeof(W)) * (double)n * n * N);
-  k_resid_bres_2d<W, false><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth, s_h2 * a0,
-                                                              s_h2, n, logP, S, N, nwarps, done, nullptr, nullptr,
-                                                              nullptr);
+  if (sizeof(W) == 8 && jd)
+    k_resid_bres_2d<W, false, true><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth,
+                                                                    s_h2 * a0, s_h2, n, logP, S, N, nwarps, done,
+                                                                    nullptr, nullptr, nullptr, jd);
+  else
+    k_resid_bres_2d<W, false><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth, s_h2 * a0,
+                                                                s_h2, n, logP, S, N, nwarps, done, nullptr, nullptr,
+                                                                nullptr);
 }
 
 void launch_ir_outer_2d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
@@ -170,10 +182,10 @@ void launch_ir_outer_2d(const double* u, const double* p, const double* F, float
 
 template void launch_resid_bres_2d<float>(const double*, const double*, const double*, double*, float*, double*,
                                           const double*, const float*, const double*, double, double, double, int,
-                                          int, long long, int, const int*, cudaStream_t);
+                                          int, long long, int, const int*, const double*, cudaStream_t);
 template void launch_resid_bres_2d<double>(const double*, const double*, const double*, double*, double*, double*,
                                            const double*, const float*, const double*, double, double, double, int,
-                                           int, long long, int, const int*, cudaStream_t);
+                                           int, long long, int, const int*, const double*, cudaStream_t);
 
 }  // namespace pt
 

@@ -117,11 +117,12 @@ void launch_resid_u_from_bres(const double* bres, const double* u, const double*
 // 2-D (n + 1 >= 32) fused outer residual: bres = F - B u (FP64, stored, norm partials over a fixed
 // grid of kReduceBlocks blocks) and r_p = -bres - tau A (p + u) in precision W (FP32: the w-stencil
 // in FP32; FP64: all in FP64).  tab / tabf: level-0 coefficient tables in FP64 / FP32.
+// jd: cached (w/D, D) pairs of tau A_n at level 0, or null (FP64: the stencils then use D)
 template <typename W>
 void launch_resid_bres_2d(const double* u, const double* p, const double* F, double* bres, W* rp,
                           double* partials, const double* tab, const float* tabf, const double* cth, double a0,
                           double tau, double h, int n, int logP, long long S, int N, const int* done,
-                          cudaStream_t st);
+                          const double* jd, cudaStream_t st);
 
 // out = scale * A(cthbar) z on one batch (Abar apply of the Hhat block solve)
 template <typename T>
