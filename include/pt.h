@@ -101,7 +101,9 @@ typedef struct {
                             sine transforms, when the reference coefficient is constant in space,
                             dim is 2 or 3 and n + 1 <= 4096; else V-cycles), 1 = V-cycles,
                             2 = exact (PT_EINVAL if unavailable) */
-  int reserved[2];       /* must be zero */
+  int krylov;            /* 0: the Uzawa iteration of eq. 3.1; m in [1, 64]: flexible GMRES(m)
+                            right-preconditioned by one inexact Uzawa step (FP64 only) */
+  int reserved[1];       /* must be zero */
 } pt_options;
 
 typedef struct pt_problem pt_problem; /* opaque, library-owned */

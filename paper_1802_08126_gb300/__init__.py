@@ -217,7 +217,7 @@ class Problem:
                  precision: str = "fp64", omega: float = 0.0, solver: str = "mg",
                  stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0,
                  autotune: bool = False, dst_cols: int = 0, coarse_elems: int = 0,
-                 graphs: bool = True, n_vcycles: int = 0, h_solver: str = "auto"):
+                 graphs: bool = True, n_vcycles: int = 0, h_solver: str = "auto", krylov: int = 0):
         L = _lib.load()
         self._lib = L
         self.dim, self.n, self.N, self.T = dim, list(n)[:dim], N, float(T)
@@ -239,6 +239,7 @@ class Problem:
         opts.coarse_elems = int(coarse_elems)
         opts.no_graphs = 0 if graphs else 1
         opts.h_solver = {"auto": 0, "vcycle": 1, "exact": 2}[h_solver]
+        opts.krylov = int(krylov)
         self._opts = opts
         fp, fdev = _ptr(f)
         up, udev = _ptr(u0)

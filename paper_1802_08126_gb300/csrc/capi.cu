@@ -98,6 +98,14 @@ struct pt_problem {
   void* dst_pre = nullptr;                      // [N] complex
   int blueM = 0, blueLogM = 0;                  // Bluestein length (N not a power of two)
   void* dst_twS = nullptr;                      // [N] complex e^{-2 pi i e / N} (power-of-two N)
+  // Krylov acceleration (FP64): V[0..m], Z[0..m-1] and a work pair, device pointer tables
+  int kr_m = 0;
+  std::vector<double*> kr_vp, kr_vu, kr_zp, kr_zu;
+  double* kr_wp = nullptr;
+  double* kr_wu = nullptr;
+  double** kr_tab = nullptr;      // device: [vp(m+1) | vu(m+1) | zp(m) | zu(m)]
+  double* kr_coef = nullptr;      // device [m + 1]
+  double* kr_part = nullptr;      // device [(m + 1) * kReduceBlocks]
   float* ir_du = nullptr;                       // mixed: FP32 corrections of u and p, residuals
   float* ir_dp = nullptr;
   float* ir_R1 = nullptr;
@@ -571,6 +579,238 @@ pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* r
   return finish_solve(p, iters_out, res_hist);
 }
 
+// ---- Krylov acceleration: flexible GMRES(m) preconditioned by one inexact Uzawa step --------
+// Solves Sad (p, u) = (F, F) (the system the Uzawa iteration of eq. 3.1 solves) with the right
+// preconditioner M^-1 (v_p, v_u) = (-A~^-1 v_p, H~^-1 (v_u - K^T z_p)): the block lower-triangular
+// M = [-A~, 0; K^T, H~] of the Uzawa step with omega = 1.  Classical Gram-Schmidt with selective
+// reorthogonalisation, Givens rotations on the host.  The history holds the preconditioned saddle-point residual
+// relative to ||(F, F)||; a cycle ends when it reaches the tolerance, and the solve ends only when
+// ||F - B u|| / ||F|| of the updated u (computed in FP64) does, else it restarts with a tenfold
+// smaller inner target.
+
+pt_status krylov_alloc(pt_problem* p, int m) {
+  if (p->kr_m == m) return PT_OK;
+  if (p->kr_m != 0) return fail(PT_EINVAL, "the Krylov restart length of a problem cannot change");
+  pt_status st = PT_OK;
+  const Level& L0 = p->lev[0];
+  auto vec = [&]() -> double* { return alloc_padded<double>(p, L0, p->N, &st); };
+  for (int k = 0; k <= m; ++k) {
+    double* a = vec();
+    double* b = a ? vec() : nullptr;
+    if (!b) return st;
+    p->kr_vp.push_back(a);
+    p->kr_vu.push_back(b);
+  }
+  for (int k = 0; k < m; ++k) {
+    double* a = vec();
+    double* b = a ? vec() : nullptr;
+    if (!b) return st;
+    p->kr_zp.push_back(a);
+    p->kr_zu.push_back(b);
+  }
+  if (!(p->kr_wp = vec()) || !(p->kr_wu = vec())) return st;
+  std::vector<double*> tab;
+  tab.insert(tab.end(), p->kr_vp.begin(), p->kr_vp.end());
+  tab.insert(tab.end(), p->kr_vu.begin(), p->kr_vu.end());
+  tab.insert(tab.end(), p->kr_zp.begin(), p->kr_zp.end());
+  tab.insert(tab.end(), p->kr_zu.begin(), p->kr_zu.end());
+  if (!(p->kr_tab = (double**)alloc_bytes(p, sizeof(double*) * tab.size(), &st))) return st;
+  PT_CUDA(cudaMemcpyAsync(p->kr_tab, tab.data(), sizeof(double*) * tab.size(), cudaMemcpyHostToDevice, p->st));
+  if (!(p->kr_coef = (double*)alloc_bytes(p, sizeof(double) * (m + 1), &st))) return st;
+  if (!(p->kr_part = (double*)alloc_bytes(p, sizeof(double) * (m + 1) * kReduceBlocks, &st))) return st;
+  p->kr_m = m;
+  return PT_OK;
+}
+
+// dots <w, v_k>, first <= k < first + nv (host result, fixed summation order)
+pt_status krylov_dots(pt_problem* p, int nv, const double* wp, const double* wu, std::vector<double>& out,
+                      int first = 0) {
+  const long long total = p->lev[0].S * p->N;
+  launch_multidot((const double* const*)(p->kr_tab + first), (const double* const*)(p->kr_tab + p->kr_m + 1 + first),
+                  wp, wu, nv, total, p->kr_part, p->st);
+  std::vector<double> part((size_t)nv * kReduceBlocks);
+  PT_CUDA(cudaMemcpyAsync(part.data(), p->kr_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, p->st));
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  out.assign(nv, 0.0);
+  for (int k = 0; k < nv; ++k)
+    for (int b = 0; b < kReduceBlocks; ++b) out[k] += part[(size_t)k * kReduceBlocks + b];
+  return PT_OK;
+}
+
+// (wp, wu) += sum_k c_k x_k over the table rows [first, first + nv) (vp) and the matching u rows
+pt_status krylov_axpy(pt_problem* p, int first_p, int first_u, const std::vector<double>& c, double* wp,
+                      double* wu) {
+  const long long total = p->lev[0].S * p->N;
+  PT_CUDA(cudaMemcpyAsync(p->kr_coef, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice, p->st));
+  launch_multiaxpy((const double* const*)(p->kr_tab + first_p), (const double* const*)(p->kr_tab + first_u),
+                   p->kr_coef, (int)c.size(), wp, wu, total, p->st);
+  PT_CHECK_LAUNCH();
+  return PT_OK;
+}
+
+// ||F - B u||^2 / ||F||^2 of the current u (FP64): the r_u kernel's partial sums
+pt_status krylov_true_residual(pt_problem* p, double* res) {
+  const StencilGeom<double> g = geom<double>(p, 0);
+  launch_resid_u<double>(p->u, p->p, p->F, (double*)p->W2, p->partials, g, p->cth_d, p->tau, p->N, nullptr, p->st);
+  std::vector<double> part(kReduceBlocks);
+  PT_CUDA(cudaMemcpyAsync(part.data(), p->partials, sizeof(double) * kReduceBlocks, cudaMemcpyDeviceToHost, p->st));
+  SolveState hs;
+  pt_status st = read_state(p, &hs);
+  if (st != PT_OK) return st;
+  double s = 0.0;
+  for (double v : part) s += v;
+  *res = std::sqrt(s / hs.fnorm2);
+  return PT_OK;
+}
+
+// z = M^-1 v for the pair k of the table
+void krylov_precondition(pt_problem* p, int k) {
+  const Level& L0 = p->lev[0];
+  double* vp = p->kr_vp[k];
+  double* vu = p->kr_vu[k];
+  double* zp = p->kr_zp[k];
+  double* zu = p->kr_zu[k];
+  double* a = (double*)p->W2;
+  double* W1 = (double*)p->W1;
+  apply_precond_A<double>(p, vp, a, 0, 1, nullptr);          // a = A~^-1 v_p
+  launch_scale_pair(a, a, -1.0, zp, zp, L0.S * p->N, p->st);  // z_p = -a (both halves: same buffers)
+  launch_uzawa_ru(vu, zp, W1, L0.S, p->N, p->st);             // W1 = v_u - K^T z_p
+  const DstPlan<double> dp = dst_plan<double>(p);
+  launch_dst_forward<double>(W1, L0.S, p->dim, p->n, L0.logP, dp, nullptr, p->st);
+  double* yhat = block_solve<double>(p, nullptr);
+  cudaMemsetAsync(zu, 0, sizeof(double) * L0.S * p->N, p->st);
+  launch_dst_inverse<double>(yhat, zu, 1, 1.0, L0.S, p->dim, p->n, L0.logP, dp, nullptr, p->st);
+}
+
+pt_status krylov_solve(pt_problem* p, double tol, int max_it, int* iters_out, double* res_hist) {
+  const int m = p->opt.krylov;
+  pt_status st = krylov_alloc(p, m);
+  if (st != PT_OK) return st;
+  if ((st = enqueue_reset(p, tol, max_it)) != PT_OK) return st;  // u = p = 0, ||F||^2
+  const long long total = p->lev[0].S * p->N;
+  const StencilGeom<double> g = geom<double>(p, 0);
+  double* xp = p->p;
+  double* xu = p->u;
+  std::vector<double> hist;
+  double res_true = 1.0;
+  hist.push_back(1.0);
+  int it = 0;
+  double inner_tol = tol;
+  double beta0 = 0.0;
+  pt_status out = PT_ENOTCONV;
+  std::vector<double> dots, dots2;
+  while (it < max_it) {
+    // r = (F, F) - Sad x  -> V_0 = r / beta
+    launch_apply_saddle(xp, xu, p->kr_wp, p->kr_wu, g, p->cth_d, p->tau, p->N, p->st);
+    launch_scale_pair(p->kr_wp, p->kr_wu, -1.0, p->kr_wp, p->kr_wu, total, p->st);
+    {
+      // add (F, F): F is not in the table, use it as a one-term sum through the work slot of V_m
+      launch_scale_pair(p->F, p->F, 1.0, p->kr_vp[m], p->kr_vu[m], total, p->st);
+      if ((st = krylov_axpy(p, m, 2 * m + 1, {1.0}, p->kr_wp, p->kr_wu)) != PT_OK) return st;
+    }
+    // beta = ||r||
+    launch_scale_pair(p->kr_wp, p->kr_wu, 1.0, p->kr_vp[0], p->kr_vu[0], total, p->st);
+    if ((st = krylov_dots(p, 1, p->kr_wp, p->kr_wu, dots)) != PT_OK) return st;
+    const double beta = std::sqrt(std::max(dots[0], 0.0));
+    if (beta0 == 0.0) beta0 = beta > 0.0 ? beta : 1.0;
+    if (!(beta > 0.0)) {
+      out = PT_OK;
+      break;
+    }
+    launch_scale_pair(p->kr_wp, p->kr_wu, 1.0 / beta, p->kr_vp[0], p->kr_vu[0], total, p->st);
+    std::vector<std::vector<double>> H(m + 1, std::vector<double>(m, 0.0));
+    std::vector<double> cs(m, 0.0), sn(m, 0.0), gv(m + 1, 0.0);
+    gv[0] = beta;
+    int j = 0;
+    for (; j < m && it < max_it; ++j) {
+      krylov_precondition(p, j);
+      launch_apply_saddle(p->kr_zp[j], p->kr_zu[j], p->kr_wp, p->kr_wu, g, p->cth_d, p->tau, p->N, p->st);
+      // classical Gram-Schmidt with selective reorthogonalisation: the copy of w in V_{j+1} gives
+      // ||w|| in the same pass; a second pass only when the projection removed more than half of
+      // w's norm squared (Kahan-Parlett "twice is enough")
+      double h = 0.0;
+      bool exact_norm = true;
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_scale_pair(p->kr_wp, p->kr_wu, 1.0, p->kr_vp[j + 1], p->kr_vu[j + 1], total, p->st);
+        if ((st = krylov_dots(p, j + 2, p->kr_wp, p->kr_wu, dots)) != PT_OK) return st;
+        const double w2 = std::max(dots[j + 1], 0.0);
+        std::vector<double> c(j + 1);
+        double proj = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          H[i][j] += dots[i];
+          c[i] = -dots[i];
+          proj += dots[i] * dots[i];
+        }
+        if ((st = krylov_axpy(p, 0, m + 1, c, p->kr_wp, p->kr_wu)) != PT_OK) return st;
+        const double rest = w2 - proj;  // ||w - sum h_i v_i||^2 in exact arithmetic
+        h = std::sqrt(std::max(rest, 0.0));
+        if (rest > 0.5 * w2) {
+          exact_norm = false;  // no cancellation: the Pythagorean value is accurate
+          break;
+        }
+      }
+      if (exact_norm) {  // two passes and still a large cancellation: measure ||w|| directly
+        launch_scale_pair(p->kr_wp, p->kr_wu, 1.0, p->kr_vp[j + 1], p->kr_vu[j + 1], total, p->st);
+        if ((st = krylov_dots(p, 1, p->kr_wp, p->kr_wu, dots2, j + 1)) != PT_OK) return st;
+        h = std::sqrt(std::max(dots2[0], 0.0));
+      }
+      H[j + 1][j] = h;
+      if (h > 0.0) launch_scale_pair(p->kr_wp, p->kr_wu, 1.0 / h, p->kr_vp[j + 1], p->kr_vu[j + 1], total, p->st);
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
+        H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
+        H[i][j] = t;
+      }
+      const double r = std::hypot(H[j][j], H[j + 1][j]);
+      cs[j] = r > 0.0 ? H[j][j] / r : 1.0;
+      sn[j] = r > 0.0 ? H[j + 1][j] / r : 0.0;
+      H[j][j] = r;
+      H[j + 1][j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++it;
+      const double est = std::fabs(gv[j + 1]) / beta0;
+      hist.push_back(est);
+      if (!(est <= 1e30)) return fail(PT_EDIVERGED, "Krylov residual became non-finite");
+      if (est <= inner_tol || h == 0.0) {
+        ++j;
+        break;
+      }
+    }
+    // x += Z y, H(0:j, 0:j) y = g(0:j)
+    std::vector<double> y(j, 0.0);
+    for (int i = j - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int k = i + 1; k < j; ++k) s -= H[i][k] * y[k];
+      y[i] = H[i][i] != 0.0 ? s / H[i][i] : 0.0;
+    }
+    if (j > 0 && (st = krylov_axpy(p, 2 * m + 2, 3 * m + 2, y, xp, xu)) != PT_OK) return st;
+    if ((st = krylov_true_residual(p, &res_true)) != PT_OK) return st;
+    hist.back() = res_true;  // the solve's own criterion for the iterate it has now
+    if (res_true <= tol) {
+      out = PT_OK;
+      break;
+    }
+    inner_tol = std::min(inner_tol, std::fabs(gv[j]) / beta0) * 0.1;
+  }
+  if (iters_out) *iters_out = it;
+  if (res_hist) {
+    for (size_t k = 0; k < hist.size() && (int)k <= max_it; ++k) res_hist[k] = hist[k];
+  }
+  // record the outcome in the device state (iteration count and status), as the Uzawa path does
+  SolveState hs;
+  if ((st = read_state(p, &hs)) != PT_OK) return st;
+  hs.done = 1;
+  hs.status = out;
+  hs.iters = it;
+  hs.last_res = res_true;
+  PT_CUDA(cudaMemcpyAsync(p->state, &hs, sizeof(SolveState), cudaMemcpyHostToDevice, p->st));
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  if (out == PT_ENOTCONV) g_err = "max_it reached before tol";
+  return out;
+}
+
 // ---- autotuner ------------------------------------------------------------------------
 struct TuneChoice {
   int dstC, coarse_elems;
@@ -725,8 +965,10 @@ pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff
     if (o->spatial_solver == PT_SOLVER_EXACT_1D && grid->dim != 1)
       return fail(PT_EINVAL, "exact spatial solves are available in 1-D only");
     if (o->n_vcycles < 0 || o->n_vcycles > 4) return fail(PT_EINVAL, "n_vcycles must be in [0, 4]");
-    for (int i = 0; i < 2; ++i)
-      if (o->reserved[i] != 0) return fail(PT_EINVAL, "reserved options must be zero");
+    if (o->reserved[0] != 0) return fail(PT_EINVAL, "reserved options must be zero");
+    if (o->krylov < 0 || o->krylov > 64) return fail(PT_EINVAL, "krylov must be in [0, 64]");
+    if (o->krylov > 0 && o->precision != PT_PREC_FP64)
+      return fail(PT_EINVAL, "the Krylov-accelerated solve is FP64 only");
     if (o->h_solver < 0 || o->h_solver > 2) return fail(PT_EINVAL, "h_solver must be 0, 1 or 2");
     if (o->dst_cols != 0 && (o->dst_cols < 0 || o->dst_cols > 16 || !is_pow2(o->dst_cols)))
       return fail(PT_EINVAL, "dst_cols must be 0 or a power of two <= 16");
@@ -1237,7 +1479,7 @@ pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_o
   pt_status st = ensure_hist(p, max_it);
   if (st != PT_OK) return st;
   if (p->opt.autotune && !p->tuned && (st = autotune(p)) != PT_OK) return st;
-  st = uzawa(p, tol, max_it, iters, res_hist);
+  st = p->opt.krylov > 0 ? krylov_solve(p, tol, max_it, iters, res_hist) : uzawa(p, tol, max_it, iters, res_hist);
   if (st != PT_OK && st != PT_ENOTCONV && st != PT_EDIVERGED) return st;
   if (u_out) {
     const Level& L = p->lev[0];

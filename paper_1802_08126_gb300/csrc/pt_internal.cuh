@@ -291,6 +291,17 @@ template <typename T>
 void launch_dsti_scale_table(T* g, const double* lam, const double* mu, double tau, double c0, int dim, int logP,
                              long long S, int B, cudaStream_t st);
 
+// Krylov acceleration (kernels_krylov.cu): pairs (p, u) of padded FP64 space-time vectors.
+void launch_apply_saddle(const double* zp, const double* zu, double* op, double* ou, StencilGeom<double> g,
+                         const double* cth, double tau, int N, cudaStream_t st);
+void launch_multidot(const double* const* vp, const double* const* vu, const double* wp, const double* wu, int nv,
+                     long long total, double* partials, cudaStream_t st);  // partials [nv][kReduceBlocks]
+void launch_multiaxpy(const double* const* vp, const double* const* vu, const double* c, int nv, double* wp,
+                      double* wu, long long total, cudaStream_t st);
+void launch_scale_pair(const double* xp, const double* xu, double s, double* yp, double* yu, long long total,
+                       cudaStream_t st);
+void launch_uzawa_ru(const double* vu, const double* zp, double* ru, long long S, int N, cudaStream_t st);
+
 // Problem hooks for the serving loop (defined in capi.cu).
 pt_status problem_begin(pt_problem* p, double tol, int max_it);   // reset + captured iteration graph
 cudaGraph_t problem_graph(pt_problem* p, unsigned long long* kernels);

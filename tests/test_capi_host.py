@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
-def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0):
+def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, krylov=0, precision=0):
     g = _lib.Grid()
     g.dim = dim
     for d in range(3):
@@ -51,6 +51,8 @@ def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0):
     o.spatial_solver = solver
     o.n_vcycles = nv
     o.reserved[0] = reserved
+    o.krylov = krylov
+    o.precision = precision
     f = np.zeros(N * n ** dim)
     h = ctypes.c_void_p()
     st = lib.pt_problem_create(ctypes.byref(g), N, 1.0, ctypes.byref(k), f.ctypes.data, 0, None, 0,
@@ -59,7 +61,8 @@ def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0):
 
 
 @pytest.mark.parametrize("kw", [dict(n=6), dict(N=3000), dict(N=0), dict(dim=4), dict(c=1.0),
-                                dict(solver=1, dim=2), dict(nv=5), dict(reserved=1)])
+                                dict(solver=1, dim=2), dict(nv=5), dict(reserved=1), dict(krylov=65),
+                                dict(krylov=-1), dict(krylov=10, precision=1)])
 def test_invalid_arguments_rejected_on_host(lib, kw):
     st, h = _create(lib, **kw)
     assert st == _lib.PT_EINVAL

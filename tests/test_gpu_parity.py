@@ -300,3 +300,25 @@ def test_full_grid_heat3d_mixed_global_residual():
         F[0] += u0.ravel()
     Bu = oracle.apply_B(prob.dim, prob.n, prob.N, prob.T, prob.coeff, u)
     assert np.linalg.norm(F - Bu) / np.linalg.norm(F) <= 1e-10 * 1.01
+
+
+@pytest.mark.parametrize("prob", [S.heat2d_uniform(31, 32), S.heat2d_uniform(63, 64), S.heat3d_bumps(15, 16),
+                                  S.heat1d_mms(31, 40)], ids=lambda p: p.name)
+def test_krylov_accelerated_solve_matches_oracle(prob):
+    """Flexible GMRES(20) preconditioned by one Uzawa step (§8.3's acceleration): the same solution
+    as the oracle's implicit Euler, in fewer iterations than the plain Uzawa iteration."""
+    import paper_1802_08126_gb300 as ptu
+    f, u0 = S.source(prob), S.initial(prob)
+    solver = "exact" if prob.dim == 1 else "mg"
+    with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, omega=0.5, solver=solver) as P:
+        _, it_plain, _ = P.solve(1e-12, 1000)
+    with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, omega=0.5, solver=solver,
+                     krylov=20) as P:
+        u = np.zeros((prob.N, prob.ns))
+        stt, it, hist = P.solve(1e-12, 1000, u_out=u)
+    assert stt == 0
+    assert it < it_plain, (it, it_plain)
+    ref = oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0)
+    assert rel_err(u, ref) <= FP64_TOL
+    T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
+    assert abs(T.residual(T.rhs(f, u0), u) - hist[-1]) <= 0.01 * hist[-1] + 1e-15
