@@ -103,6 +103,7 @@ struct pt_problem {
   std::vector<double*> kr_vp, kr_vu, kr_zp, kr_zu;
   double* kr_wp = nullptr;
   double* kr_wu = nullptr;
+  double* kr_zero = nullptr;      // a zero right-hand side (2-D: Sad by the residual kernels)
   double** kr_tab = nullptr;      // device: [vp(m+1) | vu(m+1) | zp(m) | zu(m)]
   double* kr_coef = nullptr;      // device [m + 1]
   double* kr_part = nullptr;      // device [(m + 1) * kReduceBlocks]
@@ -609,6 +610,7 @@ pt_status krylov_alloc(pt_problem* p, int m) {
     p->kr_zu.push_back(b);
   }
   if (!(p->kr_wp = vec()) || !(p->kr_wu = vec())) return st;
+  if (p->bres && !(p->kr_zero = vec())) return st;
   std::vector<double*> tab;
   tab.insert(tab.end(), p->kr_vp.begin(), p->kr_vp.end());
   tab.insert(tab.end(), p->kr_vu.begin(), p->kr_vu.end());
@@ -617,22 +619,23 @@ pt_status krylov_alloc(pt_problem* p, int m) {
   if (!(p->kr_tab = (double**)alloc_bytes(p, sizeof(double*) * tab.size(), &st))) return st;
   PT_CUDA(cudaMemcpyAsync(p->kr_tab, tab.data(), sizeof(double*) * tab.size(), cudaMemcpyHostToDevice, p->st));
   if (!(p->kr_coef = (double*)alloc_bytes(p, sizeof(double) * (m + 1), &st))) return st;
-  if (!(p->kr_part = (double*)alloc_bytes(p, sizeof(double) * (m + 1) * kReduceBlocks, &st))) return st;
+  if (!(p->kr_part = (double*)alloc_bytes(p, sizeof(double) * (m + 2) * kReduceBlocks, &st))) return st;
   p->kr_m = m;
   return PT_OK;
 }
 
-// dots <w, v_k>, first <= k < first + nv (host result, fixed summation order)
+// dots <w, v_k>, first <= k < first + nv, and with self <w, w> last (host result, fixed order)
 pt_status krylov_dots(pt_problem* p, int nv, const double* wp, const double* wu, std::vector<double>& out,
-                      int first = 0) {
+                      int first = 0, int self = 0) {
   const long long total = p->lev[0].S * p->N;
   launch_multidot((const double* const*)(p->kr_tab + first), (const double* const*)(p->kr_tab + p->kr_m + 1 + first),
-                  wp, wu, nv, total, p->kr_part, p->st);
-  std::vector<double> part((size_t)nv * kReduceBlocks);
+                  wp, wu, nv, self, total, p->kr_part, p->st);
+  const int rows = nv + (self ? 1 : 0);
+  std::vector<double> part((size_t)rows * kReduceBlocks);
   PT_CUDA(cudaMemcpyAsync(part.data(), p->kr_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, p->st));
   PT_CUDA(cudaStreamSynchronize(p->st));
-  out.assign(nv, 0.0);
-  for (int k = 0; k < nv; ++k)
+  out.assign(rows, 0.0);
+  for (int k = 0; k < rows; ++k)
     for (int b = 0; b < kReduceBlocks; ++b) out[k] += part[(size_t)k * kReduceBlocks + b];
   return PT_OK;
 }
@@ -661,6 +664,21 @@ pt_status krylov_true_residual(pt_problem* p, double* res) {
   for (double v : part) s += v;
   *res = std::sqrt(s / hs.fnorm2);
   return PT_OK;
+}
+
+// (op, ou) = Sad (zp, zu).  2-D FP64 (stored-residual path): with F = 0 the outer-residual kernel
+// gives bres = -B z_u and op = -bres - tau A (z_p + z_u) = K z_u - tau A z_p, and the second
+// residual kernel sgn (bres - K^T (z_p + z_u)) with sgn = -1 gives ou.
+void krylov_apply(pt_problem* p, const double* zp, const double* zu, double* op, double* ou) {
+  const Level& L0 = p->lev[0];
+  if (p->kr_zero) {
+    launch_resid_bres_2d<double>(zu, zp, p->kr_zero, p->bres, op, p->partials, p->tab_d + L0.tab,
+                                 p->tab_f + L0.tab, p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N,
+                                 nullptr, (const double*)p->jinvA[0], p->st);
+    launch_resid_u_from_bres<double>(p->bres, zu, zp, ou, L0.S, p->N, p->dim, p->n, nullptr, p->st, -1.0);
+  } else {
+    launch_apply_saddle(zp, zu, op, ou, geom<double>(p, 0), p->cth_d, p->tau, p->N, p->st);
+  }
 }
 
 // z = M^-1 v for the pair k of the table
@@ -701,7 +719,7 @@ pt_status krylov_solve(pt_problem* p, double tol, int max_it, int* iters_out, do
   std::vector<double> dots, dots2;
   while (it < max_it) {
     // r = (F, F) - Sad x  -> V_0 = r / beta
-    launch_apply_saddle(xp, xu, p->kr_wp, p->kr_wu, g, p->cth_d, p->tau, p->N, p->st);
+    krylov_apply(p, xp, xu, p->kr_wp, p->kr_wu);
     launch_scale_pair(p->kr_wp, p->kr_wu, -1.0, p->kr_wp, p->kr_wu, total, p->st);
     {
       // add (F, F): F is not in the table, use it as a one-term sum through the work slot of V_m
@@ -709,8 +727,7 @@ pt_status krylov_solve(pt_problem* p, double tol, int max_it, int* iters_out, do
       if ((st = krylov_axpy(p, m, 2 * m + 1, {1.0}, p->kr_wp, p->kr_wu)) != PT_OK) return st;
     }
     // beta = ||r||
-    launch_scale_pair(p->kr_wp, p->kr_wu, 1.0, p->kr_vp[0], p->kr_vu[0], total, p->st);
-    if ((st = krylov_dots(p, 1, p->kr_wp, p->kr_wu, dots)) != PT_OK) return st;
+    if ((st = krylov_dots(p, 0, p->kr_wp, p->kr_wu, dots, 0, 1)) != PT_OK) return st;
     const double beta = std::sqrt(std::max(dots[0], 0.0));
     if (beta0 == 0.0) beta0 = beta > 0.0 ? beta : 1.0;
     if (!(beta > 0.0)) {
@@ -724,15 +741,14 @@ pt_status krylov_solve(pt_problem* p, double tol, int max_it, int* iters_out, do
     int j = 0;
     for (; j < m && it < max_it; ++j) {
       krylov_precondition(p, j);
-      launch_apply_saddle(p->kr_zp[j], p->kr_zu[j], p->kr_wp, p->kr_wu, g, p->cth_d, p->tau, p->N, p->st);
+      krylov_apply(p, p->kr_zp[j], p->kr_zu[j], p->kr_wp, p->kr_wu);
       // classical Gram-Schmidt with selective reorthogonalisation: the copy of w in V_{j+1} gives
       // ||w|| in the same pass; a second pass only when the projection removed more than half of
       // w's norm squared (Kahan-Parlett "twice is enough")
       double h = 0.0;
       bool exact_norm = true;
       for (int pass = 0; pass < 2; ++pass) {
-        launch_scale_pair(p->kr_wp, p->kr_wu, 1.0, p->kr_vp[j + 1], p->kr_vu[j + 1], total, p->st);
-        if ((st = krylov_dots(p, j + 2, p->kr_wp, p->kr_wu, dots)) != PT_OK) return st;
+        if ((st = krylov_dots(p, j + 1, p->kr_wp, p->kr_wu, dots, 0, 1)) != PT_OK) return st;
         const double w2 = std::max(dots[j + 1], 0.0);
         std::vector<double> c(j + 1);
         double proj = 0.0;
@@ -750,8 +766,7 @@ pt_status krylov_solve(pt_problem* p, double tol, int max_it, int* iters_out, do
         }
       }
       if (exact_norm) {  // two passes and still a large cancellation: measure ||w|| directly
-        launch_scale_pair(p->kr_wp, p->kr_wu, 1.0, p->kr_vp[j + 1], p->kr_vu[j + 1], total, p->st);
-        if ((st = krylov_dots(p, 1, p->kr_wp, p->kr_wu, dots2, j + 1)) != PT_OK) return st;
+        if ((st = krylov_dots(p, 0, p->kr_wp, p->kr_wu, dots2, 0, 1)) != PT_OK) return st;
         h = std::sqrt(std::max(dots2[0], 0.0));
       }
       H[j + 1][j] = h;

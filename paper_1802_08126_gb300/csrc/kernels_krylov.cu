@@ -34,28 +34,49 @@ __global__ void k_apply_saddle(const double* __restrict__ zp, const double* __re
   }
 }
 
-// dots[k][block] = partial sums of <w, v_k> over both halves of the pairs, k < nv
-__global__ void k_multidot(const double* const* __restrict__ vp, const double* const* __restrict__ vu,
-                           const double* __restrict__ wp, const double* __restrict__ wu, int nv, long long total,
-                           double* __restrict__ partials) {
-  __shared__ double red[32];
-  for (int k = 0; k < nv; ++k) {
-    const double* a = vp[k];
-    const double* b = vu[k];
-    double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x)
-      acc = fma(a[i], wp[i], fma(b[i], wu[i], acc));
-    acc = warp_sum(acc);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-      v = warp_sum(v);
-      if (threadIdx.x == 0) partials[(long long)k * gridDim.x + blockIdx.x] = v;
-    }
-    __syncthreads();
+// partials[k][block] of <w, v_k> over both halves of the pairs, k < nv, and (self) of <w, w> in
+// row nv.  w is read once per chunk of kChunk vectors (blockIdx.y picks the chunk).  On this GPU
+// the two FP64 multiply-adds per element and vector bound the kernel, not the bytes.
+constexpr int kChunk = 8;
+__global__ void __launch_bounds__(256) k_multidot(const double* const* __restrict__ vp,
+                                                  const double* const* __restrict__ vu,
+                                                  const double* __restrict__ wp, const double* __restrict__ wu,
+                                                  int nv, int self, long long total, double* __restrict__ partials) {
+  __shared__ double red[kChunk + 1][8];
+  const int k0 = blockIdx.y * kChunk;
+  const int nk = min(kChunk, nv - k0);
+  const bool do_self = self && blockIdx.y == 0;
+  double acc[kChunk + 1];
+  const double* pp[kChunk];
+  const double* pu[kChunk];
+#pragma unroll
+  for (int q = 0; q <= kChunk; ++q) acc[q] = 0.0;
+#pragma unroll
+  for (int q = 0; q < kChunk; ++q) {
+    pp[q] = q < nk ? vp[k0 + q] : wp;
+    pu[q] = q < nk ? vu[k0 + q] : wu;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double a = wp[i], b = wu[i];
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q)
+      if (q < nk) acc[q] = fma(pp[q][i], a, fma(pu[q][i], b, acc[q]));
+    if (do_self) acc[kChunk] = fma(a, a, fma(b, b, acc[kChunk]));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q <= kChunk; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) red[q][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x <= kChunk) {
+    const int q = threadIdx.x;
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[q][w];
+    if (q < nk) partials[(long long)(k0 + q) * gridDim.x + blockIdx.x] = v;
+    if (q == kChunk && do_self) partials[(long long)nv * gridDim.x + blockIdx.x] = v;
   }
 }
 
@@ -109,9 +130,10 @@ void launch_apply_saddle(const double* zp, const double* zu, double* op, double*
 }
 
 void launch_multidot(const double* const* vp, const double* const* vu, const double* wp, const double* wu, int nv,
-                     long long total, double* partials, cudaStream_t st) {
+                     int self, long long total, double* partials, cudaStream_t st) {
   LaunchScope ls("krylov_dot", st, 16.0 * (nv + 1) * (double)total);
-  k_multidot<<<kReduceBlocks, kThreads, 0, st>>>(vp, vu, wp, wu, nv, total, partials);
+  const dim3 grid(kReduceBlocks, (unsigned)((nv + kChunk - 1) / kChunk > 0 ? (nv + kChunk - 1) / kChunk : 1));
+  k_multidot<<<grid, 256, 0, st>>>(vp, vu, wp, wu, nv, self, total, partials);
 }
 
 void launch_multiaxpy(const double* const* vp, const double* const* vu, const double* c, int nv, double* wp,

@@ -206,16 +206,16 @@ __global__ void k_resid_bres_mixed(const double* __restrict__ u, const double* _
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Second residual without a stencil: r_u = bres - K^T (p + u)
+// Second residual without a stencil: r_u = sgn (bres - K^T (p + u))
 template <typename Tp>
 __global__ void k_resid_u_from_bres(const double* __restrict__ bres, const double* __restrict__ u,
                                     const double* __restrict__ p, Tp* __restrict__ ru, long long S,
-                                    long long total, const int* done) {
+                                    long long total, const int* done, double sgn) {
   if (stop_requested(done)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const double next = i + S < total ? p[i + S] + u[i + S] : 0.0;
-    ru[i] = (Tp)(bres[i] - (p[i] + u[i]) + next);
+    ru[i] = (Tp)(sgn * (bres[i] - (p[i] + u[i]) + next));
   }
 }
 
@@ -400,15 +400,15 @@ void launch_resid_bres_mixed(const double* u, const double* p, const double* F, 
 
 template <typename Tp>
 void launch_resid_u_from_bres(const double* bres, const double* u, const double* p, Tp* ru, long long S,
-                              int N, int dim, int n, const int* done, cudaStream_t st) {
+                              int N, int dim, int n, const int* done, cudaStream_t st, double sgn) {
   const long long total = S * N;
   LaunchScope ls("resid_u_bres", st, (24.0 + sizeof(Tp)) * dofs(dim, n, N));
-  k_resid_u_from_bres<Tp><<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done);
+  k_resid_u_from_bres<Tp><<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done, sgn);
 }
 template void launch_resid_u_from_bres<float>(const double*, const double*, const double*, float*, long long, int,
-                                              int, int, const int*, cudaStream_t);
+                                              int, int, const int*, cudaStream_t, double);
 template void launch_resid_u_from_bres<double>(const double*, const double*, const double*, double*, long long, int,
-                                               int, int, const int*, cudaStream_t);
+                                               int, int, const int*, cudaStream_t, double);
 
 template <typename T>
 void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale, int N,

@@ -113,7 +113,7 @@ void launch_resid_bres_mixed(const double* u, const double* p, const double* F, 
                              const int* done, cudaStream_t st);
 template <typename Tp>
 void launch_resid_u_from_bres(const double* bres, const double* u, const double* p, Tp* ru, long long S,
-                              int N, int dim, int n, const int* done, cudaStream_t st);
+                              int N, int dim, int n, const int* done, cudaStream_t st, double sgn = 1.0);
 // 2-D (n + 1 >= 32) fused outer residual: bres = F - B u (FP64, stored, norm partials over a fixed
 // grid of kReduceBlocks blocks) and r_p = -bres - tau A (p + u) in precision W (FP32: the w-stencil
 // in FP32; FP64: all in FP64).  tab / tabf: level-0 coefficient tables in FP64 / FP32.
@@ -294,8 +294,9 @@ void launch_dsti_scale_table(T* g, const double* lam, const double* mu, double t
 // Krylov acceleration (kernels_krylov.cu): pairs (p, u) of padded FP64 space-time vectors.
 void launch_apply_saddle(const double* zp, const double* zu, double* op, double* ou, StencilGeom<double> g,
                          const double* cth, double tau, int N, cudaStream_t st);
+// partials [nv (+1 with self: <w, w>)][kReduceBlocks]
 void launch_multidot(const double* const* vp, const double* const* vu, const double* wp, const double* wu, int nv,
-                     long long total, double* partials, cudaStream_t st);  // partials [nv][kReduceBlocks]
+                     int self, long long total, double* partials, cudaStream_t st);
 void launch_multiaxpy(const double* const* vp, const double* const* vu, const double* c, int nv, double* wp,
                       double* wu, long long total, cudaStream_t st);
 void launch_scale_pair(const double* xp, const double* xu, double s, double* yp, double* yu, long long total,
