@@ -206,16 +206,19 @@ __global__ void k_resid_bres_mixed(const double* __restrict__ u, const double* _
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Second residual without a stencil: r_u = sgn (bres - K^T (p + u))
-template <typename Tp>
+// Second residual without a stencil: r_u = bres - K^T (p + u), or its negative (NEG; the Krylov
+// path's saddle operator).  The sign is a template parameter: a run-time factor would cost an
+// FP64 multiply per point.
+template <typename Tp, bool NEG>
 __global__ void k_resid_u_from_bres(const double* __restrict__ bres, const double* __restrict__ u,
                                     const double* __restrict__ p, Tp* __restrict__ ru, long long S,
-                                    long long total, const int* done, double sgn) {
+                                    long long total, const int* done) {
   if (stop_requested(done)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const double next = i + S < total ? p[i + S] + u[i + S] : 0.0;
-    ru[i] = (Tp)(sgn * (bres[i] - (p[i] + u[i]) + next));
+    const double v = NEG ? (p[i] + u[i]) - next - bres[i] : bres[i] - (p[i] + u[i]) + next;
+    ru[i] = (Tp)v;
   }
 }
 
@@ -403,7 +406,10 @@ void launch_resid_u_from_bres(const double* bres, const double* u, const double*
                               int N, int dim, int n, const int* done, cudaStream_t st, double sgn) {
   const long long total = S * N;
   LaunchScope ls("resid_u_bres", st, (24.0 + sizeof(Tp)) * dofs(dim, n, N));
-  k_resid_u_from_bres<Tp><<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done, sgn);
+  if (sgn < 0.0)
+    k_resid_u_from_bres<Tp, true><<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done);
+  else
+    k_resid_u_from_bres<Tp, false><<<grid_for(total), kThreads, 0, st>>>(bres, u, p, ru, S, total, done);
 }
 template void launch_resid_u_from_bres<float>(const double*, const double*, const double*, float*, long long, int,
                                               int, int, const int*, cudaStream_t, double);
