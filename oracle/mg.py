@@ -100,20 +100,21 @@ def st_vcycles(st, h_cycles: int = 2):
     """V-cycle solvers for the Uzawa preconditioners of a ``SpaceTime`` problem.
 
     Returns (Asolve, Hsolve): Asolve applies, slice n, one V-cycle for tau_n A_n
-    (coefficient at t_n); Hsolve(k, r) applies ``h_cycles`` steps of the V-cycle iteration
+    (coefficient at t_n, step length tau_n); Hsolve(k, r) applies ``h_cycles`` steps of the V-cycle iteration
     x <- x + V(r - H_k x) from x = 0 for H_k = mu_k I + tau Abar.
     """
-    from .spacetime import assemble_A, mu
+    from .spacetime import assemble_A, mu, reference_operator
 
     dim, n, N, tau = st.dim, st.n[0], st.N, st.tau
 
     def build_A(m):
-        return [tau * assemble_A(dim, [m] * dim, st.coeff, (i + 1) * tau) for i in range(N)]
+        return [st.taus[i] * assemble_A(dim, [m] * dim, st.coeff, st.times[i]) for i in range(N)]
 
     mus = mu(N)
 
     def build_H(m):
-        Abar = sum(assemble_A(dim, [m] * dim, st.coeff, (i + 1) * tau) for i in range(N)) / N
+        A = [assemble_A(dim, [m] * dim, st.coeff, st.times[i]) for i in range(N)]
+        Abar = reference_operator(A, st.taus, tau, st.uniform)
         I = sp.identity(m ** dim, format="csr")
         return [mus[k] * I + tau * Abar for k in range(N)]
 

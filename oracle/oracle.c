@@ -11,7 +11,8 @@
  *
  *     M (u_n - u_{n-1}) + tau_n A_n u_n = tau_n f_n,   u_0 = u_I,
  *
- * with M = I (finite differences), uniform tau_n = T/N, t_n = n*tau, on the
+ * with M = I (finite differences), time steps tau_n (uniform T/N unless the
+ * caller passes the N step lengths; then t_n = tau_1 + ... + tau_n), on the
  * unit box with n_d interior points per axis, h_d = 1/(n_d+1), homogeneous
  * Dirichlet data, and the conservative finite-difference operator
  *
@@ -234,7 +235,7 @@ static int oc_cg(const oc_grid* g, const oc_coeff* k, double t, double tau, cons
  */
 int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
                       const double* f, const double* u0, double* u, int n_steps, int method,
-                      double cg_tol, int nthreads) {
+                      double cg_tol, int nthreads, const double* steps) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -255,8 +256,14 @@ int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
     if (!work) return -3;
   }
   int rc = 0;
+  double t_acc = 0.0;
   for (int s = 1; s <= n_steps; ++s) {
     double t = s * tau;
+    if (steps) {
+      tau = steps[s - 1];
+      t_acc += tau;
+      t = t_acc;
+    }
     const double* prev = s == 1 ? u0 : u + (size_t)(s - 2) * ns;
     double* cur = u + (size_t)(s - 1) * ns;
     const double* fs = f + (size_t)(s - 1) * ns;
@@ -291,9 +298,10 @@ int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
   return rc;
 }
 
-/* out = B u = (K (x) I) u + diag(tau A_n) u with u_0 := 0 (§2, eq. 2.3-2.4). */
+/* out = B u = (K (x) I) u + diag(tau_n A_n) u with u_0 := 0 (§2, eq. 2.3-2.4); steps as in
+ * oc_implicit_euler. */
 void oc_apply_B(int dim, const int* n, int N, double T, const oc_coeff* k, const double* u,
-                double* out, int nthreads) {
+                double* out, int nthreads, const double* steps) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -303,10 +311,17 @@ void oc_apply_B(int dim, const int* n, int N, double T, const oc_coeff* k, const
   oc_grid_init(&g, dim, n);
   long ns = g.ns;
   double tau = T / N;
+  double t_acc = 0.0;
   for (int s = 1; s <= N; ++s) {
     const double* us = u + (size_t)(s - 1) * ns;
     double* os = out + (size_t)(s - 1) * ns;
-    oc_apply_A_slice(&g, k, s * tau, us, os);
+    double t = s * tau;
+    if (steps) {
+      tau = steps[s - 1];
+      t_acc += tau;
+      t = t_acc;
+    }
+    oc_apply_A_slice(&g, k, t, us, os);
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < ns; ++i) {
       double prev = s > 1 ? us[i - ns] : 0.0;

@@ -125,16 +125,38 @@ def dst_inverse(y: np.ndarray) -> np.ndarray:
     return phi_inv(N) @ y.reshape(N, -1)
 
 
-class SpaceTime:
-    """The FD time-global problem: grid, N uniform steps tau = T/N, t_n = n tau, M = I."""
+def step_times(N: int, T: float, taus=None):
+    """(tau_n, t_n) for n = 1..N: uniform tau = T/N, t_n = n tau, or the given step lengths with
+    t_n = tau_1 + ... + tau_n (§2, before eq. 2.1)."""
+    if taus is None:
+        tau = T / N
+        return np.full(N, tau), np.array([(i + 1) * tau for i in range(N)])
+    taus = np.asarray(taus, dtype=np.float64).reshape(-1)
+    assert taus.size == N and np.all(taus > 0)
+    return taus.copy(), np.cumsum(taus)
 
-    def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff):
+
+def reference_operator(A_list, taus, tau: float, uniform: bool):
+    """Abar with tau Abar = (1/N) sum_n tau_n A_n (eq. 2.2, "an average"); for uniform steps the
+    face-wise mean (1/N) sum_n A_n."""
+    N = len(A_list)
+    if uniform:
+        return sum(A_list) / N
+    return sum(taus[i] * A_list[i] for i in range(N)) / (N * tau)
+
+
+class SpaceTime:
+    """The FD time-global problem: grid, N steps tau_n (uniform T/N unless ``taus`` is given),
+    M = I; the reference step of the preconditioner is tau = T/N."""
+
+    def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff, taus=None):
         self.dim, self.n, self.N, self.T, self.coeff = dim, list(n)[:dim], N, float(T), coeff
         self.tau = self.T / N
+        self.uniform = taus is None
+        self.taus, self.times = step_times(N, self.T, taus)
         self.ns = int(np.prod(self.n))
-        self.A = [assemble_A(dim, self.n, coeff, (i + 1) * self.tau) for i in range(N)]
-        # reference operator: face-wise mean over the N steps (linear in the face values)
-        self.Abar = sum(self.A) / N
+        self.A = [assemble_A(dim, self.n, coeff, self.times[i]) for i in range(N)]
+        self.Abar = reference_operator(self.A, self.taus, self.tau, self.uniform)
 
     # -- time-global operators (vectors are [N][ns]) --
     def K(self, u):
@@ -148,14 +170,14 @@ class SpaceTime:
         return out
 
     def Ablk(self, v):
-        return np.stack([self.tau * (self.A[i] @ v[i]) for i in range(self.N)])
+        return np.stack([self.taus[i] * (self.A[i] @ v[i]) for i in range(self.N)])
 
     def B(self, u):
         return self.K(u) + self.Ablk(u)
 
     def rhs(self, f: np.ndarray, u0: Optional[np.ndarray]) -> np.ndarray:
-        """F = [tau f_1 + M u_I, tau f_2, ..., tau f_N]  (§2, after eq. 2.4)."""
-        F = self.tau * np.asarray(f, dtype=np.float64).reshape(self.N, self.ns).copy()
+        """F = [tau_1 f_1 + M u_I, tau_2 f_2, ..., tau_N f_N]  (§2, after eq. 2.4)."""
+        F = self.taus[:, None] * np.asarray(f, dtype=np.float64).reshape(self.N, self.ns)
         if u0 is not None:
             F[0] += u0
         return F
@@ -165,7 +187,7 @@ class SpaceTime:
 
     # -- exact spatial solvers --
     def exact_A_solver(self) -> Callable:
-        lus = [spla.splu((self.tau * self.A[i]).tocsc()) for i in range(self.N)]
+        lus = [spla.splu((self.taus[i] * self.A[i]).tocsc()) for i in range(self.N)]
 
         def solve(r):
             return np.stack([lus[i].solve(r[i]) for i in range(self.N)])
@@ -256,7 +278,7 @@ def dense_saddle(st: SpaceTime):
     """The saddle-point matrix [[A, -K], [-K^T, -(K + K^T + A)]] of §2, eq. 2.7 (dense)."""
     N, ns = st.N, st.ns
     Kb = np.kron(K_matrix(N), np.eye(ns))
-    Ab = sla.block_diag(*[st.tau * st.A[i].toarray() for i in range(N)])
+    Ab = sla.block_diag(*[st.taus[i] * st.A[i].toarray() for i in range(N)])
     top = np.hstack([Ab, -Kb])
     bot = np.hstack([-Kb.T, -(Kb + Kb.T + Ab)])
     return np.vstack([top, bot])

@@ -82,6 +82,7 @@ class Problem:
     n_bumps: int = 8
     sigma: float = 0.1
     mode: Sequence[int] = (1, 1, 1)
+    taus: Optional[np.ndarray] = None  # step lengths tau_1..tau_N, None: uniform T/N
 
     @property
     def ns(self) -> int:
@@ -104,17 +105,31 @@ def _mesh(dim: int, n: Sequence[int]):
     return grids[::-1]  # x, y, z in that order
 
 
-def mms1_exact(n: int, N: int, T: float) -> np.ndarray:
+def random_steps(N: int, T: float, seed: int, spread: float = 0.5) -> np.ndarray:
+    """Quasi-uniform step lengths tau_n = T w_n / sum(w), w_n = 1 + spread U_n, U_n = draw n-1
+    of SplitMix64(seed): the ratio of any two steps is at most 1 + spread."""
+    w = 1.0 + spread * uniform01(seed, np.arange(N, dtype=np.uint64))
+    return T * w / w.sum()
+
+
+def times(N: int, T: float, taus: Optional[np.ndarray] = None) -> np.ndarray:
+    """t_1..t_N: n T/N, or the partial sums of the given step lengths."""
+    if taus is None:
+        return np.arange(1, N + 1) * (T / N)
+    return np.cumsum(np.asarray(taus, dtype=np.float64))
+
+
+def mms1_exact(n: int, N: int, T: float, taus: Optional[np.ndarray] = None) -> np.ndarray:
     """Manufactured solution u = sin(pi x) exp(-t) at (x_i, t_n), n = 1..N."""
     x = grid_axes(1, [n])[0]
-    t = np.arange(1, N + 1) * (T / N)
+    t = times(N, T, taus)
     return np.exp(-t)[:, None] * np.sin(math.pi * x)[None, :]
 
 
-def mms1_f(n: int, N: int, T: float) -> np.ndarray:
+def mms1_f(n: int, N: int, T: float, taus: Optional[np.ndarray] = None) -> np.ndarray:
     """Source for u = sin(pi x) e^{-t}, a = 1 + 0.5 sin(pi x) cos(2 pi t) in 1-D."""
     x = grid_axes(1, [n])[0][None, :]
-    t = (np.arange(1, N + 1) * (T / N))[:, None]
+    t = times(N, T, taus)[:, None]
     a = 1.0 + 0.5 * np.sin(math.pi * x) * np.cos(2 * math.pi * t)
     ax = 0.5 * math.pi * np.cos(math.pi * x) * np.cos(2 * math.pi * t)
     return np.exp(-t) * (-np.sin(math.pi * x) - math.pi * ax * np.cos(math.pi * x)
@@ -150,7 +165,7 @@ def source(p: Problem, steps: Optional[int] = None) -> np.ndarray:
     if p.f_kind == "uniform":
         return uniform_pm1(p.seed, steps * p.ns).reshape(steps, p.ns)
     if p.f_kind == "mms1":
-        return mms1_f(p.n[0], p.N, p.T)[:steps]
+        return mms1_f(p.n[0], p.N, p.T, p.taus)[:steps]
     if p.f_kind == "bumps":
         b = bumps_field(p.dim, p.n, p.seed, p.n_bumps, p.sigma)
         return np.broadcast_to(b, (steps, p.ns)).copy()
