@@ -636,6 +636,31 @@ def main():
                   "iterations": kits[-1],
                   "rel_l2_vs_uzawa_solution": float(np.linalg.norm(uk - u64) / np.linalg.norm(u64))}
 
+    # the same workload on quasi-uniform random time steps (ratio <= 1.5, §2 eq. 2.1-2.2), FP64
+    nonuniform = None
+    if not args.no_mixed and base_prec == "fp64" and prob.dim == 2:
+        taus = S.random_steps(prob.N, prob.T, 1, 0.5)
+        Pn = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision="fp64", solver=solver,
+                         taus=taus)
+        solve_once(Pn)
+        torch.cuda.synchronize()
+        n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0.record()
+        nits = []
+        for _ in range(args.steps):
+            it, res = solve_once(Pn)
+            nits.append(it)
+        n1.record()
+        torch.cuda.synchronize()
+        nms = max_over_ranks(n0.elapsed_time(n1), dist)
+        Pn.close()
+        nonuniform = {"steps": "tau_n = T w_n / sum w, w_n = 1 + 0.5 U_n (SplitMix64 seed 1), max/min %.3f"
+                               % (taus.max() / taus.min()),
+                      "omega": "default: 1.5 / (1 + alpha), alpha of eq. 2.2 with the step ratios",
+                      "h_solver": "exact, by spatial sine transforms (reference: the time-mean coefficient)",
+                      "value": ws * dofs * args.steps / (nms / 1e3), "unit": "DOF/s",
+                      "ms_per_step": nms / args.steps, "iterations": nits[-1]}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, k, secs, cores, method = cpu_sample(prob, args.cpu_seconds, f[:64])
@@ -659,6 +684,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "ms_per_step_with_kernel_events": ms_prof / args.steps,
             "clocks": clk, ("fp64_path" if variant == "fp64" else "mixed"): mixed, "krylov": krylov,
+            "nonuniform_steps": nonuniform,
             "kernels": phases,
         }
         print(json.dumps(line), flush=True)

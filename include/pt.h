@@ -104,6 +104,13 @@ typedef struct {
   int krylov;            /* 0: the Uzawa iteration of eq. 3.1; m in [1, 64]: flexible GMRES(m)
                             right-preconditioned by one inexact Uzawa step (FP64 only) */
   int reserved[1];       /* must be zero */
+  const double* tau_steps; /* NULL: N_t uniform steps T/N_t.  Else a host array of the N_t step
+                            lengths tau_1..tau_N (§2, eq. 2.1), each finite and > 0, summing to T
+                            within 1e-10 T (else PT_EINVAL); copied at create.  t_n = tau_1 + ... +
+                            tau_n; B = K + diag(tau_n A_n), F_n = tau_n f_n (+ u0 for n = 1).  The
+                            Schur preconditioner keeps the reference pair of eq. 2.2: tau = T/N_t
+                            and Abar, the operator of the coefficient's time mean over (0, T); the
+                            default omega takes alpha of eq. 2.2 with the step ratios tau_n/tau. */
 } pt_options;
 
 typedef struct pt_problem pt_problem; /* opaque, library-owned */
@@ -114,7 +121,7 @@ typedef struct pt_problem pt_problem; /* opaque, library-owned */
  *        f = 0 (see also pt_problem_set_rhs_uniform).
  *   u0 : [n_s] initial datum u_I, or NULL for zero.
  *   opts: may be NULL (all defaults).
- * Forms F = [tau f_1 + u0, tau f_2, ..., tau f_N] on the device (§2, after eq. 2.4),
+ * Forms F = [tau_1 f_1 + u0, tau_2 f_2, ..., tau_N f_N] on the device (§2, after eq. 2.4),
  * allocates all device state, and returns the handle in *out.
  * Errors: PT_EINVAL (bad sizes/options/pointers), PT_ENOMEM, PT_ECUDA. */
 pt_status pt_problem_create(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff,
@@ -210,7 +217,7 @@ const char* pt_status_string(pt_status s);
  * problem's precision, and are what the per-kernel parity tests call.  in and out may not
  * alias.  Errors: PT_EINVAL on NULL pointers, PT_ECUDA. */
 
-/* out = B u = (K (x) I) u + diag(tau A_n) u, u_0 := 0  (§2, eq. 2.3-2.4). */
+/* out = B u = (K (x) I) u + diag(tau_n A_n) u, u_0 := 0  (§2, eq. 2.3-2.4). */
 pt_status pt_apply_B(pt_problem* p, const double* u_dev, double* out_dev);
 
 /* out = Phi^-T r: out_k = sum_n r_n sin((2k-1) n pi / (2N)), k = 1..N (§4, eq. 4.3 transposed). */
@@ -219,7 +226,7 @@ pt_status pt_dst_forward(pt_problem* p, const double* r_dev, double* out_dev);
 /* out = Phi^-1 y: out_n = sum_k y_k sin((2k-1) n pi / (2N)), n = 1..N (§4, eq. 4.3). */
 pt_status pt_dst_inverse(pt_problem* p, const double* y_dev, double* out_dev);
 
-/* out = A~^-1 r: slice n gets the spatial solver of tau A_n (one or more V-cycles, or the exact
+/* out = A~^-1 r: slice n gets the spatial solver of tau_n A_n (one V-cycle, or the exact
  * tridiagonal solve in 1-D) applied to r_n (§3, eq. 3.2). */
 pt_status pt_precond_A(pt_problem* p, const double* r_dev, double* out_dev);
 

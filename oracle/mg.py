@@ -113,8 +113,7 @@ def st_vcycles(st, h_cycles: int = 2):
     mus = mu(N)
 
     def build_H(m):
-        A = [assemble_A(dim, [m] * dim, st.coeff, st.times[i]) for i in range(N)]
-        Abar = reference_operator(A, st.taus, tau, st.uniform)
+        Abar = reference_operator(dim, [m] * dim, st.coeff, st.T)
         I = sp.identity(m ** dim, format="csr")
         return [mus[k] * I + tau * Abar for k in range(N)]
 

@@ -4,8 +4,9 @@ Everything here is written straight from the paper's definitions, at sizes
 where dense or sparse-direct linear algebra finishes in seconds:
 
 * the finite-difference spatial operators A_n (conservative, coefficient at face
-  midpoints, Dirichlet), the reference operator Abar (face-wise mean of the
-  A_n over n = 1..N, one of the choices §2 allows after eq. 2.2),
+  midpoints, Dirichlet) at t_n = tau_1 + ... + tau_n, the reference pair
+  tau = T/N and Abar = the operator of the coefficient's time mean over (0, T)
+  (one of the averages §2 allows after eq. 2.2),
 * the time-global matrices K, B = K (x) M + diag(tau_n A_n) (§2, eq. 2.3-2.4),
   the Schur complement S (eq. 2.5) and the saddle-point matrix (eq. 2.7),
 * the temporal change of basis Phi (type-III DST, §4 eq. 4.2), its inverse
@@ -20,6 +21,7 @@ No blocking, fusion or reordering beyond what those definitions state.
 from __future__ import annotations
 
 import math
+import types
 from typing import Callable, List, Optional, Sequence
 
 import numpy as np
@@ -136,13 +138,24 @@ def step_times(N: int, T: float, taus=None):
     return taus.copy(), np.cumsum(taus)
 
 
-def reference_operator(A_list, taus, tau: float, uniform: bool):
-    """Abar with tau Abar = (1/N) sum_n tau_n A_n (eq. 2.2, "an average"); for uniform steps the
-    face-wise mean (1/N) sum_n A_n."""
-    N = len(A_list)
-    if uniform:
-        return sum(A_list) / N
-    return sum(taus[i] * A_list[i] for i in range(N)) / (N * tau)
+def time_mean_factor(coeff, T: float, pieces: int = 64) -> float:
+    """(1/T) int_0^T g_t(pi m_t t) dt: composite 32-point Gauss-Legendre quadrature."""
+    x, w = np.polynomial.legendre.leggauss(32)
+    edges = np.linspace(0.0, T, pieces + 1)
+    total = 0.0
+    for a, b in zip(edges[:-1], edges[1:]):
+        t = 0.5 * (b - a) * x + 0.5 * (a + b)
+        total += 0.5 * (b - a) * float(np.dot(w, _trig(coeff.ft, math.pi * coeff.mt * t)))
+    return total / T
+
+
+def reference_operator(dim: int, n: Sequence[int], coeff, T: float) -> sp.csr_matrix:
+    """Abar (eq. 2.2, "an average"): the FD operator of the time mean of the coefficient over (0, T),
+    a0 + c gbar prod_d g_d(pi m_d x_d) with gbar = (1/T) int_0^T g_t; it does not depend on the
+    time grid (for uniform steps and a coefficient periodic over (0, T) it is the mean of the A_n)."""
+    gbar = time_mean_factor(coeff, T)
+    mean = types.SimpleNamespace(a0=coeff.a0, c=coeff.c * gbar, fx=coeff.fx, mx=coeff.mx, ft=0, mt=0.0)
+    return assemble_A(dim, n, mean, 0.0)
 
 
 class SpaceTime:
@@ -156,7 +169,7 @@ class SpaceTime:
         self.taus, self.times = step_times(N, self.T, taus)
         self.ns = int(np.prod(self.n))
         self.A = [assemble_A(dim, self.n, coeff, self.times[i]) for i in range(N)]
-        self.Abar = reference_operator(self.A, self.taus, self.tau, self.uniform)
+        self.Abar = reference_operator(dim, self.n, coeff, self.T)
 
     # -- time-global operators (vectors are [N][ns]) --
     def K(self, u):

@@ -68,8 +68,21 @@ def profile_totals() -> dict:
     return out
 
 
-def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=False, h_solver="auto"):
+def _step_array(taus, N: int):
+    """Host FP64 copy of the N step lengths (kept alive by the caller while the C call runs)."""
+    if taus is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(taus, dtype=np.float64).reshape(-1))
+    if a.size != N:
+        raise ValueError("need %d step lengths, got %d" % (N, a.size))
+    return a
+
+
+def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=False, h_solver="auto",
+             steps=None):
     o = _lib.Options()
+    if steps is not None:
+        o.tau_steps = steps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     o.h_solver = {"auto": 0, "vcycle": 1, "exact": 2}[h_solver]
     o.precision = {"fp64": _lib.PT_PREC_FP64, "mixed": _lib.PT_PREC_MIXED}[precision]
     o.omega = float(omega)
@@ -102,7 +115,7 @@ class Server:
         self._h = h
 
     def submit(self, dim, n, N, T, coeff, f=None, seed: int = 0, u0=None, tol: float = 1e-8,
-               max_it: int = 2000, **opts) -> int:
+               max_it: int = 2000, taus=None, **opts) -> int:
         g = _lib.Grid()
         g.dim = dim
         for d in range(3):
@@ -111,7 +124,8 @@ class Server:
         up, udev = _ptr(u0)
         if fdev or udev:
             raise ValueError("server requests take host arrays")
-        o = _options(**opts)
+        steps = _step_array(taus, int(N))
+        o = _options(steps=steps, **opts)
         t = ctypes.c_ulonglong()
         _check(self._lib.pt_server_submit(self._h, ctypes.byref(g), int(N), float(T), ctypes.byref(_coeff(coeff)),
                                           fp, int(seed) & 0xFFFFFFFFFFFFFFFF, up, ctypes.byref(o), float(tol),
@@ -211,13 +225,15 @@ class Problem:
 
     ``coeff`` is any object with attributes a0, c, fx[3], mx[3], ft, mt (see ``pt_coeff``).
     ``f``: [N][n_s] source values, NumPy (host) or torch CUDA tensor (device), float64.
+    ``taus``: the N step lengths tau_1..tau_N (summing to T), or None for uniform steps T/N.
     """
 
     def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff, f, u0=None,
                  precision: str = "fp64", omega: float = 0.0, solver: str = "mg",
                  stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0,
                  autotune: bool = False, dst_cols: int = 0, coarse_elems: int = 0,
-                 graphs: bool = True, n_vcycles: int = 0, h_solver: str = "auto", krylov: int = 0):
+                 graphs: bool = True, n_vcycles: int = 0, h_solver: str = "auto", krylov: int = 0,
+                 taus=None):
         L = _lib.load()
         self._lib = L
         self.dim, self.n, self.N, self.T = dim, list(n)[:dim], N, float(T)
@@ -240,7 +256,11 @@ class Problem:
         opts.no_graphs = 0 if graphs else 1
         opts.h_solver = {"auto": 0, "vcycle": 1, "exact": 2}[h_solver]
         opts.krylov = int(krylov)
+        steps = _step_array(taus, int(N))
+        if steps is not None:
+            opts.tau_steps = steps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self._opts = opts
+        self._steps = steps  # tau_steps points into it
         fp, fdev = _ptr(f)
         up, udev = _ptr(u0)
         h = ctypes.c_void_p()

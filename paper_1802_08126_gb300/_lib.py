@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("jacobi_weight", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("check_every", ctypes.c_int), ("autotune", ctypes.c_int), ("dst_cols", ctypes.c_int),
                 ("coarse_elems", ctypes.c_int), ("no_graphs", ctypes.c_int), ("h_solver", ctypes.c_int),
-                ("krylov", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("krylov", ctypes.c_int), ("reserved", ctypes.c_int * 1),
+                ("tau_steps", ctypes.POINTER(ctypes.c_double))]
 
 
 _lock = threading.Lock()

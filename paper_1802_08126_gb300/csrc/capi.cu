@@ -89,10 +89,14 @@ struct pt_problem {
   double* tab_d = nullptr;
   float* tab_f = nullptr;
   double* cth_d = nullptr;                      // [N] c * g_t(pi m_t t_n)
+  std::vector<double> steps;                    // host copy of tau_1..tau_N (empty: uniform T/N)
+  std::vector<double> tn;                       // t_1..t_N
+  double* stp_d = nullptr;                      // [3N] tau_n | sigma_n = tau_n/tau | rho_n = tau/tau_n
+  float* stp_f = nullptr;                       // the same in FP32
   void* sigA = nullptr;                         // [N] zeros       (precond precision)
   void* cthA = nullptr;                         // [N] c g_t(t_n)
   void* sigH = nullptr;                         // [N] mu_k
-  void* cthH = nullptr;                         // [N] c * mean_n g_t(t_n)
+  void* cthH = nullptr;                         // [N] c * gbar (time mean of g_t over (0, T))
   double cthbar = 0.0;
   void* dst_tw = nullptr;                       // [N/2] complex
   void* dst_pre = nullptr;                      // [N] complex
@@ -226,6 +230,14 @@ MGPlan<T> mg_plan(const pt_problem* p) {
   m.a0 = (T)p->coeff.a0;
   m.B = p->N;
   return m;
+}
+
+// per-step factors tau_n, sigma_n, rho_n (device tables)
+Steps<double> steps_d(const pt_problem* p) {
+  return {p->stp_d, p->stp_d + p->N, p->stp_d + 2 * p->N, p->steps.empty()};
+}
+Steps<float> steps_f(const pt_problem* p) {
+  return {p->stp_f, p->stp_f + p->N, p->stp_f + 2 * p->N, p->steps.empty()};
 }
 
 template <typename T>
@@ -394,25 +406,25 @@ void enqueue_iteration(pt_problem* p) {
     if (p->dim == 3 && L0.P >= 32)
       launch_ir_outer_3d(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, p->tab_d + L0.tab,
                          p->tab_f + L0.tab, p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N,
-                         p->state, p->st);
+                         steps_d(p), p->state, p->st);
     else if (p->dim == 2 && L0.P >= 32)
       launch_ir_outer_2d(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, p->tab_d + L0.tab,
                          p->tab_f + L0.tab, p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N,
-                         p->state, p->st);
+                         steps_d(p), p->state, p->st);
     else
-      launch_ir_outer(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, g, p->cth_d, p->tau, p->N,
-                      p->state, p->st);
+      launch_ir_outer(p->u, p->p, p->F, p->ir_R1, p->ir_R2, (float*)W1, p->partials, g, p->cth_d, steps_d(p),
+                      p->N, p->state, p->st);
     if (p->dim == 3 && L0.P >= 32)
       launch_ir_inner_3d(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials,
                          p->tab_f + L0.tab, (const float*)p->cthA, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S,
-                         p->N, p->state, p->st);
+                         p->N, steps_f(p), p->state, p->st);
     else if (p->dim == 2 && L0.P >= 32)
       launch_ir_inner_2d(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials,
                          p->tab_f + L0.tab, (const float*)p->cthA, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S,
-                         p->N, p->state, p->st);
+                         p->N, steps_f(p), p->state, p->st);
     else
       launch_ir_inner(p->ir_du, p->ir_dp, p->ir_R1, p->ir_R2, p->ir_bp, (float*)W1, p->partials, gf,
-                      (const float*)p->cthA, (float)p->tau, p->N, p->state, p->st);
+                      (const float*)p->cthA, steps_f(p), p->N, p->state, p->st);
     launch_ir_finalize(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->ir_dp, 1, 0, done);
     launch_ir_resid_u(p->ir_bp, p->ir_R2, p->ir_du, p->ir_dp, (float*)W1, L0.S, p->N, p->state, p->st);
@@ -426,22 +438,22 @@ void enqueue_iteration(pt_problem* p) {
     const Level& L0 = p->lev[0];
     launch_resid_bres_2d<T>(p->u, p->p, p->F, p->bres, W1, p->partials, p->tab_d + L0.tab, p->tab_f + L0.tab,
                             p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N, done,
-                            (const double*)p->jinvA[0], p->st);
+                            (const double*)p->jinvA[0], steps_d(p), p->st);
     launch_finalize_residual(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->p, 1, 1, done);
     launch_resid_u_from_bres<T>(p->bres, p->u, p->p, W1, L0.S, p->N, p->dim, p->n, done, p->st);
   } else if (p->mixed) {
     // outer residual in FP64 first (and the convergence test), then the p-update and r_u
-    launch_resid_bres_mixed(p->u, p->p, p->F, p->bres, (float*)W1, p->partials, g, p->cth_d, p->tau, p->N,
+    launch_resid_bres_mixed(p->u, p->p, p->F, p->bres, (float*)W1, p->partials, g, p->cth_d, steps_d(p), p->N,
                             done, p->st);
     launch_finalize_residual(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->p, 1, 1, done);
     launch_resid_u_from_bres<float>(p->bres, p->u, p->p, (float*)W1, p->lev[0].S, p->N, p->dim, p->n, done,
                                     p->st);
   } else {
-    launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, p->tau, p->N, done, p->st);
+    launch_resid_p<T>(p->u, p->p, p->F, W1, g, p->cth_d, steps_d(p), p->N, done, p->st);
     apply_precond_A<T>(p, W1, p->p, 1, 1, done);
-    launch_resid_u<T>(p->u, p->p, p->F, W1, p->partials, g, p->cth_d, p->tau, p->N, done, p->st);
+    launch_resid_u<T>(p->u, p->p, p->F, W1, p->partials, g, p->cth_d, steps_d(p), p->N, done, p->st);
     launch_finalize_residual(p->partials, p->state, p->hist, p->st);
   }
   launch_dst_forward<T>(W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
@@ -654,7 +666,8 @@ pt_status krylov_axpy(pt_problem* p, int first_p, int first_u, const std::vector
 // ||F - B u||^2 / ||F||^2 of the current u (FP64): the r_u kernel's partial sums
 pt_status krylov_true_residual(pt_problem* p, double* res) {
   const StencilGeom<double> g = geom<double>(p, 0);
-  launch_resid_u<double>(p->u, p->p, p->F, (double*)p->W2, p->partials, g, p->cth_d, p->tau, p->N, nullptr, p->st);
+  launch_resid_u<double>(p->u, p->p, p->F, (double*)p->W2, p->partials, g, p->cth_d, steps_d(p), p->N, nullptr,
+                         p->st);
   std::vector<double> part(kReduceBlocks);
   PT_CUDA(cudaMemcpyAsync(part.data(), p->partials, sizeof(double) * kReduceBlocks, cudaMemcpyDeviceToHost, p->st));
   SolveState hs;
@@ -667,17 +680,18 @@ pt_status krylov_true_residual(pt_problem* p, double* res) {
 }
 
 // (op, ou) = Sad (zp, zu).  2-D FP64 (stored-residual path): with F = 0 the outer-residual kernel
-// gives bres = -B z_u and op = -bres - tau A (z_p + z_u) = K z_u - tau A z_p, and the second
-// residual kernel sgn (bres - K^T (z_p + z_u)) with sgn = -1 gives ou.
+// gives bres = -B z_u and op = -bres - tau_n A (z_p + z_u) = K z_u - tau_n A z_p (no rho_n scaling:
+// a null rho), and the second residual kernel sgn (bres - K^T (z_p + z_u)) with sgn = -1 gives ou.
 void krylov_apply(pt_problem* p, const double* zp, const double* zu, double* op, double* ou) {
   const Level& L0 = p->lev[0];
+  const Steps<double> sp = steps_d(p);
   if (p->kr_zero) {
     launch_resid_bres_2d<double>(zu, zp, p->kr_zero, p->bres, op, p->partials, p->tab_d + L0.tab,
                                  p->tab_f + L0.tab, p->cth_d, p->coeff.a0, p->tau, L0.h, p->n, L0.logP, L0.S, p->N,
-                                 nullptr, (const double*)p->jinvA[0], p->st);
+                                 nullptr, (const double*)p->jinvA[0], {sp.tau, sp.sig, nullptr, sp.uniform}, p->st);
     launch_resid_u_from_bres<double>(p->bres, zu, zp, ou, L0.S, p->N, p->dim, p->n, nullptr, p->st, -1.0);
   } else {
-    launch_apply_saddle(zp, zu, op, ou, geom<double>(p, 0), p->cth_d, p->tau, p->N, p->st);
+    launch_apply_saddle(zp, zu, op, ou, geom<double>(p, 0), p->cth_d, sp, p->N, p->st);
   }
 }
 
@@ -690,8 +704,9 @@ void krylov_precondition(pt_problem* p, int k) {
   double* zu = p->kr_zu[k];
   double* a = (double*)p->W2;
   double* W1 = (double*)p->W1;
-  apply_precond_A<double>(p, vp, a, 0, 1, nullptr);          // a = A~^-1 v_p
-  launch_scale_pair(a, a, -1.0, zp, zp, L0.S * p->N, p->st);  // z_p = -a (both halves: same buffers)
+  apply_precond_A<double>(p, vp, a, 0, 1, nullptr);  // a = V-cycles for tau A_n on v_p
+  // z_p = -rho_n a = -A~^-1 v_p for tau_n A_n (both halves: same buffers)
+  launch_scale_pair(a, a, -1.0, zp, zp, L0.S * p->N, p->st, steps_d(p).rho, L0.logP * p->dim);
   launch_uzawa_ru(vu, zp, W1, L0.S, p->N, p->st);             // W1 = v_u - K^T z_p
   const DstPlan<double> dp = dst_plan<double>(p);
   launch_dst_forward<double>(W1, L0.S, p->dim, p->n, L0.logP, dp, nullptr, p->st);
@@ -982,6 +997,15 @@ pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff
     if (o->n_vcycles < 0 || o->n_vcycles > 4) return fail(PT_EINVAL, "n_vcycles must be in [0, 4]");
     if (o->reserved[0] != 0) return fail(PT_EINVAL, "reserved options must be zero");
     if (o->krylov < 0 || o->krylov > 64) return fail(PT_EINVAL, "krylov must be in [0, 64]");
+    if (o->tau_steps) {
+      double sum = 0.0;
+      for (int i = 0; i < N_t; ++i) {
+        const double v = o->tau_steps[i];
+        if (!(v > 0.0) || !std::isfinite(v)) return fail(PT_EINVAL, "time steps must be finite and positive");
+        sum += v;
+      }
+      if (!(std::fabs(sum - T) <= 1e-10 * T)) return fail(PT_EINVAL, "the time steps must sum to T");
+    }
     if (o->krylov > 0 && o->precision != PT_PREC_FP64)
       return fail(PT_EINVAL, "the Krylov-accelerated solve is FP64 only");
     if (o->h_solver < 0 || o->h_solver > 2) return fail(PT_EINVAL, "h_solver must be 0, 1 or 2");
@@ -1028,7 +1052,7 @@ pt_status setup_precision(pt_problem* p) {
   // per-slice operator parameters
   std::vector<double> zeros(p->N, 0.0), cthA(p->N), mu(p->N), cthH(p->N, p->cthbar);
   for (int i = 0; i < p->N; ++i) {
-    cthA[i] = p->coeff.c * trig(p->coeff.ft, M_PI * p->coeff.mt * (i + 1) * p->tau);
+    cthA[i] = p->coeff.c * trig(p->coeff.ft, M_PI * p->coeff.mt * p->tn[i]);
     mu[i] = 2.0 * std::sin((2.0 * (i + 1) - 1.0) * M_PI / (4.0 * p->N));
   }
   const size_t nb = sizeof(T) * p->N;
@@ -1197,12 +1221,13 @@ pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, 
     u0d = (const double*)tu;
   }
   const Level& L = p->lev[0];
+  // F_n = tau_n f_n (+ u0 for n = 1)
   if (seed)
-    launch_pack_uniform(*seed, u0d, p->F, p->tau, p->dim, L.n, L.logP, L.S, p->N, p->st);
+    launch_pack_uniform(*seed, u0d, p->F, 0.0, p->stp_d, p->dim, L.n, L.logP, L.S, p->N, p->st);
   else if (fd)
-    launch_pack(fd, u0d, p->F, p->tau, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
+    launch_pack(fd, u0d, p->F, 0.0, p->stp_d, p->dim, L.n, L.P, L.logP, L.S, p->N, p->st);
   else
-    launch_pack_uniform(0, u0d, p->F, 0.0, p->dim, L.n, L.logP, L.S, p->N, p->st);  // f = 0
+    launch_pack_uniform(0, u0d, p->F, 0.0, nullptr, p->dim, L.n, L.logP, L.S, p->N, p->st);  // f = 0
   PT_CHECK_LAUNCH();
   if (tf) PT_CUDA(cudaFreeAsync(tf, p->st));
   if (tu) PT_CUDA(cudaFreeAsync(tu, p->st));
@@ -1225,15 +1250,31 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   p->tau = T / N_t;
   p->coeff = *coeff;
   if (opts) p->opt = *opts;
+  // time grid: t_n and the per-step factors against the reference step tau = T/N (eq. 2.2)
+  p->tn.resize(N_t);
+  if (p->opt.tau_steps) {
+    p->steps.assign(p->opt.tau_steps, p->opt.tau_steps + N_t);
+    double t = 0.0;
+    for (int i = 0; i < N_t; ++i) p->tn[i] = (t += p->steps[i]);
+  } else {
+    for (int i = 0; i < N_t; ++i) p->tn[i] = (i + 1) * p->tau;
+  }
+  p->opt.tau_steps = nullptr;  // the caller's array need not outlive the call
+  double sig_max = 1.0, rho_max = 1.0;
+  for (double v : p->steps) {
+    sig_max = std::max(sig_max, v / p->tau);
+    rho_max = std::max(rho_max, p->tau / v);
+  }
   p->mixed = p->opt.precision == PT_PREC_MIXED;
   p->nv_h = p->opt.n_vcycles > 0 ? p->opt.n_vcycles : 2;
   p->exact1d = p->opt.spatial_solver == PT_SOLVER_EXACT_1D;
   if (p->opt.omega > 0.0) {
     p->omega = p->opt.omega;
   } else {
-    // alpha of eq. 2.2 for a in [a0 - |c|, a0 + |c|] against the mean coefficient a0
+    // alpha of eq. 2.2 for a in [a0 - |c|, a0 + |c|] against the mean coefficient a0, with the
+    // step ratios: (1/alpha) tau a0 <= tau_n a <= alpha tau a0
     const double a0 = coeff->a0, c = std::fabs(coeff->c);
-    const double alpha = std::max((a0 + c) / a0, a0 / (a0 - c));
+    const double alpha = std::max(sig_max * (a0 + c) / a0, rho_max * a0 / (a0 - c));
     p->omega = 1.5 / (1.0 + alpha);
   }
   p->jacobi = p->opt.jacobi_weight > 0.0 ? p->opt.jacobi_weight
@@ -1276,17 +1317,32 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   if (!(p->tab_f = (float*)alloc_bytes(p, sizeof(float) * tab.size(), &st))) return st;
   if ((st = upload<double>(p, p->tab_d, tab)) != PT_OK) return st;
   if ((st = upload<float>(p, p->tab_f, tab)) != PT_OK) return st;
-  // time factors; reference coefficient = mean over the N steps (face-wise mean of the A_n)
+  // time factors c g_t(t_n); reference coefficient (eq. 2.2, an average): the time mean of a over
+  // (0, T), a0 + c gbar prod g_d with gbar = (1/T) int_0^T g_t(pi m_t t) dt in closed form -- the
+  // same for every time grid (for uniform steps and a coefficient periodic over (0, T), the mean
+  // of the A_n)
   std::vector<double> cth(p->N);
-  double mean = 0.0;
-  for (int i = 0; i < p->N; ++i) {
-    const double g = trig(coeff->ft, M_PI * coeff->mt * (i + 1) * p->tau);
-    cth[i] = coeff->c * g;
-    mean += g;
-  }
-  p->cthbar = coeff->c * (mean / p->N);
+  for (int i = 0; i < p->N; ++i) cth[i] = coeff->c * trig(coeff->ft, M_PI * coeff->mt * p->tn[i]);
+  const double wT = M_PI * coeff->mt * p->T;
+  double gbar = 1.0;
+  if (coeff->ft == PT_TRIG_SIN)
+    gbar = wT == 0.0 ? 0.0 : (1.0 - std::cos(wT)) / wT;
+  else if (coeff->ft == PT_TRIG_COS)
+    gbar = wT == 0.0 ? 1.0 : std::sin(wT) / wT;
+  p->cthbar = coeff->c * gbar;
   if (!(p->cth_d = (double*)alloc_bytes(p, sizeof(double) * p->N, &st))) return st;
   if ((st = upload<double>(p, p->cth_d, cth)) != PT_OK) return st;
+  std::vector<double> stp(3 * (size_t)p->N);
+  for (int i = 0; i < p->N; ++i) {
+    const bool u = p->steps.empty();
+    stp[i] = u ? p->tau : p->steps[i];
+    stp[p->N + i] = u ? 1.0 : p->steps[i] / p->tau;
+    stp[2 * p->N + i] = u ? 1.0 : p->tau / p->steps[i];
+  }
+  if (!(p->stp_d = (double*)alloc_bytes(p, sizeof(double) * stp.size(), &st))) return st;
+  if (!(p->stp_f = (float*)alloc_bytes(p, sizeof(float) * stp.size(), &st))) return st;
+  if ((st = upload<double>(p, p->stp_d, stp)) != PT_OK) return st;
+  if ((st = upload<float>(p, p->stp_f, stp)) != PT_OK) return st;
   // state vectors
   const Level& L0 = p->lev[0];
   if (!(p->u = alloc_padded<double>(p, L0, p->N, &st))) return st;
@@ -1354,6 +1410,11 @@ template <typename T>
 pt_status comp_precond_A(pt_problem* p, const double* r, double* out) {
   pt_status st;
   if ((st = pack_into<T>(p, r, (T*)p->W1)) != PT_OK) return st;
+  if (!p->steps.empty()) {  // A~^-1 for tau_n A_n = rho_n times the solver for tau A_n
+    const Level& L0 = p->lev[0];
+    const T* rho = sizeof(T) == 8 ? (const T*)(const void*)steps_d(p).rho : (const T*)(const void*)steps_f(p).rho;
+    launch_scale_slices<T>((T*)p->W1, rho, L0.logP * p->dim, L0.S * p->N, p->st);
+  }
   apply_precond_A<T>(p, (const T*)p->W1, p->W2, 0, 0, nullptr);
   PT_CHECK_LAUNCH();
   return unpack_from<T>(p, (const T*)p->W2, out);
@@ -1701,7 +1762,7 @@ pt_status pt_apply_B(pt_problem* p, const double* u_dev, double* out_dev) {
   pt_status st = ensure_tmp(p);
   if (st != PT_OK) return st;
   if ((st = pack_into<double>(p, u_dev, p->tmpA)) != PT_OK) return st;
-  launch_apply_B(p->tmpA, p->tmpB, geom<double>(p, 0), p->cth_d, p->tau, p->N, p->st);
+  launch_apply_B(p->tmpA, p->tmpB, geom<double>(p, 0), p->cth_d, steps_d(p), p->N, p->st);
   PT_CHECK_LAUNCH();
   return unpack_from<double>(p, p->tmpB, out_dev);
 }

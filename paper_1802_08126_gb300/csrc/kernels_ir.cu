@@ -14,7 +14,9 @@
 //     b'   = R2 - B du                     (estimate of the outer residual F - B (u + du))
 //     r_p' = K du - tau A dp - R1,         dp += A~^-1 r_p'
 //     r_u' = b' - K^T (dp + du),           du += omega H~^-1 r_u'
-// and the next FP64 step folds them in: u += du, p += dp.  The FP64 step comes every kOuter
+// and the next FP64 step folds them in: u += du, p += dp.  With non-uniform steps tau A stands for
+// diag(tau_n A_n) and the A~ inputs are scaled by rho_n = tau / tau_n (the V-cycles are formed for
+// the reference step tau).  The FP64 step comes every kOuter
 // iterations, and at once when the FP32 estimate ||b'|| reaches the tolerance or the iteration
 // limit: the solve only ends on an FP64 residual of the FP64 iterate it returns.
 //
@@ -49,28 +51,31 @@ __global__ void k_ir_fold(double* __restrict__ u, double* __restrict__ p, float*
 }
 
 // FP64 step, part 2: bres = F - B u (FP64, norm partials), w = p + u; R1, R2 in FP32 and the
-// first r_p' = -R1 into rp.  tau A w in FP32 (w -> 0 at the solution, it only enters the
+// first A~ input rho_t r_p' = -rho_t R1 into rp.  tau A w in FP32 (w -> 0 at the solution, it only enters the
 // FP32 right-hand sides).
 template <int DIM>
 __global__ void k_ir_outer(const double* __restrict__ u, const double* __restrict__ p,
                            const double* __restrict__ F, float* __restrict__ R1, float* __restrict__ R2,
                            float* __restrict__ rp, double* __restrict__ partials, StencilGeom<double> g,
-                           const double* __restrict__ cth, double tau, int N, long long total,
+                           const double* __restrict__ cth, Steps<double> sp, int N, long long total,
                            const SolveState* st) {
   if (vload(&st->done) != 0 || !vload(&st->outer)) return;
   double acc = 0.0;
-  const float tauf = (float)tau, h2f = (float)g.h2inv;
+  const float h2f = (float)g.h2inv;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     long long t;
     int x, y, z;
-    float r1 = 0.f, r2 = 0.f;
+    float r1 = 0.f, r2 = 0.f, rho = 1.f;
     if (decode<DIM>(i, g.logP, g.n, t, x, y, z)) {
       double am[3], ap[3];
       face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
       const double uc = u[i];
       const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
       const double um = t > 0 ? u[i - g.S] : 0.0;
+      const double tau = sp.tau[t];
+      const float tauf = (float)tau;
+      rho = (float)sp.rho[t];
       const double b = F[i] - (uc - um) - tau * Au;
       acc += b * b;
       const double wc = p[i] + uc;
@@ -88,21 +93,20 @@ __global__ void k_ir_outer(const double* __restrict__ u, const double* __restric
     }
     R1[i] = r1;
     R2[i] = r2;
-    rp[i] = -r1;
+    rp[i] = -(rho * r1);
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// FP32 step: b' = R2 - B du (norm partials in FP64), r_p' = K du - tau A dp - R1
+// FP32 step: b' = R2 - B du (norm partials in FP64), A~ input rho_t r_p', r_p' = K du - tau_t A dp - R1
 template <int DIM>
 __global__ void k_ir_inner(const float* __restrict__ du, const float* __restrict__ dp,
                            const float* __restrict__ R1, const float* __restrict__ R2, float* __restrict__ bp,
                            float* __restrict__ rp, double* __restrict__ partials, StencilGeom<float> g,
-                           const float* __restrict__ cth, float tau, long long total, const SolveState* st) {
+                           const float* __restrict__ cth, Steps<float> sp, long long total, const SolveState* st) {
   if (vload(&st->done) != 0 || vload(&st->outer)) return;
   float acc = 0.f;  // per-thread sum in FP32 (an estimate), block sum in FP64
-  const float sc = tau * g.h2inv;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     long long t;
@@ -116,8 +120,9 @@ __global__ void k_ir_inner(const float* __restrict__ du, const float* __restrict
       const float Ad = stencil_sum<DIM, float>(du, i, dc, am, ap, g.P);
       const float pc = dp[i];
       const float Ap = stencil_sum<DIM, float>(dp, i, pc, am, ap, g.P);
+      const float sc = sp.tau[t] * g.h2inv;
       b = R2[i] - Kd - sc * Ad;
-      r = Kd - sc * Ap - R1[i];
+      r = (Kd - sc * Ap - R1[i]) * sp.rho[t];
       acc = fmaf(b, b, acc);
     }
     bp[i] = b;
@@ -203,20 +208,20 @@ void launch_ir_fold(double* u, double* p, float* du, float* dp, long long total,
 }
 
 void launch_ir_outer(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
-                     double* partials, StencilGeom<double> g, const double* cth, double tau, int N,
+                     double* partials, StencilGeom<double> g, const double* cth, Steps<double> sp, int N,
                      const SolveState* st, cudaStream_t s) {
   const long long total = g.S * N;
   LaunchScope ls("ir_outer", s, (24.0 + 12.0) * (double)total);
-  PT_IR_DIM(g.dim, k_ir_outer<D><<<kReduceBlocks, kThreads, 0, s>>>(u, p, F, R1, R2, rp, partials, g, cth, tau, N,
+  PT_IR_DIM(g.dim, k_ir_outer<D><<<kReduceBlocks, kThreads, 0, s>>>(u, p, F, R1, R2, rp, partials, g, cth, sp, N,
                                                                     total, st));
 }
 
 void launch_ir_inner(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
-                     double* partials, StencilGeom<float> g, const float* cth, float tau, int N,
+                     double* partials, StencilGeom<float> g, const float* cth, Steps<float> sp, int N,
                      const SolveState* st, cudaStream_t s) {
   const long long total = g.S * N;
   LaunchScope ls("ir_inner", s, 24.0 * (double)total);
-  PT_IR_DIM(g.dim, k_ir_inner<D><<<kReduceBlocks, kThreads, 0, s>>>(du, dp, R1, R2, bp, rp, partials, g, cth, tau,
+  PT_IR_DIM(g.dim, k_ir_inner<D><<<kReduceBlocks, kThreads, 0, s>>>(du, dp, R1, R2, bp, rp, partials, g, cth, sp,
                                                                     total, st));
 }
 

@@ -2,7 +2,8 @@
 // one inexact Uzawa step; the Krylov acceleration the paper applies in its 3-D experiments, §8.3).
 // Every vector is a pair (p, u) of padded FP64 space-time vectors; the saddle-point operator of
 // eq. 2.7 in the form the Uzawa iteration solves is
-//     Sad (p, u) = ( -tau A p + K u ,  K^T p + (K^T + B) u ),   B = K + tau A.
+//     Sad (p, u) = ( -tau A p + K u ,  K^T p + (K^T + B) u ),   B = K + tau A,
+// with tau A = diag(tau_n A_n).
 #include "stencil_common.cuh"
 
 namespace pt {
@@ -11,7 +12,7 @@ namespace {
 template <int DIM>
 __global__ void k_apply_saddle(const double* __restrict__ zp, const double* __restrict__ zu,
                                double* __restrict__ op, double* __restrict__ ou, StencilGeom<double> g,
-                               const double* __restrict__ cth, double tau, int N, long long total) {
+                               const double* __restrict__ cth, Steps<double> sp, int N, long long total) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     long long t;
@@ -21,6 +22,7 @@ __global__ void k_apply_saddle(const double* __restrict__ zp, const double* __re
       double am[3], ap[3];
       face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
       const double pc = zp[i], uc = zu[i];
+      const double tau = sp.tau[t];
       const double Ap = tau * g.h2inv * stencil_sum<DIM, double>(zp, i, pc, am, ap, g.P);
       const double Au = tau * g.h2inv * stencil_sum<DIM, double>(zu, i, uc, am, ap, g.P);
       const double Ku = uc - (t > 0 ? zu[i - g.S] : 0.0);
@@ -96,13 +98,15 @@ __global__ void k_multiaxpy(const double* const* __restrict__ vp, const double* 
   }
 }
 
-// (yp, yu) = s (xp, xu)
+// (yp, yu) = s (xp, xu), times rho[i >> logS] when rho is not null
 __global__ void k_scale_pair(const double* __restrict__ xp, const double* __restrict__ xu, double s,
-                             double* __restrict__ yp, double* __restrict__ yu, long long total) {
+                             double* __restrict__ yp, double* __restrict__ yu, long long total,
+                             const double* __restrict__ rho, int logS) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    yp[i] = s * xp[i];
-    yu[i] = s * xu[i];
+    const double f = rho ? s * rho[i >> logS] : s;
+    yp[i] = f * xp[i];
+    yu[i] = f * xu[i];
   }
 }
 
@@ -119,13 +123,13 @@ __global__ void k_uzawa_ru(const double* __restrict__ vu, const double* __restri
 }  // namespace
 
 void launch_apply_saddle(const double* zp, const double* zu, double* op, double* ou, StencilGeom<double> g,
-                         const double* cth, double tau, int N, cudaStream_t st) {
+                         const double* cth, Steps<double> sp, int N, cudaStream_t st) {
   const long long total = g.S * N;
   LaunchScope ls("krylov_apply", st, 48.0 * (double)total);
   switch (g.dim) {
-    case 1: k_apply_saddle<1><<<grid_for(total), kThreads, 0, st>>>(zp, zu, op, ou, g, cth, tau, N, total); break;
-    case 2: k_apply_saddle<2><<<grid_for(total), kThreads, 0, st>>>(zp, zu, op, ou, g, cth, tau, N, total); break;
-    default: k_apply_saddle<3><<<grid_for(total), kThreads, 0, st>>>(zp, zu, op, ou, g, cth, tau, N, total); break;
+    case 1: k_apply_saddle<1><<<grid_for(total), kThreads, 0, st>>>(zp, zu, op, ou, g, cth, sp, N, total); break;
+    case 2: k_apply_saddle<2><<<grid_for(total), kThreads, 0, st>>>(zp, zu, op, ou, g, cth, sp, N, total); break;
+    default: k_apply_saddle<3><<<grid_for(total), kThreads, 0, st>>>(zp, zu, op, ou, g, cth, sp, N, total); break;
   }
 }
 
@@ -143,9 +147,9 @@ void launch_multiaxpy(const double* const* vp, const double* const* vu, const do
 }
 
 void launch_scale_pair(const double* xp, const double* xu, double s, double* yp, double* yu, long long total,
-                       cudaStream_t st) {
+                       cudaStream_t st, const double* rho, int logS) {
   LaunchScope ls("krylov_scale", st, 32.0 * (double)total);
-  k_scale_pair<<<grid_for(total), kThreads, 0, st>>>(xp, xu, s, yp, yu, total);
+  k_scale_pair<<<grid_for(total), kThreads, 0, st>>>(xp, xu, s, yp, yu, total, rho, logS);
 }
 
 void launch_uzawa_ru(const double* vu, const double* zp, double* ru, long long S, int N, cudaStream_t st) {

@@ -2,15 +2,19 @@
 // its FP32 rate, so these kernels are bound by FP64 instruction issue, not by memory).
 //
 // One pass forms, for every interior point of every step t,
-//   bres = F - (u_t - u_{t-1}) - tau A_t u_t          (outer residual F - B u, FP64, stored)
-//   r_p  = -bres - tau A_t (p_t + u_t)                 (= K u - tau A_t p - F, first line of eq. 3.1)
+//   bres = F - (u_t - u_{t-1}) - tau_t A_t u_t        (outer residual F - B u, FP64, stored)
+//   r_p  = -bres - tau_t A_t (p_t + u_t)               (= K u - tau_t A_t p - F, first line of eq. 3.1)
 // and the squared norm of bres; the second residual r_u = bres - K^T (p + u) is then a
 // stencil-free pass.  w = p + u tends to zero, so its stencil is taken in FP32 in the mixed-
 // precision form (the A~ input is rounded to FP32 anyway) and in FP64 in the plain form.
 //
 // Each warp sweeps a strip of kRows rows for 32 consecutive columns: the rows above and below
 // stay in registers, x-neighbours of w come from warp shuffles, and the face coefficients
-// (tau/h^2)(a0 + c g_t(t) g_x g_y) are one FMA each from per-row / per-column factors.
+// (tau/h^2)(a0 + c g_t(t) g_x g_y) are one FMA each from per-row / per-column factors.  They are
+// formed for the reference step tau (the operator of the V-cycles); the step's own tau_t enters as
+// sigma_t = tau_t / tau in the multiply-add that subtracts the stencil from the residual, and the A~
+// input is written as rho_t r_p (rho_t = tau / tau_t), which is -rho_t bres - (tau A_t)(p + u): no
+// FP64 operation more than for uniform steps.
 #include "stencil_common.cuh"
 
 namespace pt {
@@ -19,17 +23,21 @@ namespace {
 constexpr int kRows = 16;
 
 // IR = true: the FP64 step of the mixed-precision refinement -- instead of bres and r_p it writes
-// the FP32 right-hand sides R1 = bres + tau A w, R2 = bres - K^T w and r_p' = -R1, and runs only
-// on refinement iterations (state flags).
+// the FP32 right-hand sides R1 = bres + tau_t A w, R2 = bres - K^T w and rho_t r_p' = -rho_t R1, and
+// runs only on refinement iterations (state flags).
 // DG = true (FP64 path): the cached pairs (w/D, D) of tau A_n give the diagonal, and both
 // stencils are D x_c - sum_f a_f x_f (six fewer FP64 operations per point).
-template <typename W, bool IR, bool DG = false>
-__global__ void __launch_bounds__(256) k_resid_bres_2d(
+// SC: 0 uniform steps (sigma = rho = 1, no factors), 1 sigma_t and rho_t, 2 sigma_t only and r_p
+// itself (not with IR: the Krylov path's operator).  The FP64 form with both factors is held to 64
+// registers (4 CTAs per SM, no spills), as the uniform one is.
+template <typename W, bool IR, bool DG = false, int SC = 0>
+__global__ void __launch_bounds__(256, (SC == 1 && DG && sizeof(W) == 8) ? 4 : 1) k_resid_bres_2d(
     const double* __restrict__ u, const double* __restrict__ p, const double* __restrict__ F,
     double* __restrict__ bres, W* __restrict__ rp, double* __restrict__ partials,
     const double* __restrict__ tab, const float* __restrict__ tabf, const double* __restrict__ cth,
     double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, const int* done,
-    float* __restrict__ R1, float* __restrict__ R2, const SolveState* st, const double* __restrict__ jd = nullptr) {
+    float* __restrict__ R1, float* __restrict__ R2, const SolveState* st, Steps<double> sp,
+    const double* __restrict__ jd = nullptr) {
   if (IR) {
     if (*((volatile const int*)&st->done) != 0 || !*((volatile const int*)&st->outer)) return;
   } else if (stop_requested(done)) {
@@ -53,6 +61,9 @@ __global__ void __launch_bounds__(256) k_resid_bres_2d(
     const double* ny = tab + 2 * P;
     const double* fy = tab + 3 * P;
     const double ct = s_h2 * cth[t];  // (tau/h^2) c g_t(t_t)
+    double sg = 1.0, rh = 1.0;
+    if constexpr (SC >= 1) sg = sp.sig[t];
+    if constexpr (SC == 1) rh = sp.rho[t];
     const float a0f = (float)a0s, ctf = (float)ct;
     const float* nxf = tabf;
     const float* fxf = tabf + P;
@@ -100,7 +111,10 @@ __global__ void __launch_bounds__(256) k_resid_bres_2d(
         if constexpr (DG) D = ((const double2*)jd)[i].y;
         const double su = DG ? D * u_c - (axl * uW + axr * uE + ayl * u_m + ayu * u_p)
                              : axl * (u_c - uW) + axr * (u_c - uE) + ayl * (u_c - u_m) + ayu * (u_c - u_p);
-        b = F[i] - (u_c - um) - su;
+        if constexpr (SC == 0)
+          b = F[i] - (u_c - um) - su;
+        else
+          b = fma(-sg, su, F[i] - (u_c - um));
         acc = fma(b, b, acc);
         W sw;
         if (sizeof(W) == 4) {
@@ -118,17 +132,33 @@ __global__ void __launch_bounds__(256) k_resid_bres_2d(
           const long long in = i + S;
           const double wn = t + 1 < N ? p[in] + u[in] : 0.0;
           const double wc = p[i] + u_c;
-          r1 = (float)b + (float)sw;
+          if constexpr (SC == 0)
+            r1 = (float)b + (float)sw;
+          else
+            r1 = fmaf((float)sg, (float)sw, (float)b);
           r2 = (float)(b - (wc - wn));
-        } else {
+        } else if constexpr (SC == 0) {
           r = (W)(-b) - sw;
+        } else if constexpr (SC == 1) {  // rho_t r_p = -rho_t b - sw
+          if constexpr (sizeof(W) == 8)
+            r = (W)fma(-rh, b, -(double)sw);
+          else
+            r = (W)(-(rh * b)) - sw;
+        } else {  // r_p = -b - sigma_t sw
+          if constexpr (sizeof(W) == 8)
+            r = (W)fma(-sg, (double)sw, -b);
+          else
+            r = (W)(-b) - (W)(sg * (double)sw);
         }
       }
       if (y < P) {
         if (IR) {
           R1[at(y)] = r1;
           R2[at(y)] = r2;
-          rp[at(y)] = (W)(-r1);
+          if constexpr (SC == 0)
+            rp[at(y)] = (W)(-r1);
+          else
+            rp[at(y)] = (W)(-((float)rh * r1));
         } else {
           bres[at(y)] = b;
           rp[at(y)] = r;
@@ -152,45 +182,60 @@ template <typename W>
 void launch_resid_bres_2d(const double* u, const double* p, const double* F, double* bres, W* rp,
                           double* partials, const double* tab, const float* tabf, const double* cth, double a0,
                           double tau, double h, int n, int logP, long long S, int N, const int* done,
-                          const double* jd, cudaStream_t st) {
+                          const double* jd, Steps<double> sp, cudaStream_t st) {
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("resid_bres", st, (24.0 + 8.0 + sizeof(W)) * (double)n * n * N);
-  if (sizeof(W) == 8 && jd)
-    k_resid_bres_2d<W, false, true><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth,
-                                                                    s_h2 * a0, s_h2, n, logP, S, N, nwarps, done,
-                                                                    nullptr, nullptr, nullptr, jd);
-  else
-    k_resid_bres_2d<W, false><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth, s_h2 * a0,
-                                                                s_h2, n, logP, S, N, nwarps, done, nullptr, nullptr,
-                                                                nullptr);
+  const int sc = sp.uniform ? 0 : (sp.rho ? 1 : 2);
+#define PT_RESID_BRES(DGV, SCV)                                                                                   \
+  k_resid_bres_2d<W, false, DGV, SCV><<<kReduceBlocks, 256, 0, st>>>(u, p, F, bres, rp, partials, tab, tabf, cth, \
+                                                                     s_h2 * a0, s_h2, n, logP, S, N, nwarps,    \
+                                                                     done, nullptr, nullptr, nullptr, sp, jd)
+  if (sizeof(W) == 8 && jd) {
+    if (sc == 0) PT_RESID_BRES(true, 0);
+    else if (sc == 1) PT_RESID_BRES(true, 1);
+    else PT_RESID_BRES(true, 2);
+  } else {
+    if (sc == 0) PT_RESID_BRES(false, 0);
+    else if (sc == 1) PT_RESID_BRES(false, 1);
+    else PT_RESID_BRES(false, 2);
+  }
+#undef PT_RESID_BRES
 }
 
 void launch_ir_outer_2d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
                         double* partials, const double* tab, const float* tabf, const double* cth, double a0,
-                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
-                        cudaStream_t s) {
+                        double tau, double h, int n, int logP, long long S, int N, Steps<double> sp,
+                        const SolveState* st, cudaStream_t s) {
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("ir_outer", s, (24.0 + 12.0) * (double)n * n * N);
-  k_resid_bres_2d<float, true><<<kReduceBlocks, 256, 0, s>>>(u, p, F, nullptr, rp, partials, tab, tabf, cth,
-                                                               s_h2 * a0, s_h2, n, logP, S, N, nwarps, nullptr, R1,
-                                                               R2, st);
+  if (sp.uniform)
+    k_resid_bres_2d<float, true, false, 0><<<kReduceBlocks, 256, 0, s>>>(u, p, F, nullptr, rp, partials, tab, tabf,
+                                                                         cth, s_h2 * a0, s_h2, n, logP, S, N, nwarps,
+                                                                         nullptr, R1, R2, st, sp);
+  else
+    k_resid_bres_2d<float, true, false, 1><<<kReduceBlocks, 256, 0, s>>>(u, p, F, nullptr, rp, partials, tab, tabf,
+                                                                         cth, s_h2 * a0, s_h2, n, logP, S, N, nwarps,
+                                                                         nullptr, R1, R2, st, sp);
 }
 
 template void launch_resid_bres_2d<float>(const double*, const double*, const double*, double*, float*, double*,
                                           const double*, const float*, const double*, double, double, double, int,
-                                          int, long long, int, const int*, const double*, cudaStream_t);
+                                          int, long long, int, const int*, const double*, Steps<double>,
+                                          cudaStream_t);
 template void launch_resid_bres_2d<double>(const double*, const double*, const double*, double*, double*, double*,
                                            const double*, const float*, const double*, double, double, double, int,
-                                           int, long long, int, const int*, const double*, cudaStream_t);
+                                           int, long long, int, const int*, const double*, Steps<double>,
+                                           cudaStream_t);
 
 }  // namespace pt
 
 // ---- FP32 inner step of the mixed-precision refinement, 2-D (n + 1 >= 32) ----
-//   b'   = R2 - K du - tau A du,    r_p' = K du - tau A dp - R1,    partials of ||b'||^2
+//   b'   = R2 - K du - tau_t A du,    rho_t r_p',  r_p' = K du - tau_t A dp - R1,    partials of ||b'||^2
+// (stencils for the reference step tau, times sigma_t = tau_t / tau)
 // with the same warp-strip sweep; the per-thread norm is accumulated in FP32 (it only decides
 // when the FP64 step is due) and summed in FP64 across the block.
 namespace pt {
@@ -200,7 +245,7 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
     const float* __restrict__ du, const float* __restrict__ dp, const float* __restrict__ R1,
     const float* __restrict__ R2, float* __restrict__ bp, float* __restrict__ rp, double* __restrict__ partials,
     const float* __restrict__ tabf, const float* __restrict__ cthf, float a0s, float s_h2, int n, int logP,
-    long long S, long long nwarps, const SolveState* st) {
+    long long S, long long nwarps, Steps<float> sp, const SolveState* st) {
   if (*((volatile const int*)&st->done) != 0 || *((volatile const int*)&st->outer) != 0) return;
   const int P = 1 << logP;
   const int lane = threadIdx.x & 31;
@@ -219,6 +264,7 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
     const float* ny = tabf + 2 * P;
     const float* fy = tabf + 3 * P;
     const float ct = s_h2 * cthf[t];
+    const float sg = sp.sig[t], rh = sp.rho[t];
     const bool xin = x < n;
     const float fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
     const float gxc = ct * nx[x];
@@ -275,8 +321,8 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
         const float Kd = d_c - dtm;
         const float sd = axl * (d_c - dW) + axr * (d_c - dE) + ayl * (d_c - d_m) + ayu * (d_c - d_p);
         const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - q_m) + ayu * (q_c - q_p);
-        b = r2 - Kd - sd;
-        r = Kd - sq - r1;
+        b = fmaf(-sg, sd, r2 - Kd);
+        r = (fmaf(-sg, sq, Kd) - r1) * rh;
         acc = fmaf(b, b, acc);
       }
       if (y < P) {
@@ -298,13 +344,13 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
 
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s) {
+                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s) {
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * N);
   k_ir_inner_2d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
-                                              (float)s_h2, n, logP, S, nwarps, st);
+                                              (float)s_h2, n, logP, S, nwarps, sp, st);
 }
 
 }  // namespace pt
@@ -331,12 +377,12 @@ __device__ __forceinline__ Sweep3 sweep3_decode(long long wg, int P) {
   return s;
 }
 
-// FP32 inner step: b' = R2 - K du - tau A du, r_p' = K du - tau A dp - R1
+// FP32 inner step: b' = R2 - K du - tau_t A du, rho_t r_p', r_p' = K du - tau_t A dp - R1
 __global__ void __launch_bounds__(256) k_ir_inner_3d(
     const float* __restrict__ du, const float* __restrict__ dp, const float* __restrict__ R1,
     const float* __restrict__ R2, float* __restrict__ bp, float* __restrict__ rp, double* __restrict__ partials,
     const float* __restrict__ tabf, const float* __restrict__ cthf, float a0s, float s_h2, int n, int logP,
-    long long S, long long nwarps, const SolveState* st) {
+    long long S, long long nwarps, Steps<float> sp, const SolveState* st) {
   if (*((volatile const int*)&st->done) != 0 || *((volatile const int*)&st->outer) != 0) return;
   const int P = 1 << logP;
   const long long P2 = (long long)P * P;
@@ -354,6 +400,7 @@ __global__ void __launch_bounds__(256) k_ir_inner_3d(
     const int x = (w.wx << 5) + lane;
     const bool xyin = x < n && w.y < n;
     const float ct = s_h2 * cthf[w.t];
+    const float sg = sp.sig[w.t], rh = sp.rho[w.t];
     const float gx = nx[x], gy = ny[w.y];
     const float fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
     const float fyl = fy[w.y], fyu = fy[w.y + 1 < P ? w.y + 1 : w.y];
@@ -395,8 +442,8 @@ __global__ void __launch_bounds__(256) k_ir_inner_3d(
                          azl * (d_c - d_m) + azu * (d_c - d_p);
         const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - qS) + ayu * (q_c - qN) +
                          azl * (q_c - q_m) + azu * (q_c - q_p);
-        b = R2[i] - Kd - sd;
-        r = Kd - sq - R1[i];
+        b = fmaf(-sg, sd, R2[i] - Kd);
+        r = (fmaf(-sg, sq, Kd) - R1[i]) * rh;
         acc = fmaf(b, b, acc);
       }
       if (z < P) {
@@ -414,13 +461,14 @@ __global__ void __launch_bounds__(256) k_ir_inner_3d(
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// FP64 step: bres = F - K u - tau A u (FP64, norm), w = p + u; R1 = bres + tau A w (w-stencil in
-// FP32), R2 = bres - K^T w, r_p' = -R1
+// FP64 step: bres = F - K u - tau_t A u (FP64, norm), w = p + u; R1 = bres + tau_t A w (w-stencil in
+// FP32), R2 = bres - K^T w, A~ input -rho_t R1
 __global__ void __launch_bounds__(256) k_ir_outer_3d(
     const double* __restrict__ u, const double* __restrict__ p, const double* __restrict__ F,
     float* __restrict__ R1, float* __restrict__ R2, float* __restrict__ rp, double* __restrict__ partials,
     const double* __restrict__ tab, const float* __restrict__ tabf, const double* __restrict__ cth,
-    double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, const SolveState* st) {
+    double a0s, double s_h2, int n, int logP, long long S, int N, long long nwarps, Steps<double> sp,
+    const SolveState* st) {
   if (*((volatile const int*)&st->done) != 0 || !*((volatile const int*)&st->outer)) return;
   const int P = 1 << logP;
   const long long P2 = (long long)P * P;
@@ -443,6 +491,8 @@ __global__ void __launch_bounds__(256) k_ir_outer_3d(
     const int x = (w.wx << 5) + lane;
     const bool xyin = x < n && w.y < n;
     const double ct = s_h2 * cth[w.t];
+    const double sg = sp.sig[w.t];
+    const float sgf = (float)sg, rhf = (float)sp.rho[w.t];
     const float ctf = (float)ct;
     const double gx = nx[x], gy = ny[w.y];
     const int xr = x + 1 < P ? x + 1 : x, yu = w.y + 1 < P ? w.y + 1 : w.y;
@@ -489,7 +539,7 @@ __global__ void __launch_bounds__(256) k_ir_outer_3d(
         const double su = axl * (u_c - uW) + axr * (u_c - uE) + ayl * (u_c - uS) + ayu * (u_c - uN) +
                           azl * (u_c - u_m) + azu * (u_c - u_p);
         const double um = w.t > 0 ? u[i - S] : 0.0;
-        const double b = F[i] - (u_c - um) - su;
+        const double b = fma(-sg, su, F[i] - (u_c - um));
         acc = fma(b, b, acc);
         const float gzf = ctf * nzf[z];
         const float gyzf = gzf * gyf, gxzf = gzf * gxf;
@@ -499,13 +549,13 @@ __global__ void __launch_bounds__(256) k_ir_outer_3d(
                          azlf * (w_c - w_m) + azuf * (w_c - w_p);
         const double wc = p[i] + u_c;
         const double wn = w.t + 1 < N ? wv(i + S) : 0.0;
-        r1 = (float)b + sw;
+        r1 = fmaf(sgf, sw, (float)b);
         r2 = (float)(b - (wc - wn));
       }
       if (z < P) {
         R1[at(z)] = r1;
         R2[at(z)] = r2;
-        rp[at(z)] = -r1;
+        rp[at(z)] = -(rhf * r1);
       }
       u_m = u_c;
       u_c = u_p;
@@ -523,25 +573,25 @@ __global__ void __launch_bounds__(256) k_ir_outer_3d(
 
 void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s) {
+                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s) {
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * P * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * n * N);
   k_ir_inner_3d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
-                                              (float)s_h2, n, logP, S, nwarps, st);
+                                              (float)s_h2, n, logP, S, nwarps, sp, st);
 }
 
 void launch_ir_outer_3d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
                         double* partials, const double* tab, const float* tabf, const double* cth, double a0,
-                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
-                        cudaStream_t s) {
+                        double tau, double h, int n, int logP, long long S, int N, Steps<double> sp,
+                        const SolveState* st, cudaStream_t s) {
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * P * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("ir_outer", s, 36.0 * (double)n * n * n * N);
   k_ir_outer_3d<<<kReduceBlocks, 256, 0, s>>>(u, p, F, R1, R2, rp, partials, tab, tabf, cth, s_h2 * a0, s_h2, n,
-                                              logP, S, N, nwarps, st);
+                                              logP, S, N, nwarps, sp, st);
 }
 
 }  // namespace pt

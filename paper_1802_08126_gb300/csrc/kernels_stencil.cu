@@ -11,7 +11,8 @@ namespace {
 
 template <int DIM>
 __global__ void k_pack(const double* __restrict__ src, const double* __restrict__ u0,
-                       double* __restrict__ dst, double scale, int n, int logP, long long total) {
+                       double* __restrict__ dst, double scale, const double* __restrict__ scale_t, int n,
+                       int logP, long long total) {
   const long long ns = DIM == 1 ? n : (DIM == 2 ? (long long)n * n : (long long)n * n * n);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -20,7 +21,7 @@ __global__ void k_pack(const double* __restrict__ src, const double* __restrict_
     double v = 0.0;
     if (decode<DIM>(i, logP, n, t, x, y, z)) {
       const long long q = ((long long)z * n + y) * n + x;
-      v = scale * src[t * ns + q];
+      v = (scale_t ? scale_t[t] : scale) * src[t * ns + q];
       if (u0 != nullptr && t == 0) v += u0[q];
     }
     dst[i] = v;
@@ -32,7 +33,8 @@ __global__ void k_pack(const double* __restrict__ src, const double* __restrict_
 // Flood (2014) used as a counter-based generator.
 template <int DIM>
 __global__ void k_pack_uniform(unsigned long long seed, const double* __restrict__ u0,
-                               double* __restrict__ dst, double scale, int n, int logP, long long total) {
+                               double* __restrict__ dst, double scale, const double* __restrict__ scale_t, int n,
+                               int logP, long long total) {
   const long long ns = DIM == 1 ? n : (DIM == 2 ? (long long)n * n : (long long)n * n * n);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -46,7 +48,7 @@ __global__ void k_pack_uniform(unsigned long long seed, const double* __restrict
       h = (h ^ (h >> 27)) * 0x94D049BB133111EBull;
       h ^= h >> 31;
       const double uni = (double)(h >> 11) * (1.0 / 9007199254740992.0);
-      v = scale * (2.0 * uni - 1.0);
+      v = (scale_t ? scale_t[t] : scale) * (2.0 * uni - 1.0);
       if (u0 != nullptr && t == 0) v += u0[q];
     }
     dst[i] = v;
@@ -86,7 +88,7 @@ __global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, in
 
 template <int DIM>
 __global__ void k_apply_B(const double* __restrict__ u, double* __restrict__ out,
-                          StencilGeom<double> g, const double* __restrict__ cth, double tau,
+                          StencilGeom<double> g, const double* __restrict__ cth, Steps<double> sp,
                           long long total) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -99,17 +101,18 @@ __global__ void k_apply_B(const double* __restrict__ u, double* __restrict__ out
       const double uc = u[i];
       const double um = t > 0 ? u[i - g.S] : 0.0;
       const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
-      v = (uc - um) + tau * Au;
+      v = (uc - um) + sp.tau[t] * Au;
     }
     out[i] = v;
   }
 }
 
-// r_p = K u - tau A_t p - F  (first line of eq. 3.1)
+// rho_t r_p, r_p = K u - tau_t A_t p - F  (first line of eq. 3.1; rho_t makes the A~ input of
+// the V-cycle for tau A_t that of tau_t A_t)
 template <int DIM, typename Tp>
 __global__ void k_resid_p(const double* __restrict__ u, const double* __restrict__ p,
                           const double* __restrict__ F, Tp* __restrict__ rp, StencilGeom<double> g,
-                          const double* __restrict__ cth, double tau, long long total,
+                          const double* __restrict__ cth, Steps<double> sp, long long total,
                           const int* done) {
   if (stop_requested(done)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -123,7 +126,7 @@ __global__ void k_resid_p(const double* __restrict__ u, const double* __restrict
       const double pc = p[i];
       const double Ap = stencil_sum<DIM, double>(p, i, pc, am, ap, g.P) * g.h2inv;
       const double um = t > 0 ? u[i - g.S] : 0.0;
-      v = (u[i] - um) - tau * Ap - F[i];
+      v = ((u[i] - um) - sp.tau[t] * Ap - F[i]) * sp.rho[t];
     }
     rp[i] = (Tp)v;
   }
@@ -135,7 +138,7 @@ template <int DIM, typename Tp>
 __global__ void k_resid_u(const double* __restrict__ u, const double* __restrict__ p,
                           const double* __restrict__ F, Tp* __restrict__ ru,
                           double* __restrict__ partials, StencilGeom<double> g,
-                          const double* __restrict__ cth, double tau, int N, long long total,
+                          const double* __restrict__ cth, Steps<double> sp, int N, long long total,
                           const int* done) {
   if (stop_requested(done)) return;
   double acc = 0.0;
@@ -150,7 +153,7 @@ __global__ void k_resid_u(const double* __restrict__ u, const double* __restrict
       const double uc = u[i];
       const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
       const double um = t > 0 ? u[i - g.S] : 0.0;
-      const double bres = F[i] - (uc - um) - tau * Au;
+      const double bres = F[i] - (uc - um) - sp.tau[t] * Au;
       const double next = t + 1 < N ? p[i + g.S] + u[i + g.S] : 0.0;
       v = bres - (p[i] + uc) + next;
       acc += bres * bres;
@@ -161,19 +164,19 @@ __global__ void k_resid_u(const double* __restrict__ u, const double* __restrict
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Mixed precision, first half of an iteration: the outer residual bres = F - K u - tau A_t u in
-// FP64 (stored, with its squared-norm partials), and the A~ input
-//   r_p = K u - tau A_t p - F = -bres - tau A_t (p + u)
+// Mixed precision, first half of an iteration: the outer residual bres = F - K u - tau_t A_t u in
+// FP64 (stored, with its squared-norm partials), and the A~ input rho_t r_p,
+//   r_p = K u - tau_t A_t p - F = -bres - tau_t A_t (p + u)
 // whose second term is a stencil on w = p + u, a quantity that tends to zero, taken in FP32.
 template <int DIM>
 __global__ void k_resid_bres_mixed(const double* __restrict__ u, const double* __restrict__ p,
                                    const double* __restrict__ F, double* __restrict__ bres,
                                    float* __restrict__ rp, double* __restrict__ partials,
-                                   StencilGeom<double> g, const double* __restrict__ cth, double tau,
+                                   StencilGeom<double> g, const double* __restrict__ cth, Steps<double> sp,
                                    long long total, const int* done) {
   if (stop_requested(done)) return;
   double acc = 0.0;
-  const float tauf = (float)tau, h2f = (float)g.h2inv;
+  const float h2f = (float)g.h2inv;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     long long t;
@@ -186,8 +189,10 @@ __global__ void k_resid_bres_mixed(const double* __restrict__ u, const double* _
       const double uc = u[i];
       const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
       const double um = t > 0 ? u[i - g.S] : 0.0;
+      const double tau = sp.tau[t];
       b = F[i] - (uc - um) - tau * Au;
       acc += b * b;
+      const float tauf = (float)tau;
       const float wc = (float)(p[i] + uc);
       long long off[3] = {1, g.P, (long long)g.P * g.P};
       float aw = 0.f;
@@ -197,7 +202,7 @@ __global__ void k_resid_bres_mixed(const double* __restrict__ u, const double* _
         const float wp = (float)(p[i + off[d]] + u[i + off[d]]);
         aw += (float)am[d] * (wc - wm) + (float)ap[d] * (wc - wp);
       }
-      r = (float)(-b) - tauf * h2f * aw;
+      r = ((float)(-b) - tauf * h2f * aw) * (float)sp.rho[t];
     }
     bres[i] = b;
     rp[i] = r;
@@ -301,6 +306,14 @@ __global__ void k_gather_done(SolveState* const* __restrict__ states, int count,
     out[i] = states[i]->done == 1;
 }
 
+// x[i] *= f[i >> logS]: one factor per slot of 2^logS elements
+template <typename T>
+__global__ void k_scale_slices(T* __restrict__ x, const T* __restrict__ f, int logS, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= f[i >> logS];
+}
+
 template <typename Tp>
 __global__ void k_axpy(double* __restrict__ y, const Tp* __restrict__ x, double a, long long count,
                        const int* done) {
@@ -334,19 +347,20 @@ inline double dofs(int dim, int n, int N) {
   return d;
 }
 
-void launch_pack(const double* src, const double* u0, double* dst, double scale, int dim, int n,
-                 int P, int logP, long long S, int N, cudaStream_t st) {
+void launch_pack(const double* src, const double* u0, double* dst, double scale, const double* scale_t, int dim,
+                 int n, int P, int logP, long long S, int N, cudaStream_t st) {
   (void)P;
   const long long total = S * N;
   LaunchScope ls("pack", st, 16.0 * dofs(dim, n, N));
-  PT_DISPATCH_DIM(dim, k_pack<D><<<grid_for(total), kThreads, 0, st>>>(src, u0, dst, scale, n, logP, total));
+  PT_DISPATCH_DIM(dim, k_pack<D><<<grid_for(total), kThreads, 0, st>>>(src, u0, dst, scale, scale_t, n, logP, total));
 }
 
-void launch_pack_uniform(unsigned long long seed, const double* u0, double* dst, double scale, int dim,
-                         int n, int logP, long long S, int N, cudaStream_t st) {
+void launch_pack_uniform(unsigned long long seed, const double* u0, double* dst, double scale,
+                         const double* scale_t, int dim, int n, int logP, long long S, int N, cudaStream_t st) {
   const long long total = S * N;
   LaunchScope ls("pack", st, 8.0 * dofs(dim, n, N));
-  PT_DISPATCH_DIM(dim, k_pack_uniform<D><<<grid_for(total), kThreads, 0, st>>>(seed, u0, dst, scale, n, logP, total));
+  PT_DISPATCH_DIM(dim, k_pack_uniform<D><<<grid_for(total), kThreads, 0, st>>>(seed, u0, dst, scale, scale_t, n,
+                                                                               logP, total));
 }
 
 template <typename T>
@@ -369,36 +383,36 @@ void launch_unpack(const T* src, double* dst, int dim, int n, int P, int logP, l
   PT_DISPATCH_DIM(dim, k_unpack<D, T><<<grid_for(total), kThreads, 0, st>>>(src, dst, n, logP, S, total));
 }
 
-void launch_apply_B(const double* u, double* out, StencilGeom<double> g, const double* cth, double tau,
+void launch_apply_B(const double* u, double* out, StencilGeom<double> g, const double* cth, Steps<double> sp,
                     int N, cudaStream_t st) {
   const long long total = g.S * N;
   LaunchScope ls("apply_B", st, 16.0 * dofs(g.dim, g.n, N));
-  PT_DISPATCH_DIM(g.dim, k_apply_B<D><<<grid_for(total), kThreads, 0, st>>>(u, out, g, cth, tau, total));
+  PT_DISPATCH_DIM(g.dim, k_apply_B<D><<<grid_for(total), kThreads, 0, st>>>(u, out, g, cth, sp, total));
 }
 
 template <typename Tp>
 void launch_resid_p(const double* u, const double* p, const double* F, Tp* rp, StencilGeom<double> g,
-                    const double* cth, double tau, int N, const int* done, cudaStream_t st) {
+                    const double* cth, Steps<double> sp, int N, const int* done, cudaStream_t st) {
   const long long total = g.S * N;
   LaunchScope ls("resid_p", st, (24.0 + sizeof(Tp)) * dofs(g.dim, g.n, N));
-  PT_DISPATCH_DIM(g.dim, k_resid_p<D, Tp><<<grid_for(total), kThreads, 0, st>>>(u, p, F, rp, g, cth, tau, total, done));
+  PT_DISPATCH_DIM(g.dim, k_resid_p<D, Tp><<<grid_for(total), kThreads, 0, st>>>(u, p, F, rp, g, cth, sp, total, done));
 }
 
 template <typename Tp>
 void launch_resid_u(const double* u, const double* p, const double* F, Tp* ru, double* partials,
-                    StencilGeom<double> g, const double* cth, double tau, int N, const int* done,
+                    StencilGeom<double> g, const double* cth, Steps<double> sp, int N, const int* done,
                     cudaStream_t st) {
   const long long total = g.S * N;
   LaunchScope ls("resid_u", st, (24.0 + sizeof(Tp)) * dofs(g.dim, g.n, N));
-  PT_DISPATCH_DIM(g.dim, k_resid_u<D, Tp><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, ru, partials, g, cth, tau, N, total, done));
+  PT_DISPATCH_DIM(g.dim, k_resid_u<D, Tp><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, ru, partials, g, cth, sp, N, total, done));
 }
 
 void launch_resid_bres_mixed(const double* u, const double* p, const double* F, double* bres, float* rp,
-                             double* partials, StencilGeom<double> g, const double* cth, double tau, int N,
+                             double* partials, StencilGeom<double> g, const double* cth, Steps<double> sp, int N,
                              const int* done, cudaStream_t st) {
   const long long total = g.S * N;
   LaunchScope ls("resid_bres", st, (24.0 + 8.0 + 4.0) * dofs(g.dim, g.n, N));
-  PT_DISPATCH_DIM(g.dim, k_resid_bres_mixed<D><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, bres, rp, partials, g, cth, tau, total, done));
+  PT_DISPATCH_DIM(g.dim, k_resid_bres_mixed<D><<<kReduceBlocks, kThreads, 0, st>>>(u, p, F, bres, rp, partials, g, cth, sp, total, done));
 }
 
 template <typename Tp>
@@ -445,6 +459,14 @@ void launch_gather_done(SolveState* const* states, int count, int* out, cudaStre
   k_gather_done<<<(count + 255) / 256, 256, 0, st>>>(states, count, out);
 }
 
+template <typename T>
+void launch_scale_slices(T* x, const T* f, int logS, long long total, cudaStream_t st) {
+  LaunchScope ls("scale_slices", st, 2.0 * sizeof(T) * (double)total);
+  k_scale_slices<T><<<grid_for(total), kThreads, 0, st>>>(x, f, logS, total);
+}
+template void launch_scale_slices<float>(float*, const float*, int, long long, cudaStream_t);
+template void launch_scale_slices<double>(double*, const double*, int, long long, cudaStream_t);
+
 template <typename Tp>
 void launch_axpy(double* y, const Tp* x, double a, long long count, const int* done, cudaStream_t st) {
   LaunchScope ls("axpy", st, (16.0 + sizeof(Tp)) * (double)count);
@@ -455,10 +477,10 @@ template void launch_pack_typed<float>(const double*, float*, int, int, int, int
 template void launch_pack_typed<double>(const double*, double*, int, int, int, int, long long, int, cudaStream_t);
 template void launch_unpack<float>(const float*, double*, int, int, int, int, long long, int, cudaStream_t);
 template void launch_unpack<double>(const double*, double*, int, int, int, int, long long, int, cudaStream_t);
-template void launch_resid_p<float>(const double*, const double*, const double*, float*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
-template void launch_resid_p<double>(const double*, const double*, const double*, double*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
-template void launch_resid_u<float>(const double*, const double*, const double*, float*, double*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
-template void launch_resid_u<double>(const double*, const double*, const double*, double*, double*, StencilGeom<double>, const double*, double, int, const int*, cudaStream_t);
+template void launch_resid_p<float>(const double*, const double*, const double*, float*, StencilGeom<double>, const double*, Steps<double>, int, const int*, cudaStream_t);
+template void launch_resid_p<double>(const double*, const double*, const double*, double*, StencilGeom<double>, const double*, Steps<double>, int, const int*, cudaStream_t);
+template void launch_resid_u<float>(const double*, const double*, const double*, float*, double*, StencilGeom<double>, const double*, Steps<double>, int, const int*, cudaStream_t);
+template void launch_resid_u<double>(const double*, const double*, const double*, double*, double*, StencilGeom<double>, const double*, Steps<double>, int, const int*, cudaStream_t);
 template void launch_apply_A_scaled<float>(const float*, float*, StencilGeom<float>, float, float, int, const int*, cudaStream_t);
 template void launch_apply_A_scaled<double>(const double*, double*, StencilGeom<double>, double, double, int, const int*, cudaStream_t);
 template void launch_axpy<float>(double*, const float*, double, long long, const int*, cudaStream_t);

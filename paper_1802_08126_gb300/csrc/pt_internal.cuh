@@ -68,6 +68,19 @@ struct StencilGeom {
   T h2inv;        // 1/h^2
 };
 
+// Per-step factors of the time grid (§2, eq. 2.1), [N] each: the step lengths tau_n, and against
+// the reference step tau = T/N of the preconditioner sigma_n = tau_n / tau and rho_n = tau / tau_n
+// (all 1 for uniform steps).  tau_n A_n = sigma_n (tau A_n), and the V-cycle being homogeneous of
+// degree -1 in the operator, A~^-1 for tau_n A_n is rho_n times the V-cycle for tau A_n: the kernels
+// that form the A~ input scale it by rho_n, and the multigrid kernels keep the scale tau.
+template <typename T>
+struct Steps {
+  const T* tau;
+  const T* sig;
+  const T* rho;   // null: no scaling of the A~ input (the Krylov path's operator application)
+  bool uniform;   // all steps equal (sigma = rho = 1): kernels may skip the factors
+};
+
 // Batched operator L_b = sig[b] I + s * A(cth[b]) on one level, used by the V-cycle.
 template <typename T>
 struct OpBatch {
@@ -79,11 +92,12 @@ struct OpBatch {
 
 // ---- stencil / residual kernels (kernels_stencil.cu) --------------------------------------
 // F (padded) = scale * pack(src) (+ u0 on slot 0 when u0 != nullptr), src packed [N][ns].
-void launch_pack(const double* src, const double* u0, double* dst, double scale, int dim, int n,
-                 int P, int logP, long long S, int N, cudaStream_t st);
+// scale_t: [N] per-slice factors (the step lengths) replacing scale when not null.
+void launch_pack(const double* src, const double* u0, double* dst, double scale, const double* scale_t, int dim,
+                 int n, int P, int logP, long long S, int N, cudaStream_t st);
 // F (padded) = scale * (2 U - 1) (+ u0 on slot 0), U from SplitMix64(seed) at the packed index
-void launch_pack_uniform(unsigned long long seed, const double* u0, double* dst, double scale, int dim,
-                         int n, int logP, long long S, int N, cudaStream_t st);
+void launch_pack_uniform(unsigned long long seed, const double* u0, double* dst, double scale,
+                         const double* scale_t, int dim, int n, int logP, long long S, int N, cudaStream_t st);
 template <typename T>
 void launch_unpack(const T* src, double* dst, int dim, int n, int P, int logP, long long S, int N,
                    cudaStream_t st);
@@ -92,42 +106,47 @@ void launch_pack_typed(const double* src, T* dst, int dim, int n, int P, int log
                        int N, cudaStream_t st);
 
 // out = B u (FP64)
-void launch_apply_B(const double* u, double* out, StencilGeom<double> g, const double* cth, double tau,
+void launch_apply_B(const double* u, double* out, StencilGeom<double> g, const double* cth, Steps<double> sp,
                     int N, cudaStream_t st);
 
-// r_p = K u - tau A_n p - F   (written in precision Tp)
+// rho_n r_p with r_p = K u - tau_n A_n p - F   (written in precision Tp)
 template <typename Tp>
 void launch_resid_p(const double* u, const double* p, const double* F, Tp* rp, StencilGeom<double> g,
-                    const double* cth, double tau, int N, const int* done, cudaStream_t st);
+                    const double* cth, Steps<double> sp, int N, const int* done, cudaStream_t st);
 
-// r_u = F - K^T p - (K + K^T + tau A_n) u, partial sums of ||F - B u||^2 per block
+// r_u = F - K^T p - (K + K^T + tau_n A_n) u, partial sums of ||F - B u||^2 per block
 template <typename Tp>
 void launch_resid_u(const double* u, const double* p, const double* F, Tp* ru, double* partials,
-                    StencilGeom<double> g, const double* cth, double tau, int N, const int* done,
+                    StencilGeom<double> g, const double* cth, Steps<double> sp, int N, const int* done,
                     cudaStream_t st);
 
-// Mixed precision: bres = F - B u (FP64, stored, norm partials) and r_p = -bres - tau A_n (p + u)
-// with the second stencil in FP32; then r_u = bres - K^T (p + u) (no stencil).
+// Mixed precision: bres = F - B u (FP64, stored, norm partials) and rho_n r_p, r_p = -bres -
+// tau_n A_n (p + u) with the second stencil in FP32; then r_u = bres - K^T (p + u) (no stencil).
 void launch_resid_bres_mixed(const double* u, const double* p, const double* F, double* bres, float* rp,
-                             double* partials, StencilGeom<double> g, const double* cth, double tau, int N,
+                             double* partials, StencilGeom<double> g, const double* cth, Steps<double> sp, int N,
                              const int* done, cudaStream_t st);
 template <typename Tp>
 void launch_resid_u_from_bres(const double* bres, const double* u, const double* p, Tp* ru, long long S,
                               int N, int dim, int n, const int* done, cudaStream_t st, double sgn = 1.0);
 // 2-D (n + 1 >= 32) fused outer residual: bres = F - B u (FP64, stored, norm partials over a fixed
-// grid of kReduceBlocks blocks) and r_p = -bres - tau A (p + u) in precision W (FP32: the w-stencil
-// in FP32; FP64: all in FP64).  tab / tabf: level-0 coefficient tables in FP64 / FP32.
+// grid of kReduceBlocks blocks) and rho_n r_p, r_p = -bres - tau_n A (p + u), in precision W (FP32:
+// the w-stencil in FP32; FP64: all in FP64).  tab / tabf: level-0 coefficient tables in FP64 / FP32;
+// tau: the reference step (the stencils are formed for tau A_n and scaled by sigma_n).
 // jd: cached (w/D, D) pairs of tau A_n at level 0, or null (FP64: the stencils then use D)
 template <typename W>
 void launch_resid_bres_2d(const double* u, const double* p, const double* F, double* bres, W* rp,
                           double* partials, const double* tab, const float* tabf, const double* cth, double a0,
                           double tau, double h, int n, int logP, long long S, int N, const int* done,
-                          const double* jd, cudaStream_t st);
+                          const double* jd, Steps<double> sp, cudaStream_t st);
 
 // out = scale * A(cthbar) z on one batch (Abar apply of the Hhat block solve)
 template <typename T>
 void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale, int N,
                            const int* done, cudaStream_t st);
+
+// x[i] *= f[i >> logS] (padded space-time vector, one factor per slot)
+template <typename T>
+void launch_scale_slices(T* x, const T* f, int logS, long long total, cudaStream_t st);
 
 // partial sums of ||v||^2 (padded vector, ghosts are zero)
 void launch_norm2_partials(const double* v, long long count, double* partials, cudaStream_t st);
@@ -152,27 +171,27 @@ void launch_ir_begin(SolveState* st, int kouter, cudaStream_t s);
 void launch_ir_fold(double* u, double* p, float* du, float* dp, long long total, const SolveState* st,
                     cudaStream_t s);
 void launch_ir_outer(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
-                     double* partials, StencilGeom<double> g, const double* cth, double tau, int N,
+                     double* partials, StencilGeom<double> g, const double* cth, Steps<double> sp, int N,
                      const SolveState* st, cudaStream_t s);
 void launch_ir_inner(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
-                     double* partials, StencilGeom<float> g, const float* cth, float tau, int N,
+                     double* partials, StencilGeom<float> g, const float* cth, Steps<float> sp, int N,
                      const SolveState* st, cudaStream_t s);
 // 2-D (n + 1 >= 32) warp-strip forms of launch_ir_outer / launch_ir_inner (kernels_resid2d.cu);
 // tab / tabf: level-0 FP64 / FP32 tables
 void launch_ir_outer_2d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
                         double* partials, const double* tab, const float* tabf, const double* cth, double a0,
-                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
-                        cudaStream_t s);
+                        double tau, double h, int n, int logP, long long S, int N, Steps<double> sp,
+                        const SolveState* st, cudaStream_t s);
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s);
+                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s);
 void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, const SolveState* st, cudaStream_t s);
+                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s);
 void launch_ir_outer_3d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
                         double* partials, const double* tab, const float* tabf, const double* cth, double a0,
-                        double tau, double h, int n, int logP, long long S, int N, const SolveState* st,
-                        cudaStream_t s);
+                        double tau, double h, int n, int logP, long long S, int N, Steps<double> sp,
+                        const SolveState* st, cudaStream_t s);
 void launch_ir_resid_u(const float* bp, const float* R2, const float* du, const float* dp, float* ru, long long S,
                        int N, const SolveState* st, cudaStream_t s);
 void launch_ir_finalize(const double* partials, SolveState* state, double* hist, cudaStream_t s);
@@ -293,14 +312,15 @@ void launch_dsti_scale_table(T* g, const double* lam, const double* mu, double t
 
 // Krylov acceleration (kernels_krylov.cu): pairs (p, u) of padded FP64 space-time vectors.
 void launch_apply_saddle(const double* zp, const double* zu, double* op, double* ou, StencilGeom<double> g,
-                         const double* cth, double tau, int N, cudaStream_t st);
+                         const double* cth, Steps<double> sp, int N, cudaStream_t st);
 // partials [nv (+1 with self: <w, w>)][kReduceBlocks]
 void launch_multidot(const double* const* vp, const double* const* vu, const double* wp, const double* wu, int nv,
                      int self, long long total, double* partials, cudaStream_t st);
 void launch_multiaxpy(const double* const* vp, const double* const* vu, const double* c, int nv, double* wp,
                       double* wu, long long total, cudaStream_t st);
+// (yp, yu) = s (xp, xu), times rho[t] on slice t (slices of 2^logS elements) when rho is not null
 void launch_scale_pair(const double* xp, const double* xu, double s, double* yp, double* yu, long long total,
-                       cudaStream_t st);
+                       cudaStream_t st, const double* rho = nullptr, int logS = 0);
 void launch_uzawa_ru(const double* vu, const double* zp, double* ru, long long S, int N, cudaStream_t st);
 
 // Problem hooks for the serving loop (defined in capi.cu).

@@ -36,7 +36,7 @@ struct Request {
   double T = 0.0;
   pt_coeff coeff{};
   pt_options opt{};
-  std::vector<double> f, u0;
+  std::vector<double> f, u0, steps;
   bool seeded = false;
   unsigned long long seed = 0;
   double tol = 0.0;
@@ -296,6 +296,10 @@ pt_status pt_server_submit(pt_server* sv, const pt_grid* grid, int N_t, double T
   r->coeff = *coeff;
   if (opts) r->opt = *opts;
   r->opt.stream = nullptr;
+  if (r->opt.tau_steps) {  // the request outlives the caller's array
+    r->steps.assign(r->opt.tau_steps, r->opt.tau_steps + N_t);
+    r->opt.tau_steps = r->steps.data();
+  }
   long long ns = 1;
   for (int d = 0; d < grid->dim; ++d) ns *= grid->n[d];
   r->dofs = ns * N_t;

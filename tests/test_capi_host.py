@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
-def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, krylov=0, precision=0):
+def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, krylov=0, precision=0, steps=None):
     g = _lib.Grid()
     g.dim = dim
     for d in range(3):
@@ -53,6 +53,9 @@ def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, kry
     o.reserved[0] = reserved
     o.krylov = krylov
     o.precision = precision
+    if steps is not None:
+        steps = np.ascontiguousarray(steps, dtype=np.float64)
+        o.tau_steps = steps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     f = np.zeros(N * n ** dim)
     h = ctypes.c_void_p()
     st = lib.pt_problem_create(ctypes.byref(g), N, 1.0, ctypes.byref(k), f.ctypes.data, 0, None, 0,
@@ -62,7 +65,10 @@ def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, kry
 
 @pytest.mark.parametrize("kw", [dict(n=6), dict(N=3000), dict(N=0), dict(dim=4), dict(c=1.0),
                                 dict(solver=1, dim=2), dict(nv=5), dict(reserved=1), dict(krylov=65),
-                                dict(krylov=-1), dict(krylov=10, precision=1)])
+                                dict(krylov=-1), dict(krylov=10, precision=1),
+                                dict(steps=[0.125] * 7 + [0.0]), dict(steps=[0.125] * 7 + [-0.125]),
+                                dict(steps=[0.125] * 7 + [float("nan")]), dict(steps=[0.125] * 7 + [0.126]),
+                                dict(steps=[0.25] * 8)])
 def test_invalid_arguments_rejected_on_host(lib, kw):
     st, h = _create(lib, **kw)
     assert st == _lib.PT_EINVAL

@@ -98,13 +98,25 @@ def test_equal_steps_reduce_to_the_uniform_oracle():
     assert np.abs(a - b).max() <= 1e-15 * np.abs(a).max()
 
 
-def test_reference_operator_is_the_tau_weighted_mean():
-    """tau Abar = (1/N) sum tau_n A_n: for a coefficient constant in time it is A itself."""
+def test_reference_operator_is_the_time_mean():
+    """Abar is the operator of (1/T) int_0^T a dt (eq. 2.2, an average): A itself for a coefficient
+    constant in time; for sin(pi t) over (0, 1/2) the operator at the time t* with
+    sin(pi t*) = 2/pi; for the workloads' periodic coefficients the a0-only operator, which is also
+    the mean of the A_n over uniform steps."""
     p = _with_steps(S.heat2d_uniform(7, 16), seed=4)
     c = dataclasses.replace(p.coeff, ft=S.TRIG_ONE, mt=0.0)
     T = st.SpaceTime(p.dim, p.n, p.N, p.T, c, taus=p.taus)
     assert abs(sum(p.taus) - p.T) < 1e-14
     assert abs((T.Abar - T.A[0]).toarray()).max() < 1e-12 * abs(T.A[0].toarray()).max()
+    s = dataclasses.replace(p.coeff, ft=S.TRIG_SIN, mt=1.0)
+    t_star = math.asin(2.0 / math.pi) / math.pi
+    ref = st.assemble_A(2, p.n, s, t_star).toarray()
+    assert abs(st.reference_operator(2, p.n, s, 0.5).toarray() - ref).max() < 1e-13 * abs(ref).max()
+    for q in (S.heat2d_uniform(7, 16), S.heat3d_bumps(3, 8)):
+        a0_only = st.assemble_A(q.dim, q.n, dataclasses.replace(q.coeff, c=0.0), 0.0).toarray()
+        Tq = st.SpaceTime(q.dim, q.n, q.N, q.T, q.coeff)
+        assert abs(Tq.Abar.toarray() - a0_only).max() < 1e-13 * abs(a0_only).max()
+        assert abs((sum(Tq.A) / q.N).toarray() - a0_only).max() < 1e-13 * abs(a0_only).max()
 
 
 @pytest.mark.parametrize("use_mg", [False, True])
