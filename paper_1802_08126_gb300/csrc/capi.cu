@@ -1203,6 +1203,14 @@ pt_status setup_precision(pt_problem* p) {
   return PT_OK;
 }
 
+// Host arrays move through the preconditioner work buffer W1 (free between solves; its start is
+// aligned to 32 elements by the guard) in chunks of whole slices: contiguous copies and no device
+// allocation per call.  Slices per chunk, 0 if not even one fits (then a temporary is allocated).
+int staging_slices(const pt_problem* p) {
+  const size_t avail = (size_t)p->lev[0].S * p->N * (p->mixed ? sizeof(float) : sizeof(double));
+  return (int)std::min<size_t>((size_t)p->N, avail / (sizeof(double) * (size_t)p->ns));
+}
+
 pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, int u0_dev,
                    const unsigned long long* seed = nullptr) {
   const size_t fbytes = sizeof(double) * (size_t)p->ns * p->N;
@@ -1210,17 +1218,32 @@ pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, 
   const double* u0d = u0;
   void* tf = nullptr;
   void* tu = nullptr;
-  if (f && !f_dev) {
-    PT_CUDA(cudaMallocAsync(&tf, fbytes, p->st));
-    PT_CUDA(cudaMemcpyAsync(tf, f, fbytes, cudaMemcpyHostToDevice, p->st));
-    fd = (const double*)tf;
-  }
+  const Level& L = p->lev[0];
   if (u0 && !u0_dev) {
     PT_CUDA(cudaMallocAsync(&tu, sizeof(double) * p->ns, p->st));
     PT_CUDA(cudaMemcpyAsync(tu, u0, sizeof(double) * p->ns, cudaMemcpyHostToDevice, p->st));
     u0d = (const double*)tu;
   }
-  const Level& L = p->lev[0];
+  const int chunk = staging_slices(p);
+  if (!seed && f && !f_dev && chunk >= 1) {
+    // F_n = tau_n f_n (+ u0 for n = 1), chunk by chunk through W1
+    const size_t slice = sizeof(double) * (size_t)p->ns;
+    double* stg = (double*)p->W1;
+    for (int t0 = 0; t0 < p->N; t0 += chunk) {
+      const int c = std::min(chunk, p->N - t0);
+      PT_CUDA(cudaMemcpyAsync(stg, f + (size_t)t0 * p->ns, slice * c, cudaMemcpyHostToDevice, p->st));
+      launch_pack(stg, t0 == 0 ? u0d : nullptr, p->F + (size_t)t0 * L.S, 0.0, p->stp_d + t0, p->dim, L.n, L.P,
+                  L.logP, L.S, c, p->st);
+      PT_CHECK_LAUNCH();
+    }
+    if (tu) PT_CUDA(cudaFreeAsync(tu, p->st));
+    return PT_OK;
+  }
+  if (f && !f_dev) {
+    PT_CUDA(cudaMallocAsync(&tf, fbytes, p->st));
+    PT_CUDA(cudaMemcpyAsync(tf, f, fbytes, cudaMemcpyHostToDevice, p->st));
+    fd = (const double*)tf;
+  }
   // F_n = tau_n f_n (+ u0 for n = 1)
   if (seed)
     launch_pack_uniform(*seed, u0d, p->F, 0.0, p->stp_d, p->dim, L.n, L.logP, L.S, p->N, p->st);
@@ -1562,6 +1585,19 @@ pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_o
     const size_t bytes = sizeof(double) * (size_t)p->ns * p->N;
     double* dst = u_out;
     void* tmp = nullptr;
+    const int chunk = staging_slices(p);
+    if (!u_out_on_device && chunk >= 1) {  // through W1, chunk by chunk (see load_rhs)
+      const size_t slice = sizeof(double) * (size_t)p->ns;
+      double* stg = (double*)p->W1;
+      for (int t0 = 0; t0 < p->N; t0 += chunk) {
+        const int c = std::min(chunk, p->N - t0);
+        launch_unpack<double>(p->u + (size_t)t0 * L.S, stg, p->dim, L.n, L.P, L.logP, L.S, c, p->st);
+        PT_CHECK_LAUNCH();
+        PT_CUDA(cudaMemcpyAsync(u_out + (size_t)t0 * p->ns, stg, slice * c, cudaMemcpyDeviceToHost, p->st));
+      }
+      PT_CUDA(cudaStreamSynchronize(p->st));
+      return st;
+    }
     if (!u_out_on_device) {
       PT_CUDA(cudaMallocAsync(&tmp, bytes, p->st));
       dst = (double*)tmp;

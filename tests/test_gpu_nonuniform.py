@@ -212,3 +212,29 @@ def test_full_size_heat2d_random_steps_first_steps_and_global_residual():
     F = prob.taus[:, None] * f
     Bu = oracle.apply_B(prob.dim, prob.n, prob.N, prob.T, prob.coeff, u, taus=prob.taus)
     assert np.linalg.norm(F - Bu) / np.linalg.norm(F) <= 1e-12 * 1.01
+
+
+@pytest.mark.parametrize("prob", [S.heat2d_uniform(31, 16), steps(S.heat2d_uniform(31, 16), seed=2),
+                                  steps(S.heat3d_bumps(15, 6), seed=6), steps(S.heat1d_mms(31, 12), seed=7)],
+                         ids=lambda p: p.name + ("_uniform" if p.taus is None else "_steps"))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_buffers_match_device_buffers(prob, precision):
+    """Host f and u move through the work buffer in chunks of whole slices (two or more chunks in
+    mixed precision here): the same F, iterates and u as with device buffers, bit for bit."""
+    import paper_1802_08126_gb300 as ptu
+    f, u0 = S.source(prob), S.initial(prob)
+    out = []
+    for on_dev in (False, True):
+        fa = dev(f) if on_dev else f
+        with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, fa, u0, precision=precision,
+                         omega=OMEGA, taus=prob.taus) as P:
+            if on_dev:
+                u = torch.zeros((prob.N, prob.ns), dtype=torch.float64, device="cuda")
+                _, it, hist = P.solve(1e-10, 1000, u_out=u)
+                u = host(u)
+            else:
+                u = np.zeros((prob.N, prob.ns))
+                _, it, hist = P.solve(1e-10, 1000, u_out=u)
+        out.append((u, hist))
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[1][0])
