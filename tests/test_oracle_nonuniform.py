@@ -135,3 +135,26 @@ def test_uzawa_nonuniform_reaches_the_stepping_solution(use_mg):
     assert hist[-1] <= 1e-11
     ref = oracle.implicit_euler(p.dim, p.n, p.N, p.T, p.coeff, f, taus=p.taus)
     assert np.linalg.norm(u - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("dim,n", [(1, 31), (2, 15), (3, 7)])
+def test_vcycle_is_homogeneous_of_degree_minus_one(dim, n):
+    """The V-cycle reading (weighted Jacobi, full weighting, rediscretised coarse operators, exact
+    coarsest solve) of c L is (1/c) times that of L: the property that lets the library run the
+    V-cycles of tau A_n for every step and scale the A~ input by rho_n = tau / tau_n (§3, the
+    block-diagonal A~ of diag(tau_n A_n))."""
+    p = _with_steps(S.heat2d_uniform(n, 6) if dim == 2 else (S.heat1d_mms(n, 6) if dim == 1 else S.heat3d_bumps(n, 6)),
+                    seed=12)
+    tau = p.T / p.N
+    times = np.cumsum(p.taus)
+
+    def build(scales):
+        return lambda m: [scales[i] * st.assemble_A(dim, [m] * dim, p.coeff, times[i]) for i in range(p.N)]
+    Vn = mg.VCycle(dim, n, build(p.taus))
+    Vr = mg.VCycle(dim, n, build(np.full(p.N, tau)))
+    r = np.random.default_rng(2).standard_normal((p.N, n ** dim))
+    a = Vn.apply(r)
+    b = (tau / p.taus)[:, None] * Vr.apply(r)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    # and the scaling is not trivially satisfied: tau_n differ from tau by up to ~25 %
+    assert np.abs(p.taus / tau - 1).max() > 0.1
