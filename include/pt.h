@@ -3,10 +3,10 @@
  *
  * Problem (Neumüller & Smears, "Time-parallel iterative solvers for parabolic
  * evolution equations", §2, eq. 2.1): implicit Euler for u_t - div(a grad u) = f on
- * the unit box (0,1)^dim, homogeneous Dirichlet data, uniform steps tau = T/N_t,
- * t_n = n tau,
+ * the unit box (0,1)^dim, homogeneous Dirichlet data, steps tau_n (uniform T/N_t unless
+ * pt_options.tau_steps gives them), t_n = tau_1 + ... + tau_n,
  *
- *     (u_n - u_{n-1}) + tau A_n u_n = tau f_n,  n = 1..N_t,  u_0 = u0,
+ *     (u_n - u_{n-1}) + tau_n A_n u_n = tau_n f_n,  n = 1..N_t,  u_0 = u0,
  *
  * with M = I and the conservative finite-difference operator
  *     (A_n v)_i = sum_d h^-2 [a(x_i - h e_d/2, t_n)(v_i - v_{i-e_d}) + a(x_i + h e_d/2, t_n)(v_i - v_{i+e_d})].
