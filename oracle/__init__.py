@@ -8,8 +8,8 @@ CUDA path; the only common module is ``synthetic`` (seeded inputs).
 Contents
 --------
 ``_native``   C (gcc, OpenMP) sequential implicit Euler with a banded Cholesky
-              (or CG) solve per step, and the action of the time-global matrix B
-              (§2, eq. 2.1 and 2.3).  This is the plain definition the solver must
+              (or CG) solve per step, on uniform or given time steps, and the action
+              of the time-global matrix B (§2, eq. 2.1 and 2.3).  This is the plain definition the solver must
               reproduce: the saddle-point system (eq. 2.7) has u as its second
               component, which is exactly the implicit-Euler solution.
 ``spacetime`` NumPy/SciPy statement of K, B, S, the DST change of basis Phi,
