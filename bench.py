@@ -193,6 +193,41 @@ def fp64_flops_per_launch(name, dim, n, N):
     return None
 
 
+# Fused-minimum algorithmic bytes per DOF per Uzawa iteration (outer passes at 8 B, preconditioner
+# passes at 8 B or 4 B, three V(1,1) cycles): the model the path-level HBM roofline is quoted on.
+HBM_MODEL_BYTES = {("fp64", 2): 368.0, ("mixed", 2): 232.0, ("fp64", 3): 336.0, ("mixed", 3): 216.0}
+
+
+def path_roofline(prof, dims, iterations, value, precision, peaks, steps):
+    """Whole-solve bounds in DOFs/s: HBM bandwidth over the byte model, and (FP64 path) the FP64
+    pipe over the algorithmic flops of the modelled kernels; `frac` = value / the smaller."""
+    try:
+        dim, n, N = dims
+        dofs = float(N) * n ** dim
+        out = {}
+        b = HBM_MODEL_BYTES.get((precision, dim))
+        if b:
+            out["hbm_model_bytes_per_dof_iteration"] = b
+            out["hbm_bound_dofs_per_s"] = peaks["hbm_gbs"] * 1e9 / (b * iterations)
+        if precision == "fp64":
+            fl = 0.0
+            for k, v in prof.items():
+                f = fp64_flops_per_launch(k, dim, n, N)
+                if f is not None:
+                    fl += f * v["launches"] / steps
+            if fl > 0:
+                out["fp64_flops_per_dof_iteration"] = fl / dofs / iterations
+                out["fp64_bound_dofs_per_s"] = fp64_peak_tflops(peaks) * 1e12 * dofs / fl
+        bounds = [v for k, v in out.items() if k.endswith("_bound_dofs_per_s")]
+        if not bounds:
+            return None
+        out["bound"] = "hbm" if min(bounds) == out.get("hbm_bound_dofs_per_s") else "fp64"
+        out["frac"] = value / min(bounds)
+        return out
+    except Exception:
+        return None
+
+
 def roofline_of(prof, name, bound_fp64, dims, peaks, peak_src, tr):
     d = prof[name]
     per_launch_ms = d["ms"] / max(d["launches"], 1)
@@ -682,6 +717,7 @@ def main():
                        "l2": "inputs larger than L2 (533 MB per space-time vector)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "path_roofline": path_roofline(prof, dims, its[-1], value, base_prec, peaks, args.steps),
             "ms_per_step_with_kernel_events": ms_prof / args.steps,
             "clocks": clk, ("fp64_path" if variant == "fp64" else "mixed"): mixed, "krylov": krylov,
             "nonuniform_steps": nonuniform,
