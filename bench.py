@@ -296,6 +296,22 @@ def cpu_sample(prob, seconds, f=None):
     return k * prob.ns / secs, k, secs, cores, method
 
 
+def cpu_single_thread(prob, f, method, cores):
+    """The oracle on one host thread: DOFs/s of its first step (then all cores again)."""
+    import oracle
+    try:
+        u0 = S.initial(prob)
+        t0 = time.perf_counter()
+        oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, steps=1, method=method,
+                              threads=1)
+        secs = time.perf_counter() - t0
+        return {"value": prob.ns / secs, "unit": "DOF/s", "cores": 1, "sample": "first step (%.2f s)" % secs}
+    except Exception:
+        return None
+    finally:
+        oracle.implicit_euler(prob.dim, [1] * prob.dim, 1, prob.T, prob.coeff, np.zeros(1), None, threads=cores)
+
+
 def run_reference(args, rank, ws, dist):
     if rank != 0:
         return 0
@@ -701,7 +717,8 @@ def main():
         v, k, secs, cores, method = cpu_sample(prob, args.cpu_seconds, f[:64])
         cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
                "sample": "first %d of %d implicit-Euler steps, %s per step (%.1f s)"
-                         % (k, prob.N, "banded Cholesky" if method == "cholesky" else "CG to 1e-14", secs)}
+                         % (k, prob.N, "banded Cholesky" if method == "cholesky" else "CG to 1e-14", secs),
+               "single_thread": cpu_single_thread(prob, f[:64], method, cores)}
 
     if rank == 0:
         line = {

@@ -35,3 +35,13 @@ def test_path_roofline_mixed_and_unmodelled():
     assert out["frac"] == pytest.approx(2.9e8 / (6696.2e9 / (232.0 * 53)))
     assert bench.path_roofline({}, (1, 63, 64), 60, 7.6e5, "fp64", PEAKS, 3) is None
     assert bench.path_roofline({}, (2, 255, 1024), 53, 1.0, "mixed", {}, 3) is None  # no peaks
+
+
+def test_cpu_single_thread_baseline_and_thread_restore():
+    import oracle
+    import synthetic as S
+    p = S.heat2d_uniform(31, 8)
+    cores = oracle.max_threads()
+    out = bench.cpu_single_thread(p, S.source(p, steps=2), "cholesky", cores)
+    assert out["cores"] == 1 and out["value"] > 0
+    assert oracle.max_threads() == cores
