@@ -65,6 +65,11 @@ def parse():
                          "to the continuous-batching server (finished solves replaced at once)")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per arrival rate")
     ap.add_argument("--rates", default="0.5,0.9,1.1", help="serve: arrival rates as fractions of capacity")
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--no-3d", action="store_true", help="leave out the 3-D entry")
+    ap.add_argument("--batch-sample", type=int, default=64,
+                    help="problems of the batch distribution in the default line's batch entry (0: none)")
+    ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -277,39 +282,128 @@ def traffic_table():
     return table
 
 
-def cpu_sample(prob, seconds, f=None):
-    """Oracle implicit Euler on the first k steps of the workload; returns (dofs/s, k, secs, cores)."""
+def r4(x):
+    """x rounded to 4 significant digits (keeps the JSON line short)."""
+    if isinstance(x, bool) or not isinstance(x, float) or x == 0.0 or not math.isfinite(x):
+        return x
+    return float("%.4g" % x)
+
+
+def compact(d):
+    """A copy of dict d with its float values rounded by r4 (nested dicts too)."""
+    if not isinstance(d, dict):
+        return d
+    return {k: (compact(v) if isinstance(v, dict) else r4(v)) for k, v in d.items()}
+
+
+# ---- the CPU leg: the oracle on a bounded sample, in a fresh process --------------------------
+
+def workload_problem(name):
+    """The synthetic problem of a named workload (shared by the GPU arm and the CPU leg)."""
+    if name == "heat1d":
+        return S.heat1d_mms(63, 64)
+    if name == "heat3d":
+        return S.heat3d_bumps(127, 256)
+    if name.startswith("batch"):
+        return S.batch_problem(int(name[5:]))
+    if name.startswith("heat2d"):
+        n, N = (int(v) for v in name[6:].split("x")) if "x" in name else (255, 1024)
+        return S.heat2d_uniform(n, N)
+    raise ValueError(name)
+
+
+def cpu_leg_main(spec):
+    """Child-process body of the CPU leg: the oracle (sequential implicit Euler) on the first k steps
+    of the workload, k chosen for about `seconds` of work (at most `max_steps`); the steps are
+    written to `out` for the parity check and the timing is printed as one JSON line.  The child
+    imports neither torch nor the CUDA library, as the reference arm does not."""
     import oracle
     oracle.build()
+    prob = workload_problem(spec["workload"])
     cores = oracle.max_threads()
-    if f is None:
-        f = S.source(prob, steps=min(prob.N, 64))
-    method = "cg" if prob.dim == 3 else "cholesky"  # the 3-D band is too wide to factor
+    kmax = int(min(prob.N, spec.get("max_steps", prob.N)))
+    f = S.source(prob, steps=kmax)
     u0 = S.initial(prob)
+    method = "cg" if prob.dim == 3 else "cholesky"  # the 3-D band is too wide to factor
     t0 = time.perf_counter()
     oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, steps=1, method=method)
     one = time.perf_counter() - t0
-    k = int(max(1, min(f.shape[0], seconds / max(one, 1e-3))))
+    k = int(max(1, min(kmax, spec["seconds"] / max(one, 1e-4))))
     t0 = time.perf_counter()
-    oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, steps=k, method=method)
+    u = oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, steps=k, method=method)
     secs = time.perf_counter() - t0
-    return k * prob.ns / secs, k, secs, cores, method
-
-
-def cpu_single_thread(prob, f, method, cores):
-    """The oracle on one host thread: DOFs/s of its first step (then all cores again)."""
-    import oracle
-    try:
-        u0 = S.initial(prob)
+    np.save(spec["out"], u)
+    res = {"value": k * prob.ns / secs, "k": k, "secs": secs, "cores": cores, "method": method}
+    if spec.get("single_thread"):
         t0 = time.perf_counter()
         oracle.implicit_euler(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, steps=1, method=method,
                               threads=1)
-        secs = time.perf_counter() - t0
-        return {"value": prob.ns / secs, "unit": "DOF/s", "cores": 1, "sample": "first step (%.2f s)" % secs}
-    except Exception:
-        return None
+        st = time.perf_counter() - t0
+        res["single_thread"] = {"value": prob.ns / st, "cores": 1, "sample": "first step (%.2f s)" % st}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+def cpu_leg(workload, seconds, max_steps, single_thread=False):
+    """Run the CPU leg in a fresh interpreter; returns (timing dict, oracle steps [k][ns]), or
+    (None, None) when it fails (the CPU leg is a reported baseline, not the measurement)."""
+    import tempfile
+    fd, out = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    spec = {"workload": workload, "seconds": seconds, "max_steps": max_steps, "out": out,
+            "single_thread": single_thread}
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", json.dumps(spec)],
+                           capture_output=True, text=True, timeout=900, cwd=ROOT)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            sys.stderr.write("cpu leg %s failed:\n%s\n" % (workload, r.stderr[-2000:]))
+            return None, None
+        return json.loads(lines[-1]), np.load(out)
+    except Exception as exc:
+        sys.stderr.write("cpu leg %s failed: %s\n" % (workload, exc))
+        return None, None
     finally:
-        oracle.implicit_euler(prob.dim, [1] * prob.dim, 1, prob.T, prob.coeff, np.zeros(1), None, threads=cores)
+        try:
+            os.remove(out)
+        except OSError:
+            pass
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cpu_baseline_entry(res, prob):
+    if res is None:
+        return None
+    out = {"value": res["value"], "unit": "DOF/s", "cores": res["cores"], "kind": "oracle",
+           "sample": "first %d of %d implicit-Euler steps, %s per step (%.1f s), in a fresh process"
+                     % (res["k"], prob.N, "banded Cholesky" if res["method"] == "cholesky" else "CG to 1e-14",
+                        res["secs"])}
+    if "single_thread" in res:
+        out["single_thread"] = dict(res["single_thread"], unit="DOF/s")
+    return out
+
+
+def spatial_solver_label(dim, solver, h_solver):
+    if solver == "exact":
+        return "exact tridiagonal solves (A~_n and H_k)"
+    a = "A~_n: one V(1,1) geometric-multigrid cycle per step; "
+    if h_solver == "vcycle":
+        return a + "H_k: two V(1,1) cycles per frequency"
+    if dim == 2:
+        return a + ("H_k: exact, spatial DST-I in x and tridiagonal eliminations in y (FP64), "
+                    "DST-I in x and y (FP32)")
+    return a + "H_k: exact, spatial DST-I along every axis"
+
+
+def headline_config(prob, tol, omega, ws, precision="fp64", solver="mg"):
+    return {"workload": WORKLOAD, "grid": list(prob.n), "precision": precision, "N_t": prob.N, "T": prob.T,
+            "dofs_per_gpu": prob.dofs, "tol": tol, "omega": omega,
+            "spatial_solver": spatial_solver_label(prob.dim, solver, "auto"),
+            "l2": "inputs larger than L2 (%d MB per space-time vector)" % (prob.dofs * 8 >> 20),
+            "parallelism": "replicas" if ws > 1 else "single"}
 
 
 def run_reference(args, rank, ws, dist):
@@ -332,8 +426,7 @@ def run_reference(args, rank, ws, dist):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [prob.n[0]] * 2, "N_t": prob.N,
-                                        "tol": args.tol},
+        "data": "synthetic", "config": headline_config(prob, args.tol, args.omega, ws),
         "cpu_baseline": {"kind": "oracle", "value": value, "unit": "DOF/s", "cores": cores,
                          "sample": "%d implicit-Euler steps (banded Cholesky, 255^2) per timed step"
                                    % per_step},
@@ -341,6 +434,7 @@ def run_reference(args, rank, ws, dist):
     }
     print(json.dumps(line), flush=True)
     return 0
+
 
 
 def make_batch_problem(ptu, p, precision="mixed"):
@@ -499,8 +593,62 @@ def local_rank():
     return int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def solve_timed(P, count, tol, max_it):
+    """`count` solves from zero, CUDA events on the current stream; (ms per solve, iterations)."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    its = []
+    for _ in range(count):
+        st, it, hist = P.solve(tol, max_it)
+        if st != 0:
+            raise RuntimeError("solve did not converge: status %d after %d iterations" % (st, it))
+        its.append(it)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / count, its[-1]
+
+
+def kernel_profile(ptu, P, count, tol, max_it):
+    """Per-kernel totals of `count` solves with an event pair around every kernel (graphs off)."""
+    import torch
+    ptu.profile_reset()
+    ptu.profile_enable(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(count):
+        P.solve(tol, max_it)
+    e1.record()
+    torch.cuda.synchronize()
+    ptu.profile_enable(False)
+    return ptu.profile_totals(), e0.elapsed_time(e1) / count
+
+
+def dominant_roofline(prof, fp64, dims, peaks, peak_src, tr, short=False):
+    if not prof:
+        return None
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0]
+    roof = roofline_of(prof, dom, fp64, dims, peaks, peak_src, tr)
+    if short:
+        roof = {k: roof[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "share")}
+    return compact(roof)
+
+
+def secondary(value, ms, it, rel, ksteps, roof, **extra):
+    out = {"value": value, "unit": "DOF/s", "ms_per_solve": ms, "iterations": it,
+           "rel_l2_vs_oracle": rel, "oracle_steps": ksteps}
+    out.update(extra)
+    if roof is not None:
+        out["roofline"] = roof
+    return compact(out)
+
+
 def main():
     args = parse()
+    if args.cpu_leg:
+        return cpu_leg_main(json.loads(args.cpu_leg))
     rank, ws, local, dist = dist_init(args)
     if args.impl == "reference":
         return run_reference(args, rank, ws, dist)
@@ -518,85 +666,50 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    if args.workload == "heat1d":
-        prob = S.heat1d_mms(63, 64)
-        solver, base_prec = "exact", "fp64"
-    elif args.workload == "heat3d":
-        prob = S.heat3d_bumps(127, 256)
-        solver, base_prec = "mg", "mixed"  # the 3-D workload is specified in mixed precision
-    else:
-        prob = S.heat2d_uniform(args.n, args.nt)
-        solver, base_prec = "mg", "fp64"
-    if args.precision:
-        base_prec = args.precision
-    global WORKLOAD
-    WORKLOAD = {"heat1d": "heat1d_fd3_63_Nt64_T1_fp64_exact", "heat3d": "heat3d_fd7_127^3_Nt256_T2",
-                "heat2d": WORKLOAD}[args.workload]
-    dofs = prob.dofs
-    f = S.source(prob)
-    u0 = S.initial(prob)
-    P = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision=base_prec,
-                    omega=args.omega, solver=solver)
-    variant = "fp64" if base_prec == "mixed" else "mixed"
-
-    def solve_once(Pr):
-        st, it, hist = Pr.solve(args.tol, args.max_it)
-        if st != 0:
-            raise RuntimeError("solve did not converge: status %d after %d iterations" % (st, it))
-        return it, hist[-1]
-
-    for _ in range(args.warmup):
-        iters, res = solve_once(P)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
+    # the metric's workload (2-D, FP64); --workload / --precision / --n / --nt select another one for
+    # profiling runs, which then report that workload alone
+    global WORKLOAD
+    wl = args.workload
+    prec = args.precision or ("mixed" if wl == "heat3d" else "fp64")
+    solver = "exact" if wl == "heat1d" else "mg"
+    prob = workload_problem("heat2d%dx%d" % (args.n, args.nt) if wl == "heat2d" else wl)
+    if (wl, prec, args.n, args.nt) != ("heat2d", "fp64", 255, 1024):
+        WORKLOAD = "%s_%s_%s" % (wl, "x".join(str(v) for v in prob.n) + "_Nt%d" % prob.N, prec)
+        args.no_extras, args.no_mixed = True, True
+    dims = (prob.dim, prob.n[0], prob.N)
+    dofs = prob.dofs
+    f = S.source(prob)
+    u0 = S.initial(prob)
+    P = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision=prec, omega=args.omega,
+                    solver=solver)
+    for _ in range(args.warmup):
+        st, it, _ = P.solve(args.tol, args.max_it)
+        if st != 0:
+            raise RuntimeError("solve did not converge: status %d" % st)
+
+    # ---- the timed region: K complete solves with F resident in HBM ----
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ptu.launch_count()
     barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    its = []
-    for _ in range(args.steps):
-        it, res = solve_once(P)
-        its.append(it)
-    ev1.record()
-    torch.cuda.synchronize()
+    ms, iters = solve_timed(P, args.steps, args.tol, args.max_it)
     barrier()
-    ms = ev0.elapsed_time(ev1)
     launches = ptu.launch_count() - launches0
     clk = clocks.stop()
-    # the same steps again with a CUDA event pair around every kernel (graphs off): per-kernel
-    # times for the breakdown and the roofline (the value above is measured without them)
-    ptu.profile_reset()
-    ptu.profile_enable(True)
-    torch.cuda.synchronize()
-    e0p, e1p = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0p.record()
-    for _ in range(args.steps):
-        solve_once(P)
-    e1p.record()
-    torch.cuda.synchronize()
-    ms_prof = e0p.elapsed_time(e1p)
-    ptu.profile_enable(False)
-    prof = ptu.profile_totals()
     ms = max_over_ranks(ms, dist)
-    value = ws * dofs * args.steps / (ms / 1e3)
+    value = ws * dofs / (ms / 1e3)
 
-    # roofline of the dominant kernel (largest share of the timed region): FP64-pipe bound for the
-    # FP64 kernels of the FP64 path, HBM bound otherwise
+    # per-kernel event timings of a few more solves (graphs off): breakdown and roofline
     peaks, peak_src = load_peaks()
     tr = traffic_table()
-    dims = (prob.dim, prob.n[0], prob.N)
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
-    roof = roofline_of(prof, dom, base_prec == "fp64", dims, peaks, peak_src, tr) if dom else None
-    phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                  "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
+    prof, ms_prof = kernel_profile(ptu, P, min(args.steps, 5), args.tol, args.max_it)
+    roof = dominant_roofline(prof, prec == "fp64", dims, peaks, peak_src, tr)
+    phases = {k: [r4(v["ms"] / min(args.steps, 5)), v["launches"] // min(args.steps, 5)]
               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
     # end to end through the C ABI: pinned host source in, solution out, every step
@@ -621,124 +734,166 @@ def main():
     else:
         u64 = np.zeros((prob.N, prob.ns))
         P.solve(args.tol, args.max_it, u_out=u64)
-
-    # the other precision on the same workload (mixed for the FP64 workloads, FP64 for the 3-D one)
-    mixed = None
-    if not args.no_mixed:
-        Pm = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision=variant,
-                         omega=args.omega, solver=solver)
-        vsteps = args.steps if variant == "mixed" else 1
-        if variant == "mixed":
-            solve_once(Pm)
-        barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        mits = []
-        for _ in range(vsteps):
-            it, res = solve_once(Pm)
-            mits.append(it)
-        e1.record()
-        torch.cuda.synchronize()
-        mms = e0.elapsed_time(e1)
-        # per-kernel breakdown from one more solve with kernel events
-        ptu.profile_reset()
-        ptu.profile_enable(True)
-        solve_once(Pm)
-        torch.cuda.synchronize()
-        ptu.profile_enable(False)
-        vprof = ptu.profile_totals()
-        um = np.zeros((prob.N, prob.ns))
-        Pm.solve(args.tol, args.max_it, u_out=um)
-        Pm.close()
-        mms = max_over_ranks(mms, dist)
-        vdom = max(vprof.items(), key=lambda kv: kv[1]["ms"])[0] if vprof else None
-        mixed = {"precision": variant, "value": ws * dofs * vsteps / (mms / 1e3), "unit": "DOF/s",
-                 "roofline": roofline_of(vprof, vdom, variant == "fp64", dims, peaks, peak_src, tr)
-                 if vdom else None,
-                 "ms_per_step": mms / vsteps, "iterations": mits[-1],
-                 "rel_l2_mixed_vs_fp64_path": float(np.linalg.norm(um - u64) / np.linalg.norm(u64)),
-                 "kernels": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"],
-                                 "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
-                             for k, v in sorted(vprof.items(), key=lambda kv: -kv[1]["ms"])}}
     P.close()
+    k2 = min(args.steps, 3)  # timed solves of the secondary entries (after one warm-up solve)
 
-    # the Krylov-accelerated form (flexible GMRES(10) preconditioned by one Uzawa step), FP64 2-D
-    krylov = None
-    if not args.no_mixed and base_prec == "fp64" and prob.dim == 2:
+    extras = {}
+    if not args.no_extras:
+        # the Krylov-accelerated form (flexible GMRES(10) preconditioned by one Uzawa step), FP64
         Pk = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision="fp64",
-                         omega=args.omega, solver=solver, krylov=10)
-        solve_once(Pk)
-        torch.cuda.synchronize()
-        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k0.record()
-        kits = []
-        for _ in range(args.steps):
-            it, res = solve_once(Pk)
-            kits.append(it)
-        k1.record()
-        torch.cuda.synchronize()
-        kms = max_over_ranks(k0.elapsed_time(k1), dist)
+                         omega=args.omega, krylov=10)
+        Pk.solve(args.tol, args.max_it)
+        kms, kit = solve_timed(Pk, k2, args.tol, args.max_it)
         uk = np.zeros((prob.N, prob.ns))
         Pk.solve(args.tol, args.max_it, u_out=uk)
         Pk.close()
-        krylov = {"solver": "FGMRES(10), right preconditioner: one inexact Uzawa step",
-                  "value": ws * dofs * args.steps / (kms / 1e3), "unit": "DOF/s", "ms_per_step": kms / args.steps,
-                  "iterations": kits[-1],
-                  "rel_l2_vs_uzawa_solution": float(np.linalg.norm(uk - u64) / np.linalg.norm(u64))}
-
-    # the same workload on quasi-uniform random time steps (ratio <= 1.5, §2 eq. 2.1-2.2), FP64
-    nonuniform = None
-    if not args.no_mixed and base_prec == "fp64" and prob.dim == 2:
+        extras["krylov"] = compact({"solver": "FGMRES(10), right preconditioner: one inexact Uzawa step",
+                                    "value": dofs / (kms / 1e3), "ms_per_solve": kms, "iterations": kit,
+                                    "rel_l2_vs_uzawa_solution": rel_l2(uk, u64)})
+        # quasi-uniform random time steps (ratio <= 1.5, eq. 2.1-2.2), FP64
         taus = S.random_steps(prob.N, prob.T, 1, 0.5)
-        Pn = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision="fp64", solver=solver,
-                         taus=taus)
-        solve_once(Pn)
-        torch.cuda.synchronize()
-        n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n0.record()
-        nits = []
-        for _ in range(args.steps):
-            it, res = solve_once(Pn)
-            nits.append(it)
-        n1.record()
-        torch.cuda.synchronize()
-        nms = max_over_ranks(n0.elapsed_time(n1), dist)
+        Pn = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision="fp64", taus=taus)
+        Pn.solve(args.tol, args.max_it)
+        nms, nit = solve_timed(Pn, k2, args.tol, args.max_it)
         Pn.close()
-        nonuniform = {"steps": "tau_n = T w_n / sum w, w_n = 1 + 0.5 U_n (SplitMix64 seed 1), max/min %.3f"
-                               % (taus.max() / taus.min()),
-                      "omega": "default: 1.5 / (1 + alpha), alpha of eq. 2.2 with the step ratios",
-                      "h_solver": "exact, by spatial sine transforms (reference: the time-mean coefficient)",
-                      "value": ws * dofs * args.steps / (nms / 1e3), "unit": "DOF/s",
-                      "ms_per_step": nms / args.steps, "iterations": nits[-1]}
+        extras["nonuniform_steps"] = compact({
+            "steps": "tau_n = T w_n / sum w, w_n = 1 + 0.5 U_n (SplitMix64 seed 1), max/min %.3f"
+                     % (taus.max() / taus.min()),
+            "omega": "1.5 / (1 + alpha), alpha of eq. 2.2 with the step ratios",
+            "value": dofs / (nms / 1e3), "ms_per_solve": nms, "iterations": nit})
 
+    # the CPU leg of the headline workload (oracle on its first steps, in a fresh process)
     cpu = None
+    rel64 = None
+    ref2 = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, k, secs, cores, method = cpu_sample(prob, args.cpu_seconds, f[:64])
-        cpu = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle",
-               "sample": "first %d of %d implicit-Euler steps, %s per step (%.1f s)"
-                         % (k, prob.N, "banded Cholesky" if method == "cholesky" else "CG to 1e-14", secs),
-               "single_thread": cpu_single_thread(prob, f[:64], method, cores)}
+        res2, ref2 = cpu_leg("heat2d%dx%d" % (args.n, args.nt) if wl == "heat2d" else wl, args.cpu_seconds,
+                             64 if prob.dim < 3 else 1, single_thread=prob.dim < 3)
+        cpu = cpu_baseline_entry(res2, prob)
+        if ref2 is not None:
+            rel64 = rel_l2(u64[:ref2.shape[0]], ref2)
+
+    tail = {}
+    if not args.no_extras and rank == 0:
+        # the benchmark spec's GMG-only form: two V-cycles per H_k solve instead of the transform solves
+        Pv = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision="fp64", omega=args.omega,
+                         h_solver="vcycle")
+        Pv.solve(args.tol, args.max_it)
+        vms, vit = solve_timed(Pv, k2, args.tol, args.max_it)
+        vprof, _ = kernel_profile(ptu, Pv, 1, args.tol, args.max_it)
+        uv = np.zeros((prob.N, prob.ns))
+        Pv.solve(args.tol, args.max_it, u_out=uv)
+        Pv.close()
+        tail["vcycle_h"] = secondary(dofs / (vms / 1e3), vms, vit,
+                                     rel_l2(uv[:ref2.shape[0]], ref2) if ref2 is not None else None,
+                                     ref2.shape[0] if ref2 is not None else None,
+                                     dominant_roofline(vprof, True, dims, peaks, peak_src, tr, short=True),
+                                     precision="fp64")
+        del uv
+
+        # config 1: 1-D, 63 points, 64 steps, exact tridiagonal solves, FP64
+        p1 = workload_problem("heat1d")
+        P1 = ptu.Problem(p1.dim, p1.n, p1.N, p1.T, p1.coeff, S.source(p1), S.initial(p1), precision="fp64",
+                         omega=args.omega, solver="exact")
+        for _ in range(3):
+            P1.solve(args.tol, args.max_it)
+        ms1, it1 = solve_timed(P1, 20, args.tol, args.max_it)
+        u1 = np.zeros((p1.N, p1.ns))
+        P1.solve(args.tol, args.max_it, u_out=u1)
+        P1.close()
+        r1, ref1 = cpu_leg("heat1d", 5.0, p1.N) if not args.no_cpu else (None, None)
+        tail["heat1d"] = secondary(p1.dofs / (ms1 / 1e3), ms1, it1,
+                                   rel_l2(u1[:ref1.shape[0]], ref1) if ref1 is not None else None,
+                                   ref1.shape[0] if ref1 is not None else None, None, precision="fp64",
+                                   cpu_dofs_per_s=r1["value"] if r1 else None)
+
+        # reduced batch (config 4 distribution, problems 0..B-1), mixed, one pt_solve_batch
+        nb = args.batch_sample
+        if nb > 0:
+            bprobs = [S.batch_problem(i) for i in range(nb)]
+            small = sorted(bprobs, key=lambda q: q.dofs)[:4]
+            Ps = [make_batch_problem(ptu, q) for q in small]
+            ptu.solve_batch(Ps, args.tol, args.max_it)
+            for Q in Ps:
+                Q.close()
+            Ps = [make_batch_problem(ptu, q) for q in bprobs]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bits, bsts = ptu.solve_batch(Ps, args.tol, args.max_it)
+            torch.cuda.synchronize()
+            bsec = time.perf_counter() - t0
+            # the parity sample: the largest problem of the batch, against the oracle's first steps
+            js = max(range(nb), key=lambda i: bprobs[i].dofs)
+            us = np.zeros((bprobs[js].N, bprobs[js].ns))
+            Ps[js].get_state(u_out=us)
+            for Q in Ps:
+                Q.close()
+            rb, refb = cpu_leg("batch%d" % js, 8.0, 256) if not args.no_cpu else (None, None)
+            tail["batch"] = secondary(sum(q.dofs for q in bprobs) / bsec, 1e3 * bsec, float(np.mean(bits)),
+                                      rel_l2(us[:refb.shape[0]], refb) if refb is not None else None,
+                                      refb.shape[0] if refb is not None else None, None, precision="mixed",
+                                      problems=nb, iterations_max=int(max(bits)),
+                                      converged=int(sum(1 for x in bsts if x == 0)),
+                                      sample="problem %d (%dx%d, N_t %d)" % (js, bprobs[js].n[0], bprobs[js].n[1],
+                                                                              bprobs[js].N))
+
+        # config 3: 3-D 127^3 x 256, mixed precision (FP32 preconditioner, FP64 refinement)
+        if not args.no_3d:
+            p3 = workload_problem("heat3d")
+            f3 = S.source(p3)
+            P3 = ptu.Problem(p3.dim, p3.n, p3.N, p3.T, p3.coeff, f3, S.initial(p3), precision="mixed",
+                             omega=args.omega)
+            del f3
+            P3.solve(args.tol, args.max_it)
+            ms3, it3 = solve_timed(P3, k2, args.tol, args.max_it)
+            prof3, _ = kernel_profile(ptu, P3, 1, args.tol, args.max_it)
+            u3 = np.zeros((p3.N, p3.ns))
+            P3.solve(args.tol, args.max_it, u_out=u3)
+            P3.close()
+            u3 = u3[:4].copy()
+            r3, ref3 = cpu_leg("heat3d", 1.0, 1) if not args.no_cpu else (None, None)
+            tail["heat3d"] = secondary(p3.dofs / (ms3 / 1e3), ms3, it3,
+                                       rel_l2(u3[:ref3.shape[0]], ref3) if ref3 is not None else None,
+                                       ref3.shape[0] if ref3 is not None else None,
+                                       dominant_roofline(prof3, False, (3, p3.n[0], p3.N), peaks, peak_src, tr,
+                                                         short=True),
+                                       precision="mixed", cpu_dofs_per_s=r3["value"] if r3 else None)
+
+    # config 2 in mixed precision (FP32 preconditioner and sweeps, FP64 refinement): the last key
+    if not args.no_mixed:
+        Pm = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision="mixed", omega=args.omega)
+        Pm.solve(args.tol, args.max_it)
+        barrier()
+        mms, mit = solve_timed(Pm, min(args.steps, 10), args.tol, args.max_it)
+        mms = max_over_ranks(mms, dist)
+        mprof, _ = kernel_profile(ptu, Pm, 1, args.tol, args.max_it)
+        um = np.zeros((prob.N, prob.ns))
+        Pm.solve(args.tol, args.max_it, u_out=um)
+        Pm.close()
+        tail["mixed"] = secondary(ws * dofs / (mms / 1e3), mms, mit,
+                                  rel_l2(um[:ref2.shape[0]], ref2) if ref2 is not None else None,
+                                  ref2.shape[0] if ref2 is not None else None,
+                                  dominant_roofline(mprof, False, dims, peaks, peak_src, tr, short=True),
+                                  precision="mixed", rel_l2_vs_fp64_path=rel_l2(um, u64),
+                                  speedup_vs_fp64=ms / mms,
+                                  kernels={k: r4(v["ms"]) for k, v in
+                                           sorted(mprof.items(), key=lambda kv: -kv[1]["ms"])[:8]})
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if base_prec == "fp64" else "f64+f32",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": list(prob.n), "precision": base_prec, "N_t": prob.N, "T": prob.T,
-                       "dofs_per_gpu": dofs, "tol": args.tol, "omega": args.omega,
-                       "iterations": its[-1],
-                       "spatial_solver": "exact tridiagonal" if solver == "exact"
-                       else "V(1,1) geometric multigrid (1 cycle per A_n solve, 2 per H_k solve)",
-                       "l2": "inputs larger than L2 (533 MB per space-time vector)",
-                       "parallelism": "replicas" if ws > 1 else "single"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "path_roofline": path_roofline(prof, dims, its[-1], value, base_prec, peaks, args.steps),
-            "ms_per_step_with_kernel_events": ms_prof / args.steps,
-            "clocks": clk, ("fp64_path" if variant == "fp64" else "mixed"): mixed, "krylov": krylov,
-            "nonuniform_steps": nonuniform,
-            "kernels": phases,
+            "config": dict(headline_config(prob, args.tol, args.omega, ws, prec, solver), iterations=iters),
+            "gpu_launches": int(launches), "clocks": clk,
+            "ms_per_step_with_kernel_events": ms_prof,
+            "kernels_ms_launches_per_solve": phases,
+            "path_roofline": compact(path_roofline(prof, dims, iters, value, prec, peaks, min(args.steps, 5))),
+            **extras,
+            "e2e": e2e, "cpu_baseline": compact(cpu), "rel_l2_vs_oracle": r4(rel64),
+            "oracle_steps": None if ref2 is None else int(ref2.shape[0]), "roofline": roof,
+            **tail,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -243,11 +243,13 @@ pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev);
  * out_k = sum_n r_n sin((2k-1) n pi / (2N)) for each of `ncols` columns: the same transform as
  * pt_dst_forward, on caller-owned device arrays r_dev and out_dev of layout [N_t][ncols]
  * (FP64), without a pt_problem and without allocating anything.  Its working memory is one
- * file-scope device array of 16.2 MiB that every GPU loading this library reserves until the
- * process exits; limits: N_t a power of two <= 8192 and N_t * ceil32(ncols) <= 2^21 (else
- * PT_EINVAL with a message naming the limit).  The first call on each device looks up that
- * array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array, which keeps the last call's contents (each call rewrites
+ * file-scope device array of 16.2 MiB, reserved on a device when the library's device code is
+ * loaded there (under CUDA's lazy module loading: at the first call on that device) and kept
+ * until the process exits; limits: N_t a power of two <= 8192 and N_t * ceil32(ncols) <= 2^21
+ * (else PT_EINVAL with a message naming the limit).  The first call on each device looks up
+ * that array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The address stays valid for the life of the device's context: do not call this
+ * entry point on a device after cudaDeviceReset.  All calls share the array, which keeps the last call's contents (each call rewrites
  * the tables and the padded copy of its input before using them), so calls whose work
  * overlaps on the GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  Work is ordered on `stream` (NULL = legacy default stream); the

@@ -566,7 +566,15 @@ pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* r
   const bool small = total < (1LL << 22);
   int check = p->opt.check_every;
   if (check <= 0) check = small ? 8 : 1;
-  const bool graphs = !p->opt.no_graphs && !profiling_enabled();
+  const bool profiling = profiling_enabled();
+  const bool graphs = !p->opt.no_graphs && !profiling;
+  // kernels timed one by one: poll every iteration so that the scopes of the refinement kernels
+  // know which kind of iteration comes next (the first one is the FP64 step, j = 0)
+  if (profiling) check = 1;
+  struct StepKindReset {
+    ~StepKindReset() { set_step_kind(kAnyStep); }
+  } reset_kind;
+  if (profiling && p->mixed) set_step_kind(kOuterStep);
   const int per_launch = graphs ? std::min(check, graph_iterations(p)) : 1;
   if (graphs && (st = ensure_graph(p, per_launch)) != PT_OK) return st;
   long long launched = 0, since_poll = 0;
@@ -585,6 +593,7 @@ pt_status uzawa(pt_problem* p, double tol, int max_it, int* iters_out, double* r
       SolveState hs;
       if ((st = read_state(p, &hs)) != PT_OK) return st;
       if (hs.done == 1) break;
+      if (profiling && p->mixed) set_step_kind((hs.done == 2 || hs.j % kOuter == 0) ? kOuterStep : kInnerStep);
       // (the mixed form may take one extra launch: the FP64 step that confirms the last estimate)
       if (launched > (long long)max_it + 2 * per_launch + 2) return fail(PT_ECUDA, "solver did not stop at max_it");
     }

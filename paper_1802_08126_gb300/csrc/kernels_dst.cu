@@ -517,31 +517,24 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
   const int L = plan_stride(plan);
   const int C = plan.C > 0 ? plan.C : dst_cols<T>(L, S);
   const size_t smem = (size_t)C * L * sizeof(T2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_dst_forward<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_dst_forward<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
   const int blocks = (int)(S / (2 * C));
   const ColGeom cg{dim, n, logP};
   double interior = plan.N;
   for (int d = 0; d < dim; ++d) interior *= n;
   LaunchScope ls("dst_forward", st, 2.0 * sizeof(T) * interior);
   if (stockham_ok(plan)) {
-    static bool attr_s = false;
-    if (!attr_s) {
-      cudaFuncSetAttribute(k_dst_forward_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_s = true;
-    }
+    set_smem_limit((const void*)k_dst_forward_s<T>, 200 * 1024);
     const int F = stockham_cols(plan, S);
     const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
     const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2);
     k_dst_forward_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(x, S, cg, plan, F, done);
-  } else if (plan.M > 0)
+  } else if (plan.M > 0) {
+    set_smem_limit((const void*)k_dst_forward<T, true>, 200 * 1024);
     k_dst_forward<T, true><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
-  else
+  } else {
+    set_smem_limit((const void*)k_dst_forward<T, false>, 200 * 1024);
     k_dst_forward<T, false><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
+  }
 }
 
 template <typename T>
@@ -551,12 +544,6 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
   const int L = plan_stride(plan);
   const int C = plan.C > 0 ? plan.C : dst_cols<T>(L, S);
   const size_t smem = (size_t)C * L * sizeof(T2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_dst_inverse<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_dst_inverse<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
   const int blocks = (int)(S / (2 * C));
   const ColGeom cg{dim, n, logP};
   double interior = plan.N;
@@ -564,20 +551,19 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
   LaunchScope ls("dst_inverse", st,
                  (sizeof(T) + (mode == 1 ? 16.0 : mode == 2 ? 2.0 * sizeof(T) : (double)sizeof(T))) * interior);
   if (stockham_ok(plan)) {
-    static bool attr_s = false;
-    if (!attr_s) {
-      cudaFuncSetAttribute(k_dst_inverse_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_s = true;
-    }
+    set_smem_limit((const void*)k_dst_inverse_s<T>, 200 * 1024);
     const int F = stockham_cols(plan, S);
     const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
     const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2) +
                       (mode == 2 && sizeof(T2) == 8 ? (size_t)F * plan.N * sizeof(T2) : 0);
     k_dst_inverse_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(y, out, mode, omega, S, cg, plan, F, done);
-  } else if (plan.M > 0)
+  } else if (plan.M > 0) {
+    set_smem_limit((const void*)k_dst_inverse<T, true>, 200 * 1024);
     k_dst_inverse<T, true><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);
-  else
+  } else {
+    set_smem_limit((const void*)k_dst_inverse<T, false>, 200 * 1024);
     k_dst_inverse<T, false><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);
+  }
 }
 
 // Forward transform of `ncols` packed columns held at pitch S (S a multiple of 32, columns
@@ -587,11 +573,7 @@ void launch_dst_forward_plain(double* x, long long S, int ncols, DstPlan<double>
   const int L = plan.N + 1;
   const int C = dst_cols<double>(L, S);
   const size_t smem = (size_t)C * L * sizeof(double2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_dst_forward<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  set_smem_limit((const void*)k_dst_forward<double, false>, 200 * 1024);
   int logP = 0;
   while ((1LL << logP) <= S) ++logP;  // pitch above every column index: only column ncols is "ghost"
   const ColGeom cg{1, ncols, logP};

@@ -286,13 +286,8 @@ void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const 
   double d = B;
   for (int k = 0; k < dim; ++k) d *= n;
   LaunchScope ls("dsti_rows", st, 2.0 * sizeof(T) * d);
-  // (every length's kernel has the same pointer type: the attribute flag is kept per length)
-  static bool attr[32] = {};
   auto go = [&](auto kern) {
-    if (!attr[logP]) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-      attr[logP] = true;
-    }
+    set_smem_limit((const void*)kern, 210 * 1024);
     kern<<<(unsigned)blocks, wpb * 32, smem, st>>>(x, logP, dim, npairs, tabs<T>(tw, sn, nullptr));
   };
   // (the run-time-length kernel: unrolling the row transform raises its register count past
@@ -313,12 +308,8 @@ void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int ax
   double d = B;
   for (int k = 0; k < dim; ++k) d *= n;
   LaunchScope ls(scale ? "dsti_cols_scale" : "dsti_cols", st, 2.0 * sizeof(T) * d);
-  static bool attr[32] = {};
   auto go = [&](auto kern) {
-    if (!attr[logP]) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-      attr[logP] = true;
-    }
+    set_smem_limit((const void*)kern, 210 * 1024);
     kern<<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, tabs<T>(tw, sn, gtab));
   };
   // FP32: compile-time lengths (instruction-bound, the unrolled form measured 11 % faster);

@@ -203,7 +203,7 @@ void launch_ir_begin(SolveState* st, int kouter, cudaStream_t s) {
 
 void launch_ir_fold(double* u, double* p, float* du, float* dp, long long total, const SolveState* st,
                     cudaStream_t s) {
-  LaunchScope ls("ir_fold", s, 40.0 * (double)total);
+  LaunchScope ls("ir_fold", s, 40.0 * (double)total, 0.0, kOuterStep);
   k_ir_fold<<<grid_for(total), kThreads, 0, s>>>(u, p, du, dp, total, st);
 }
 
@@ -211,7 +211,7 @@ void launch_ir_outer(const double* u, const double* p, const double* F, float* R
                      double* partials, StencilGeom<double> g, const double* cth, Steps<double> sp, int N,
                      const SolveState* st, cudaStream_t s) {
   const long long total = g.S * N;
-  LaunchScope ls("ir_outer", s, (24.0 + 12.0) * (double)total);
+  LaunchScope ls("ir_outer", s, (24.0 + 12.0) * (double)total, 0.0, kOuterStep);
   PT_IR_DIM(g.dim, k_ir_outer<D><<<kReduceBlocks, kThreads, 0, s>>>(u, p, F, R1, R2, rp, partials, g, cth, sp, N,
                                                                     total, st));
 }
@@ -220,7 +220,7 @@ void launch_ir_inner(const float* du, const float* dp, const float* R1, const fl
                      double* partials, StencilGeom<float> g, const float* cth, Steps<float> sp, int N,
                      const SolveState* st, cudaStream_t s) {
   const long long total = g.S * N;
-  LaunchScope ls("ir_inner", s, 24.0 * (double)total);
+  LaunchScope ls("ir_inner", s, 24.0 * (double)total, 0.0, kInnerStep);
   PT_IR_DIM(g.dim, k_ir_inner<D><<<kReduceBlocks, kThreads, 0, s>>>(du, dp, R1, R2, bp, rp, partials, g, cth, sp,
                                                                     total, st));
 }

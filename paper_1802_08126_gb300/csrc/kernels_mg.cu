@@ -489,11 +489,7 @@ void coarse_launch(const MGPlan<T>& plan, OpBatch<T> op, const T* bl, void* out,
     off += 3 * (c.guard + c.S);
   }
   const size_t smem = (size_t)off * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_coarse_vcycle<DIM, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  set_smem_limit((const void*)k_coarse_vcycle<DIM, T>, 200 * 1024);
   void* dst = plan.lc == 0 ? out : plan.buf[plan.lc].x;
   const int dmode = plan.lc == 0 ? mode : 0;
   const int dfp64 = plan.lc == 0 ? out_fp64 : 0;

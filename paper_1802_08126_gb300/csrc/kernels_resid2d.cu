@@ -211,7 +211,7 @@ void launch_ir_outer_2d(const double* u, const double* p, const double* F, float
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
-  LaunchScope ls("ir_outer", s, (24.0 + 12.0) * (double)n * n * N);
+  LaunchScope ls("ir_outer", s, (24.0 + 12.0) * (double)n * n * N, 0.0, kOuterStep);
   if (sp.uniform)
     k_resid_bres_2d<float, true, false, 0><<<kReduceBlocks, 256, 0, s>>>(u, p, F, nullptr, rp, partials, tab, tabf,
                                                                          cth, s_h2 * a0, s_h2, n, logP, S, N, nwarps,
@@ -348,7 +348,7 @@ void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
-  LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * N);
+  LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * N, 0.0, kInnerStep);
   k_ir_inner_2d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
                                               (float)s_h2, n, logP, S, nwarps, sp, st);
 }
@@ -577,7 +577,7 @@ void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * P * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
-  LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * n * N);
+  LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * n * N, 0.0, kInnerStep);
   k_ir_inner_3d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
                                               (float)s_h2, n, logP, S, nwarps, sp, st);
 }
@@ -589,7 +589,7 @@ void launch_ir_outer_3d(const double* u, const double* p, const double* F, float
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * P * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
-  LaunchScope ls("ir_outer", s, 36.0 * (double)n * n * n * N);
+  LaunchScope ls("ir_outer", s, 36.0 * (double)n * n * n * N, 0.0, kOuterStep);
   k_ir_outer_3d<<<kReduceBlocks, 256, 0, s>>>(u, p, F, R1, R2, rp, partials, tab, tabf, cth, s_h2 * a0, s_h2, n,
                                               logP, S, N, nwarps, sp, st);
 }

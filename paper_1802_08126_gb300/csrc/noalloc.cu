@@ -5,8 +5,13 @@
 // GPU), or they run latency-critical loops in which a cudaMalloc, which may synchronise the
 // device, is not acceptable.  For them this entry point computes the same transform as
 // pt_dst_forward without a pt_problem and without any allocation: the working copy of the
-// input and the transform tables live in one file-scope device array of fixed size, reserved
-// when the library is loaded and held by every GPU that loads it until the process exits.
+// input and the transform tables live in one file-scope device array of fixed size.  The array
+// is reserved on a device when the library's device code is loaded there; under CUDA's default
+// lazy module loading that happens at the first call on the device (its symbol lookup), which
+// is why the first call must come before any stream capture.  The device keeps it until the
+// process exits.  The address looked up at the first call stays valid for the life of the
+// device's context: a cudaDeviceReset invalidates it (and every other device pointer the
+// caller holds), so this entry point must not be used on a device after it has been reset.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -23,7 +28,7 @@ constexpr long long kTables = 3LL * kMaxN;          // twiddles (<= N/2 complex)
 constexpr long long kScratchElems = kTables + kMaxData;
 
 // The scratch array.  In host code its name is only a host-side stand-in: the device address
-// comes from cudaGetSymbolAddress, taken once per device below.
+// comes from cudaGetSymbolAddress, taken once per device below (with that device current).
 static __device__ __align__(256) double g_noalloc_scratch[kScratchElems];
 
 constexpr int kMaxDevices = 64;

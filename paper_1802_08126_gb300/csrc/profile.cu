@@ -10,7 +10,9 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "pt_internal.cuh"
@@ -66,8 +68,25 @@ void drain_locked() {
 
 }  // namespace
 
+std::mutex g_attr_mu;
+std::set<std::pair<int, const void*>> g_attr_done;
+
+cudaError_t set_smem_limit(const void* func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_done.count({dev, func})) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) g_attr_done.insert({dev, func});
+  return e;
+}
+
 thread_local int g_capturing = 0;
 thread_local unsigned long long g_captured = 0;
+thread_local int g_step_kind = kAnyStep;
+
+void set_step_kind(int kind) { g_step_kind = kind; }
 
 void note_launch(int count) { g_launches.fetch_add((unsigned long long)count, std::memory_order_relaxed); }
 
@@ -83,8 +102,9 @@ unsigned long long capture_end() {
   return g_captured;
 }
 
-LaunchScope::LaunchScope(const char* name, cudaStream_t st, double bytes, double flops)
+LaunchScope::LaunchScope(const char* name, cudaStream_t st, double bytes, double flops, int works_on)
     : name_(name), st_(st), bytes_(bytes), flops_(flops), e0_(nullptr) {
+  if (works_on != kAnyStep && g_step_kind != kAnyStep && works_on != g_step_kind) bytes_ = flops_ = 0.0;
   if (g_capturing) {  // recorded into a graph: counted when the graph is launched
     ++g_captured;
     return;

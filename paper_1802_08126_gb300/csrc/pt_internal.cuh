@@ -26,9 +26,18 @@ constexpr int kCoarseMaxElems = 1024; // levels with P^dim <= this run inside on
 // timing is enabled, brackets it with CUDA events on its stream.  `bytes` is the algorithmic
 // traffic of the launch (every operand read once, every result written once) and `flops` its
 // FP64 arithmetic, both used for roofline figures.
+// Kernels of the mixed-precision refinement do their work only on one kind of iteration (the
+// FP64 step or the FP32 iterations between) and return at once on the other.  While kernels are
+// timed one by one, the solve loop tells the scopes which kind the next iteration is
+// (set_step_kind, per host thread), and a scope whose kernel works only on the other kind books
+// no bytes or flops for that launch (its time still counts).
+enum StepKind { kAnyStep = -1, kInnerStep = 0, kOuterStep = 1 };
+void set_step_kind(int kind);
+
 class LaunchScope {
  public:
-  LaunchScope(const char* name, cudaStream_t st, double bytes = 0.0, double flops = 0.0);
+  LaunchScope(const char* name, cudaStream_t st, double bytes = 0.0, double flops = 0.0,
+              int works_on = kAnyStep);
   ~LaunchScope();
   LaunchScope(const LaunchScope&) = delete;
   LaunchScope& operator=(const LaunchScope&) = delete;
@@ -41,6 +50,11 @@ class LaunchScope {
 };
 void note_launch(int count = 1);
 bool profiling_enabled();
+// Raise the dynamic shared-memory limit of kernel `func` to `bytes` on the current device.
+// cudaFuncSetAttribute acts per device, so the call is made once per (device, kernel) pair;
+// the record of which pairs are done is guarded by a mutex (launches may come from several
+// host threads, e.g. the serving worker and a caller).  Returns the CUDA status of the call.
+cudaError_t set_smem_limit(const void* func, int bytes);
 // Launches between capture_begin and capture_end (same thread) are recorded into a CUDA graph:
 // they are not counted as executed; capture_end returns how many were recorded.
 void capture_begin();

@@ -1,6 +1,7 @@
 """Host-side arithmetic of the benchmark's roofline entries (no GPU)."""
 import math
 
+import numpy as np
 import pytest
 
 import bench
@@ -37,11 +38,30 @@ def test_path_roofline_mixed_and_unmodelled():
     assert bench.path_roofline({}, (2, 255, 1024), 53, 1.0, "mixed", {}, 3) is None  # no peaks
 
 
-def test_cpu_single_thread_baseline_and_thread_restore():
+def test_cpu_leg_runs_the_oracle_in_a_fresh_process():
+    """The CPU leg returns the oracle's first steps of the named workload and its timing (all
+    cores, and one thread on the first step)."""
     import oracle
     import synthetic as S
+    res, u = bench.cpu_leg("heat2d31x8", 0.5, 4, single_thread=True)
+    assert res is not None and res["cores"] >= 1 and res["value"] > 0
+    assert res["single_thread"]["cores"] == 1 and res["single_thread"]["value"] > 0
+    k = res["k"]
+    assert 1 <= k <= 4 and u.shape == (k, 31 * 31)
     p = S.heat2d_uniform(31, 8)
-    cores = oracle.max_threads()
-    out = bench.cpu_single_thread(p, S.source(p, steps=2), "cholesky", cores)
-    assert out["cores"] == 1 and out["value"] > 0
-    assert oracle.max_threads() == cores
+    ref = oracle.implicit_euler(p.dim, p.n, p.N, p.T, p.coeff, S.source(p, steps=k), None, steps=k)
+    assert np.array_equal(u, ref)
+
+
+def test_workload_names_and_rounding():
+    assert bench.workload_problem("heat2d").n == [255, 255]
+    assert bench.workload_problem("heat2d63x32").N == 32
+    assert bench.workload_problem("heat3d").dim == 3
+    assert bench.workload_problem("batch7").name == S_batch_name(7)
+    assert bench.r4(123456.789) == 123500.0 and bench.r4(3) == 3 and bench.r4(None) is None
+    assert bench.compact({"a": 1.23456789, "b": {"c": 2.0000001}, "d": "x"}) == {"a": 1.235, "b": {"c": 2.0}, "d": "x"}
+
+
+def S_batch_name(i):
+    import synthetic as S
+    return S.batch_problem(i).name
