@@ -50,10 +50,10 @@ def lib():
             ip = ctypes.POINTER(ctypes.c_int)
             L.oc_implicit_euler.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.c_double,
                                             ctypes.POINTER(OcCoeff), dp, dp, dp, ctypes.c_int,
-                                            ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int]
             L.oc_implicit_euler.restype = ctypes.c_int
             L.oc_apply_B.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.c_double,
-                                     ctypes.POINTER(OcCoeff), dp, dp, ctypes.c_int, dp]
+                                     ctypes.POINTER(OcCoeff), dp, dp, ctypes.c_int, dp, ctypes.c_int]
             L.oc_apply_B.restype = None
             L.oc_apply_A.argtypes = [ctypes.c_int, ip, ctypes.c_double, ctypes.POINTER(OcCoeff),
                                      dp, dp, ctypes.c_int]
@@ -96,13 +96,18 @@ def _step_lengths(N: int, taus) -> Optional[np.ndarray]:
     return taus
 
 
+MASS = {"identity": 0, "p1": 1}
+
+
 def implicit_euler(dim: int, n: Sequence[int], N: int, T: float, coeff, f: np.ndarray,
                    u0: Optional[np.ndarray] = None, steps: Optional[int] = None,
                    method: str = "cholesky", cg_tol: float = 1e-14, threads: int = 0,
-                   taus: Optional[Sequence[float]] = None) -> np.ndarray:
+                   taus: Optional[Sequence[float]] = None, mass: str = "identity") -> np.ndarray:
     """Sequential implicit Euler (§2, eq. 2.1) for steps 1..steps; returns [steps][ns].
 
-    taus: the N step lengths tau_1..tau_N (t_n = tau_1 + ... + tau_n), or None for T/N."""
+    taus: the N step lengths tau_1..tau_N (t_n = tau_1 + ... + tau_n), or None for T/N.
+    mass: "identity" (M = I, finite differences) or "p1" (the P1 mass matrix over h^d, dim <= 2;
+    the source enters as the consistent load M f_n)."""
     steps = N if steps is None else steps
     tv = _step_lengths(N, taus)
     ns = int(np.prod(list(n)[:dim]))
@@ -114,21 +119,21 @@ def implicit_euler(dim: int, n: Sequence[int], N: int, T: float, coeff, f: np.nd
     k = _coeff(coeff)
     rc = lib().oc_implicit_euler(dim, _iarr(n), N, float(T), ctypes.byref(k), _dptr(f), _dptr(u0c),
                                  _dptr(out), steps, 0 if method == "cholesky" else 1,
-                                 float(cg_tol), int(threads), _dptr(tv))
+                                 float(cg_tol), int(threads), _dptr(tv), MASS[mass])
     if rc != 0:
         raise RuntimeError("oracle implicit Euler failed (code %d)" % rc)
     return out
 
 
 def apply_B(dim: int, n: Sequence[int], N: int, T: float, coeff, u: np.ndarray,
-            threads: int = 0, taus: Optional[Sequence[float]] = None) -> np.ndarray:
-    """B u = (K (x) I) u + diag(tau_n A_n) u, u_0 := 0 (§2, eq. 2.3-2.4); u is [N][ns]."""
+            threads: int = 0, taus: Optional[Sequence[float]] = None, mass: str = "identity") -> np.ndarray:
+    """B u = (K (x) M) u + diag(tau_n A_n) u, u_0 := 0 (§2, eq. 2.3-2.4); u is [N][ns]."""
     u = np.ascontiguousarray(u, dtype=np.float64).reshape(N, -1)
     out = np.empty_like(u)
     k = _coeff(coeff)
     tv = _step_lengths(N, taus)
     lib().oc_apply_B(dim, _iarr(n), N, float(T), ctypes.byref(k), _dptr(u), _dptr(out), int(threads),
-                     _dptr(tv))
+                     _dptr(tv), MASS[mass])
     return out
 
 

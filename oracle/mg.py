@@ -6,8 +6,9 @@ symmetric positive definite, convergent approximation of its operator (§3,
 eq. 3.3; §4, eq. 4.7).  The reading implemented here (and by the GPU path) is:
 
 * grids with n_l interior points per axis, n_{l+1} = (n_l - 1)/2, down to one point;
-* level operator L_l = sigma I + s A_l, where A_l is the finite-difference operator
-  of the same coefficient field sampled at level-l face midpoints (rediscretised);
+* level operator L_l = sigma M_l + s A_l, where A_l is the finite-difference operator
+  of the same coefficient field sampled at level-l face midpoints (rediscretised) and M_l the
+  mass matrix of the problem over h^d at level l (the identity, or the P1 stencil);
 * prolongation P = d-linear interpolation, restriction R = P^T / 2^d (full weighting);
 * V(1,1): one weighted-Jacobi sweep x <- x + w D^-1 (b - L x) before and after the
   coarse-grid correction, w = 2/3, 4/5, 6/7 for d = 1, 2, 3; exact solve on the
@@ -101,9 +102,9 @@ def st_vcycles(st, h_cycles: int = 2):
 
     Returns (Asolve, Hsolve): Asolve applies, slice n, one V-cycle for tau_n A_n
     (coefficient at t_n, step length tau_n); Hsolve(k, r) applies ``h_cycles`` steps of the V-cycle iteration
-    x <- x + V(r - H_k x) from x = 0 for H_k = mu_k I + tau Abar.
+    x <- x + V(r - H_k x) from x = 0 for H_k = mu_k M + tau Abar.
     """
-    from .spacetime import assemble_A, mu, reference_operator
+    from .spacetime import assemble_A, assemble_M, mu, reference_operator
 
     dim, n, N, tau = st.dim, st.n[0], st.N, st.tau
 
@@ -114,8 +115,8 @@ def st_vcycles(st, h_cycles: int = 2):
 
     def build_H(m):
         Abar = reference_operator(dim, [m] * dim, st.coeff, st.T)
-        I = sp.identity(m ** dim, format="csr")
-        return [mus[k] * I + tau * Abar for k in range(N)]
+        M = assemble_M(dim, [m] * dim, getattr(st, "mass", "identity"))
+        return [mus[k] * M + tau * Abar for k in range(N)]
 
     VA = VCycle(dim, n, build_A)
     VH = VCycle(dim, n, build_H)

@@ -9,9 +9,18 @@
  * What it computes is the plain definition the whole method must reproduce:
  * sequential implicit Euler time stepping (§2, eq. 2.1)
  *
- *     M (u_n - u_{n-1}) + tau_n A_n u_n = tau_n f_n,   u_0 = u_I,
+ *     M (u_n - u_{n-1}) + tau_n A_n u_n = tau_n M f_n,   u_0 = u_I,
  *
- * with M = I (finite differences), time steps tau_n (uniform T/N unless the
+ * with M = I (finite differences, mass = 0) or, for mass = 1 (dim <= 2), the P1
+ * finite-element mass matrix of the uniform mesh divided by h^d (1-D: the
+ * tridiagonal [1/6, 2/3, 1/6]; 2-D, each grid square cut by its diagonal from
+ * the lower-left to the upper-right corner: 1/2 at the point and 1/12 at the
+ * four axis neighbours and at the upper-right and lower-left diagonal ones),
+ * and the source entering as the consistent load M f_n of its nodal values.
+ * The finite-element stiffness matrix of the coefficient taken at the edge
+ * midpoints is h^d times the finite-difference operator below, so dividing the
+ * finite-element system by h^d gives exactly this one.  Time steps tau_n
+ * (uniform T/N unless the
  * caller passes the N step lengths; then t_n = tau_1 + ... + tau_n), on the
  * unit box with n_d interior points per axis, h_d = 1/(n_d+1), homogeneous
  * Dirichlet data, and the conservative finite-difference operator
@@ -20,9 +29,10 @@
  *                             + a(x_i + h_d e_d/2, t_n) (v_i - v_{i+e_d}) ]
  *
  * (coefficient sampled at face midpoints, v = 0 outside the grid).  Each
- * step factors I + tau A_n by a hand-written banded Cholesky (band = one
- * grid line / plane) and solves; for grids where the band is too wide the
- * per-step solve is conjugate gradients to a relative residual of cg_tol.
+ * step factors M + tau A_n by a hand-written banded Cholesky (band = one
+ * grid line / plane, one more for the 2-D P1 mass) and solves; for grids where
+ * the band is too wide the per-step solve is conjugate gradients to a relative
+ * residual of cg_tol.
  *
  * Also provided: the action of the time-global matrix B = K (x) M +
  * diag(tau_n A_n) of §2, eq. 2.3-2.4, used to check residuals at any size.
@@ -101,6 +111,35 @@ static void oc_faces(const oc_grid* g, const oc_coeff* k, double t, const int* i
   *ap = oc_coef(k, g->dim, x, t);
 }
 
+/* out = M v for one spatial slice (mass 0: M = I; 1: the P1 mass over h^d, dim <= 2). */
+static void oc_apply_M_slice(const oc_grid* g, int mass, const double* v, double* out) {
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < g->ns; ++i) {
+    if (mass == 0) {
+      out[i] = v[i];
+      continue;
+    }
+    int idx[3];
+    oc_coords(g, i, idx);
+    if (g->dim == 1) {
+      double vm = idx[0] > 0 ? v[i - 1] : 0.0;
+      double vp = idx[0] < g->n[0] - 1 ? v[i + 1] : 0.0;
+      out[i] = (2.0 / 3.0) * v[i] + (vm + vp) / 6.0;
+    } else {
+      int x = idx[0], y = idx[1], nx = g->n[0], ny = g->n[1];
+      long sy = g->stride[1];
+      double s = 0.0;
+      if (x > 0) s += v[i - 1];
+      if (x < nx - 1) s += v[i + 1];
+      if (y > 0) s += v[i - sy];
+      if (y < ny - 1) s += v[i + sy];
+      if (x > 0 && y > 0) s += v[i - sy - 1];
+      if (x < nx - 1 && y < ny - 1) s += v[i + sy + 1];
+      out[i] = 0.5 * v[i] + s / 12.0;
+    }
+  }
+}
+
 /* out = A(t) v for one spatial slice. */
 static void oc_apply_A_slice(const oc_grid* g, const oc_coeff* k, double t, const double* v,
                              double* out) {
@@ -120,24 +159,30 @@ static void oc_apply_A_slice(const oc_grid* g, const oc_coeff* k, double t, cons
   }
 }
 
-/* ---- banded Cholesky of I + tau A(t) ----------------------------------
+/* ---- banded Cholesky of M + tau A(t) ----------------------------------
  * Lower band storage, column major: ab[j*(b+1) + (i-j)] = M[i][j], j <= i <= j+b.
- * b is the stride of the slowest axis (one grid line in 2-D, one plane in 3-D). */
+ * b is the stride of the slowest axis (one grid line in 2-D, one plane in 3-D), plus one
+ * for the upper-right diagonal coupling of the 2-D P1 mass. */
 static void oc_assemble_band(const oc_grid* g, const oc_coeff* k, double t, double tau, long b,
-                             double* ab) {
+                             int mass, double* ab) {
   memset(ab, 0, sizeof(double) * (size_t)(b + 1) * (size_t)g->ns);
+  const double mc = mass == 0 ? 1.0 : (g->dim == 1 ? 2.0 / 3.0 : 0.5);
+  const double mo = mass == 0 ? 0.0 : (g->dim == 1 ? 1.0 / 6.0 : 1.0 / 12.0);
 #pragma omp parallel for schedule(static)
   for (long i = 0; i < g->ns; ++i) {
     int idx[3];
     oc_coords(g, i, idx);
-    double diag = 1.0;
+    double diag = mc;
     for (int d = 0; d < g->dim; ++d) {
       double am, ap, w = tau / (g->h[d] * g->h[d]);
       oc_faces(g, k, t, idx, d, &am, &ap);
       diag += w * (am + ap);
       /* coupling to the upper neighbour (row i + stride, column i) */
-      if (idx[d] < g->n[d] - 1) ab[i * (b + 1) + g->stride[d]] = -w * ap;
+      if (idx[d] < g->n[d] - 1) ab[i * (b + 1) + g->stride[d]] = -w * ap + mo;
     }
+    /* 2-D P1 mass: the upper-right diagonal neighbour (row i + stride + 1, column i) */
+    if (mass && g->dim == 2 && idx[0] < g->n[0] - 1 && idx[1] < g->n[1] - 1)
+      ab[i * (b + 1) + g->stride[1] + 1] = mo;
     ab[i * (b + 1)] = diag;
   }
 }
@@ -181,7 +226,7 @@ static void oc_band_solve(long n, long b, const double* ab, double* x) {
   }
 }
 
-/* ---- conjugate gradients on I + tau A(t) ------------------------------ */
+/* ---- conjugate gradients on M + tau A(t) ------------------------------ */
 static double oc_dot(long n, const double* a, const double* b) {
   double s = 0.0;
 #pragma omp parallel for reduction(+ : s) schedule(static)
@@ -189,15 +234,16 @@ static double oc_dot(long n, const double* a, const double* b) {
   return s;
 }
 
-static int oc_cg(const oc_grid* g, const oc_coeff* k, double t, double tau, const double* rhs,
+static int oc_cg(const oc_grid* g, const oc_coeff* k, double t, double tau, int mass, const double* rhs,
                  double* x, double tol, int max_it, double* work) {
   long n = g->ns;
-  double *r = work, *p = work + n, *q = work + 2 * n;
+  double *r = work, *p = work + n, *q = work + 2 * n, *m = work + 3 * n;
   /* x holds the initial guess */
   oc_apply_A_slice(g, k, t, x, q);
+  oc_apply_M_slice(g, mass, x, m);
 #pragma omp parallel for schedule(static)
   for (long i = 0; i < n; ++i) {
-    r[i] = rhs[i] - (x[i] + tau * q[i]);
+    r[i] = rhs[i] - (m[i] + tau * q[i]);
     p[i] = r[i];
   }
   double bb = oc_dot(n, rhs, rhs);
@@ -206,8 +252,9 @@ static int oc_cg(const oc_grid* g, const oc_coeff* k, double t, double tau, cons
   int it = 0;
   while (rr > tol * tol * bb && it < max_it) {
     oc_apply_A_slice(g, k, t, p, q);
+    oc_apply_M_slice(g, mass, p, m);
 #pragma omp parallel for schedule(static)
-    for (long i = 0; i < n; ++i) q[i] = p[i] + tau * q[i];
+    for (long i = 0; i < n; ++i) q[i] = m[i] + tau * q[i];
     double alpha = rr / oc_dot(n, p, q);
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) {
@@ -230,12 +277,13 @@ static int oc_cg(const oc_grid* g, const oc_coeff* k, double t, double tau, cons
  *   u0 : [ns] initial datum u_I, or NULL for zero
  *   u  : [n_steps][ns] output
  *   method : 0 = banded Cholesky, 1 = CG to relative residual cg_tol
+ *   mass   : 0 = M = I, 1 = P1 mass over h^d (dim <= 2)
  * Returns 0 on success, -1 on a failed factorization, -2 on CG failure,
- * -3 on allocation failure.
+ * -3 on allocation failure, -4 on an unsupported mass.
  */
 int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
                       const double* f, const double* u0, double* u, int n_steps, int method,
-                      double cg_tol, int nthreads, const double* steps) {
+                      double cg_tol, int nthreads, const double* steps, int mass) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -243,17 +291,26 @@ int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
 #endif
   oc_grid g;
   oc_grid_init(&g, dim, n);
+  if (mass != 0 && (mass != 1 || dim > 2)) return -4;
   long ns = g.ns;
-  long b = dim == 1 ? 1 : g.stride[dim - 1];
+  long b = dim == 1 ? 1 : g.stride[dim - 1] + (mass && dim == 2 ? 1 : 0);
   double tau = T / N;
   double* ab = NULL;
   double* work = NULL;
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)ns);
+  if (!tmp) return -3;
   if (method == 0) {
     ab = (double*)malloc(sizeof(double) * (size_t)(b + 1) * (size_t)ns);
-    if (!ab) return -3;
+    if (!ab) {
+      free(tmp);
+      return -3;
+    }
   } else {
-    work = (double*)malloc(sizeof(double) * 3 * (size_t)ns);
-    if (!work) return -3;
+    work = (double*)malloc(sizeof(double) * 4 * (size_t)ns);
+    if (!work) {
+      free(tmp);
+      return -3;
+    }
   }
   int rc = 0;
   double t_acc = 0.0;
@@ -267,9 +324,11 @@ int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
     const double* prev = s == 1 ? u0 : u + (size_t)(s - 2) * ns;
     double* cur = u + (size_t)(s - 1) * ns;
     const double* fs = f + (size_t)(s - 1) * ns;
-    for (long i = 0; i < ns; ++i) cur[i] = (prev ? prev[i] : 0.0) + tau * fs[i];
+    /* right-hand side M (u_{n-1} + tau_n f_n) */
+    for (long i = 0; i < ns; ++i) tmp[i] = (prev ? prev[i] : 0.0) + tau * fs[i];
+    oc_apply_M_slice(&g, mass, tmp, cur);
     if (method == 0) {
-      oc_assemble_band(&g, k, t, tau, b, ab);
+      oc_assemble_band(&g, k, t, tau, b, mass, ab);
       if (oc_band_cholesky(ns, b, ab) != 0) {
         rc = -1;
         break;
@@ -285,7 +344,7 @@ int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
       /* initial guess: the previous step (or the rhs) */
       if (prev)
         memcpy(cur, prev, sizeof(double) * (size_t)ns);
-      int it = oc_cg(&g, k, t, tau, rhs, cur, cg_tol, 100000, work);
+      int it = oc_cg(&g, k, t, tau, mass, rhs, cur, cg_tol, 100000, work);
       free(rhs);
       if (it < 0) {
         rc = -2;
@@ -295,13 +354,14 @@ int oc_implicit_euler(int dim, const int* n, int N, double T, const oc_coeff* k,
   }
   free(ab);
   free(work);
+  free(tmp);
   return rc;
 }
 
-/* out = B u = (K (x) I) u + diag(tau_n A_n) u with u_0 := 0 (§2, eq. 2.3-2.4); steps as in
- * oc_implicit_euler. */
+/* out = B u = (K (x) M) u + diag(tau_n A_n) u with u_0 := 0 (§2, eq. 2.3-2.4); steps and mass
+ * as in oc_implicit_euler. */
 void oc_apply_B(int dim, const int* n, int N, double T, const oc_coeff* k, const double* u,
-                double* out, int nthreads, const double* steps) {
+                double* out, int nthreads, const double* steps, int mass) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -312,6 +372,13 @@ void oc_apply_B(int dim, const int* n, int N, double T, const oc_coeff* k, const
   long ns = g.ns;
   double tau = T / N;
   double t_acc = 0.0;
+  double* diff = (double*)malloc(sizeof(double) * (size_t)ns);
+  double* mdiff = (double*)malloc(sizeof(double) * (size_t)ns);
+  if (!diff || !mdiff) {
+    free(diff);
+    free(mdiff);
+    return;
+  }
   for (int s = 1; s <= N; ++s) {
     const double* us = u + (size_t)(s - 1) * ns;
     double* os = out + (size_t)(s - 1) * ns;
@@ -322,12 +389,13 @@ void oc_apply_B(int dim, const int* n, int N, double T, const oc_coeff* k, const
       t = t_acc;
     }
     oc_apply_A_slice(&g, k, t, us, os);
+    for (long i = 0; i < ns; ++i) diff[i] = us[i] - (s > 1 ? us[i - ns] : 0.0);
+    oc_apply_M_slice(&g, mass, diff, mdiff);
 #pragma omp parallel for schedule(static)
-    for (long i = 0; i < ns; ++i) {
-      double prev = s > 1 ? us[i - ns] : 0.0;
-      os[i] = (us[i] - prev) + tau * os[i];
-    }
+    for (long i = 0; i < ns; ++i) os[i] = mdiff[i] + tau * os[i];
   }
+  free(diff);
+  free(mdiff);
 }
 
 /* out = A(t) v on one slice. */

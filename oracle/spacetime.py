@@ -7,6 +7,11 @@ where dense or sparse-direct linear algebra finishes in seconds:
   midpoints, Dirichlet) at t_n = tau_1 + ... + tau_n, the reference pair
   tau = T/N and Abar = the operator of the coefficient's time mean over (0, T)
   (one of the averages §2 allows after eq. 2.2),
+* the mass matrix M of eq. 2.1: the identity (finite differences) or the P1 finite-element mass
+  matrix of the uniform mesh divided by h^d (1-D and 2-D, the 2-D mesh cutting every square along
+  its lower-left to upper-right diagonal); the P1 stiffness matrix with the coefficient at the edge
+  midpoints is h^d times the finite-difference operator, so the finite-element system divided by
+  h^d uses the same A_n,
 * the time-global matrices K, B = K (x) M + diag(tau_n A_n) (§2, eq. 2.3-2.4),
   the Schur complement S (eq. 2.5) and the saddle-point matrix (eq. 2.7),
 * the temporal change of basis Phi (type-III DST, §4 eq. 4.2), its inverse
@@ -89,6 +94,33 @@ def assemble_A(dim: int, n: Sequence[int], coeff, t: float) -> sp.csr_matrix:
                          shape=(ns, ns))
 
 
+def assemble_M(dim: int, n: Sequence[int], mass: str = "identity") -> sp.csr_matrix:
+    """The mass matrix of eq. 2.1 over h^d: the identity, or for "p1" the P1 mass matrix of the
+    uniform mesh (1-D: h [1/6, 2/3, 1/6]; 2-D, squares cut along the lower-left to upper-right
+    diagonal: h^2/2 at the point, h^2/12 at the four axis neighbours and at the upper-right and
+    lower-left ones) divided by h^d."""
+    n = list(n)[:dim]
+    ns = int(np.prod(n))
+    if mass == "identity":
+        return sp.identity(ns, format="csr")
+    if mass != "p1" or dim > 2:
+        raise ValueError("mass %r in %d-D" % (mass, dim))
+    if dim == 1:
+        m = n[0]
+        return sp.diags([np.full(m - 1, 1 / 6), np.full(m, 2 / 3), np.full(m - 1, 1 / 6)], [-1, 0, 1],
+                        format="csr")
+    x, y = grid_index(dim, n)
+    rows, cols, vals = [np.arange(ns)], [np.arange(ns)], [np.full(ns, 0.5)]
+    for dx, dy in ((1, 0), (0, 1), (1, 1)):  # each coupling once, then mirrored
+        i = np.nonzero((x + dx < n[0]) & (y + dy < n[1]))[0]
+        j = i + dx + dy * n[0]
+        rows += [i, j]
+        cols += [j, i]
+        vals += [np.full(i.size, 1 / 12), np.full(i.size, 1 / 12)]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(ns, ns))
+
+
 def K_matrix(N: int) -> np.ndarray:
     """Lower bidiagonal [1; -1 1] of §2, eq. 2.4."""
     return np.eye(N) - np.eye(N, k=-1)
@@ -159,11 +191,14 @@ def reference_operator(dim: int, n: Sequence[int], coeff, T: float) -> sp.csr_ma
 
 
 class SpaceTime:
-    """The FD time-global problem: grid, N steps tau_n (uniform T/N unless ``taus`` is given),
-    M = I; the reference step of the preconditioner is tau = T/N."""
+    """The time-global problem: grid, N steps tau_n (uniform T/N unless ``taus`` is given), the
+    mass matrix M (``mass``: "identity" for finite differences, "p1" for P1 finite elements, see
+    assemble_M); the reference step of the preconditioner is tau = T/N."""
 
-    def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff, taus=None):
+    def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff, taus=None, mass="identity"):
         self.dim, self.n, self.N, self.T, self.coeff = dim, list(n)[:dim], N, float(T), coeff
+        self.mass = mass
+        self.M = assemble_M(dim, self.n, mass)
         self.tau = self.T / N
         self.uniform = taus is None
         self.taus, self.times = step_times(N, self.T, taus)
@@ -173,14 +208,16 @@ class SpaceTime:
 
     # -- time-global operators (vectors are [N][ns]) --
     def K(self, u):
+        """(K (x) M) u: M (u_n - u_{n-1}), u_0 := 0."""
         out = u.copy()
         out[1:] -= u[:-1]
-        return out
+        return (self.M @ out.T).T
 
     def Kt(self, p):
+        """(K^T (x) M) p: M (p_n - p_{n+1}), p_{N+1} := 0."""
         out = p.copy()
         out[:-1] -= p[1:]
-        return out
+        return (self.M @ out.T).T
 
     def Ablk(self, v):
         return np.stack([self.taus[i] * (self.A[i] @ v[i]) for i in range(self.N)])
@@ -189,11 +226,12 @@ class SpaceTime:
         return self.K(u) + self.Ablk(u)
 
     def rhs(self, f: np.ndarray, u0: Optional[np.ndarray]) -> np.ndarray:
-        """F = [tau_1 f_1 + M u_I, tau_2 f_2, ..., tau_N f_N]  (§2, after eq. 2.4)."""
+        """F = [tau_1 f_1 + M u_I, tau_2 f_2, ..., tau_N f_N]  (§2, after eq. 2.4), the load f_n
+        being M times the nodal values given (the identity for finite differences)."""
         F = self.taus[:, None] * np.asarray(f, dtype=np.float64).reshape(self.N, self.ns)
         if u0 is not None:
             F[0] += u0
-        return F
+        return np.ascontiguousarray((self.M @ F.T).T)
 
     def residual(self, F, u):
         return np.linalg.norm(F - self.B(u)) / np.linalg.norm(F)
@@ -208,8 +246,7 @@ class SpaceTime:
 
     def exact_H_solver(self) -> Callable:
         m = mu(self.N)
-        I = sp.identity(self.ns, format="csc")
-        lus = [spla.splu((m[k] * I + self.tau * self.Abar).tocsc()) for k in range(self.N)]
+        lus = [spla.splu((m[k] * self.M + self.tau * self.Abar).tocsc()) for k in range(self.N)]
 
         def solve(k, r):
             return lus[k].solve(r)
@@ -290,7 +327,7 @@ def table1_eigs(h: float, N: int, T: float = 1.0):
 def dense_saddle(st: SpaceTime):
     """The saddle-point matrix [[A, -K], [-K^T, -(K + K^T + A)]] of §2, eq. 2.7 (dense)."""
     N, ns = st.N, st.ns
-    Kb = np.kron(K_matrix(N), np.eye(ns))
+    Kb = np.kron(K_matrix(N), st.M.toarray())
     Ab = sla.block_diag(*[st.taus[i] * st.A[i].toarray() for i in range(N)])
     top = np.hstack([Ab, -Kb])
     bot = np.hstack([-Kb.T, -(Kb + Kb.T + Ab)])
