@@ -9,7 +9,9 @@
  *     (u_n - u_{n-1}) + tau_n A_n u_n = tau_n f_n,  n = 1..N_t,  u_0 = u0,
  *
  * with M = I and the conservative finite-difference operator
- *     (A_n v)_i = sum_d h^-2 [a(x_i - h e_d/2, t_n)(v_i - v_{i-e_d}) + a(x_i + h e_d/2, t_n)(v_i - v_{i+e_d})].
+ *     (A_n v)_i = sum_d h^-2 [a(x_i - h e_d/2, t_n)(v_i - v_{i-e_d}) + a(x_i + h e_d/2, t_n)(v_i - v_{i+e_d})]
+ * or, with pt_options.mass = 1, the P1 finite-element form M (u_n - u_{n-1}) + tau_n A_n u_n =
+ * tau_n M f_n (see pt_options.mass).
  * All N_t steps are solved at once: the time-global system B u = F (eq. 2.3-2.4) is
  * rewritten as the symmetric saddle-point system of eq. 2.7 and solved by the inexact
  * Uzawa iteration of §3, eq. 3.1, preconditioned by the DST-in-time Schur-complement
@@ -87,11 +89,13 @@ typedef struct {
   double jacobi_weight;  /* weighted-Jacobi smoothing weight; <= 0 selects 2/3, 4/5, 6/7 by dim */
   void* stream;          /* cudaStream_t for all work of this problem; NULL = default stream */
   int check_every;       /* iterations between host polls of the device convergence flag; 0 = auto */
-  int autotune;          /* 1: before the first solve, time the candidate launch configurations
-                            (temporal-transform tile width, multigrid coarse-level split) and keep
-                            the fastest; results are cached per (dim, n, N_t, precision, solver) in
-                            the process and, when the environment variable PT_TUNE_CACHE names a
-                            file, in that JSON file.  0: defaults. */
+  int autotune;          /* Before the first solve, time the candidate launch configurations
+                            (temporal-transform tile width, multigrid coarse-level split) on the
+                            problem's own data and keep the fastest; the choice is cached per grid,
+                            precision, solvers and power-of-two bucket of N_t in the process and,
+                            when the environment variable PT_TUNE_CACHE names a file, in that JSON
+                            file.  1: for every solve; 0: for pt_solve_batch and the server only;
+                            -1: never (defaults). */
   int dst_cols;          /* complex columns per CTA of the temporal transform; 0 = automatic */
   int coarse_elems;      /* multigrid levels with at most this many points per slice run in one
                             CTA per slice; 0 = 1024; else a power of two in [64, 4096] */
@@ -103,7 +107,15 @@ typedef struct {
                             2 = exact (PT_EINVAL if unavailable) */
   int krylov;            /* 0: the Uzawa iteration of eq. 3.1; m in [1, 64]: flexible GMRES(m)
                             right-preconditioned by one inexact Uzawa step (FP64 only) */
-  int reserved[1];       /* must be zero */
+  int mass;              /* M of eq. 2.1.  0: M = I (finite differences).  1: P1 finite elements on
+                            the uniform mesh (1-D; 2-D with every grid square cut along its lower-left
+                            to upper-right diagonal), the system divided by h^d: M is the P1 mass
+                            matrix over h^d (1-D [1/6, 2/3, 1/6]; 2-D 1/2 at the point, 1/12 at the
+                            four axis neighbours and the upper-right and lower-left ones), A_n the
+                            stiffness matrix over h^d with the coefficient at the edge midpoints (the
+                            finite-difference operator above), F_n = tau_n M f_n with f the nodal
+                            values (+ M u0 for n = 1), and H_k = mu_k M + tau Abar.  dim <= 2, FP64,
+                            krylov = 0; in 2-D the H_k solves are V-cycles (h_solver 2 is refused). */
   const double* tau_steps; /* NULL: N_t uniform steps T/N_t.  Else a host array of the N_t step
                             lengths tau_1..tau_N (§2, eq. 2.1), each finite and > 0, summing to T
                             within 1e-10 T (else PT_EINVAL); copied at create.  t_n = tau_1 + ... +
@@ -217,8 +229,13 @@ const char* pt_status_string(pt_status s);
  * problem's precision, and are what the per-kernel parity tests call.  in and out may not
  * alias.  Errors: PT_EINVAL on NULL pointers, PT_ECUDA. */
 
-/* out = B u = (K (x) I) u + diag(tau_n A_n) u, u_0 := 0  (§2, eq. 2.3-2.4). */
+/* out = B u = (K (x) M) u + diag(tau_n A_n) u, u_0 := 0  (§2, eq. 2.3-2.4). */
 pt_status pt_apply_B(pt_problem* p, const double* u_dev, double* out_dev);
+
+/* out = S u with S = K^T A~^-1 K + K + K^T + A (§2, eq. 2.5; K = K (x) M, A = diag(tau_n A_n)) and
+ * A~^-1 the problem's spatial solver of tau_n A_n: the exact Schur complement when that solver is
+ * exact (1-D exact tridiagonal solves), else its inexact form.  FP64 problems only (PT_EINVAL). */
+pt_status pt_apply_S(pt_problem* p, const double* u_dev, double* out_dev);
 
 /* out = Phi^-T r: out_k = sum_n r_n sin((2k-1) n pi / (2N)), k = 1..N (§4, eq. 4.3 transposed). */
 pt_status pt_dst_forward(pt_problem* p, const double* r_dev, double* out_dev);
@@ -231,7 +248,7 @@ pt_status pt_dst_inverse(pt_problem* p, const double* y_dev, double* out_dev);
 pt_status pt_precond_A(pt_problem* p, const double* r_dev, double* out_dev);
 
 /* out = H~^-1 r = Phi^-1 Hhat~^-1 Phi^-T r with Hhat~_k^-1 = (2 tau/N) H~_k^-1 Abar H~_k^-1,
- * H_k = mu_k I + tau Abar, mu_k = 2 sin((2k-1) pi/(4N))  (§4, eq. 4.4-4.6). */
+ * H_k = mu_k M + tau Abar, mu_k = 2 sin((2k-1) pi/(4N))  (§4, eq. 4.4-4.6). */
 pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev);
 
 /* ---- Allocation-free transform ------------------------------------------------------------

@@ -78,7 +78,7 @@ def _step_array(taus, N: int):
     return a
 
 
-def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=False, h_solver="auto",
+def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=0, h_solver="auto",
              steps=None):
     o = _lib.Options()
     if steps is not None:
@@ -88,7 +88,7 @@ def _options(precision="mixed", omega=0.0, solver="mg", check_every=0, autotune=
     o.omega = float(omega)
     o.spatial_solver = {"mg": _lib.PT_SOLVER_MG, "exact": _lib.PT_SOLVER_EXACT_1D}[solver]
     o.check_every = int(check_every)
-    o.autotune = 1 if autotune else 0
+    o.autotune = 1 if autotune is True else (-1 if autotune is False else int(autotune))
     return o
 
 
@@ -226,14 +226,15 @@ class Problem:
     ``coeff`` is any object with attributes a0, c, fx[3], mx[3], ft, mt (see ``pt_coeff``).
     ``f``: [N][n_s] source values, NumPy (host) or torch CUDA tensor (device), float64.
     ``taus``: the N step lengths tau_1..tau_N (summing to T), or None for uniform steps T/N.
+    ``mass``: "identity" (finite differences, M = I) or "p1" (P1 finite elements, ``pt_options.mass``).
     """
 
     def __init__(self, dim: int, n: Sequence[int], N: int, T: float, coeff, f, u0=None,
                  precision: str = "fp64", omega: float = 0.0, solver: str = "mg",
                  stream: Optional[int] = None, check_every: int = 0, jacobi_weight: float = 0.0,
-                 autotune: bool = False, dst_cols: int = 0, coarse_elems: int = 0,
+                 autotune=0, dst_cols: int = 0, coarse_elems: int = 0,
                  graphs: bool = True, n_vcycles: int = 0, h_solver: str = "auto", krylov: int = 0,
-                 taus=None):
+                 taus=None, mass: str = "identity"):
         L = _lib.load()
         self._lib = L
         self.dim, self.n, self.N, self.T = dim, list(n)[:dim], N, float(T)
@@ -250,12 +251,13 @@ class Problem:
         opts.jacobi_weight = float(jacobi_weight)
         opts.stream = stream
         opts.check_every = int(check_every)
-        opts.autotune = 1 if autotune else 0
+        opts.autotune = 1 if autotune is True else (-1 if autotune is False else int(autotune))
         opts.dst_cols = int(dst_cols)
         opts.coarse_elems = int(coarse_elems)
         opts.no_graphs = 0 if graphs else 1
         opts.h_solver = {"auto": 0, "vcycle": 1, "exact": 2}[h_solver]
         opts.krylov = int(krylov)
+        opts.mass = {"identity": 0, "p1": 1}[mass]
         steps = _step_array(taus, int(N))
         if steps is not None:
             opts.tau_steps = steps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -320,6 +322,10 @@ class Problem:
 
     def apply_B(self, u, out):
         return self._component("pt_apply_B", u, out)
+
+    def apply_S(self, u, out):
+        """out = S u, the Schur complement of eq. 2.5 with the problem's A~ (FP64 problems)."""
+        return self._component("pt_apply_S", u, out)
 
     def dst_forward(self, r, out):
         return self._component("pt_dst_forward", r, out)

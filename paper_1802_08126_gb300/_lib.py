@@ -19,6 +19,7 @@ EXPORTED = (
     "pt_profile_reset", "pt_profile_get", "pt_dst_forward_noalloc", "pt_solve_batch",
     "pt_problem_set_rhs_uniform", "pt_server_create", "pt_server_submit", "pt_server_wait",
     "pt_server_stats", "pt_server_destroy", "pt_problem_estimate_bytes", "pt_problem_device_bytes",
+    "pt_apply_S",
 )
 
 
@@ -37,7 +38,7 @@ class Options(ctypes.Structure):
                 ("jacobi_weight", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("check_every", ctypes.c_int), ("autotune", ctypes.c_int), ("dst_cols", ctypes.c_int),
                 ("coarse_elems", ctypes.c_int), ("no_graphs", ctypes.c_int), ("h_solver", ctypes.c_int),
-                ("krylov", ctypes.c_int), ("reserved", ctypes.c_int * 1),
+                ("krylov", ctypes.c_int), ("mass", ctypes.c_int),
                 ("tau_steps", ctypes.POINTER(ctypes.c_double))]
 
 
@@ -69,7 +70,8 @@ def load(path: str = LIB_PATH):
         L.pt_last_error.restype = ctypes.c_char_p
         L.pt_status_string.argtypes = [i]
         L.pt_status_string.restype = ctypes.c_char_p
-        for name in ("pt_apply_B", "pt_dst_forward", "pt_dst_inverse", "pt_precond_A", "pt_precond_H"):
+        for name in ("pt_apply_B", "pt_apply_S", "pt_dst_forward", "pt_dst_inverse", "pt_precond_A",
+                     "pt_precond_H"):
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp]
             fn.restype = i

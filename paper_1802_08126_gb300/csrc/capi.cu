@@ -62,6 +62,7 @@ struct pt_problem {
   pt_options opt{};
   int mixed = 0;
   int exact1d = 0;
+  int mass = 0;                                 // M of eq. 2.1: 0 identity, 1 P1 mass over h^d
   double omega = 0.5;
   double jacobi = 0.0;
   cudaStream_t st = nullptr;
@@ -211,6 +212,7 @@ StencilGeom<T> geom(const pt_problem* p, int l) {
   g.tab = (sizeof(T) == 8 ? (const T*)(const void*)p->tab_d : (const T*)(const void*)p->tab_f) + p->lev[l].tab;
   g.a0 = (T)p->coeff.a0;
   g.h2inv = (T)(1.0 / (p->lev[l].h * p->lev[l].h));
+  g.mass = p->mass;
   return g;
 }
 
@@ -257,6 +259,7 @@ OpBatch<T> op_H(const pt_problem* p) {
   o.cth = (const T*)p->cthH;
   o.s = (T)p->tau;
   o.omega = (T)p->jacobi;
+  o.mass = p->mass;  // H_k = mu_k M + tau Abar
   return o;
 }
 
@@ -325,7 +328,7 @@ void apply_precond_A(pt_problem* p, const T* b, void* out, int mode, int out_fp6
 // One V-cycle for all H_k: out = V(b) (mode 0) or out += V(b) (mode 1)
 template <typename T>
 void vcycle_H(pt_problem* p, const T* b, T* out, int mode, const int* done) {
-  if (p->dim == 2) {
+  if (p->dim == 2 && !p->mass) {
     const T* dinv[kMaxLevels];
     for (int l = 0; l < kMaxLevels; ++l) dinv[l] = (const T*)p->dinvH[l];
     vcycle2d<T>(mg_plan<T>(p), op_H<T>(p), b, out, mode, 0, p->hvar, p->hvar ? nullptr : dinv, nullptr,
@@ -858,11 +861,29 @@ std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune_cache;
 bool g_tune_file_loaded = false;
 
+// Problems share a tuning when they have the same grid, precision and solvers and their N_t falls
+// in the same power-of-two bucket with the same temporal-transform kind (radix for powers of two,
+// Bluestein otherwise): the launch shapes scale alike within a bucket, so a batch or a request
+// stream of many N_t tunes once per bucket.
 std::string tune_key(const pt_problem* p) {
+  long long bucket = 1;
+  while (bucket < p->N) bucket <<= 1;
   std::ostringstream k;
-  k << "d" << p->dim << "_n" << p->n << "_N" << p->N << "_" << (p->mixed ? "mixed" : "fp64") << "_"
-    << (p->exact1d ? "exact" : "mg");
+  k << "d" << p->dim << "_n" << p->n << "_N" << bucket << (bucket == p->N ? "r" : "b") << "_"
+    << (p->mixed ? "mixed" : "fp64") << "_" << (p->exact1d ? "exact" : "mg") << (p->hdst ? "_hdst" : "")
+    << (p->mass ? "_p1" : "");
   return k.str();
+}
+
+// temporal-transform columns per CTA (0: automatic) that fit this problem's shared memory and slice
+std::vector<int> tune_cols(const pt_problem* p) {
+  std::vector<int> cols = {0};
+  for (int c = 1; c <= 16; c *= 2) {
+    const long long L = p->blueM > 0 ? p->blueM + 1 : p->N + 1;
+    const long long bytes = (long long)c * L * 2 * (p->mixed ? 4 : 8) * 2;
+    if (p->lev[0].S % (2 * c) == 0 && bytes <= 200 * 1024 && 2 * c <= p->lev[0].S) cols.push_back(c);
+  }
+  return cols;
 }
 
 void tune_file_load() {
@@ -905,6 +926,12 @@ int lc_for(const pt_problem* p, int elems) {
 }
 
 void apply_choice(pt_problem* p, TuneChoice t) {
+  // a choice tuned on another problem of the bucket: the largest valid column count <= its own
+  const std::vector<int> cols = tune_cols(p);
+  int c = 0;
+  for (int v : cols)
+    if (v <= t.dstC) c = std::max(c, v);
+  t.dstC = c;
   p->dstC = t.dstC;
   p->coarse_elems = t.coarse_elems;
   p->lc = std::min(std::max(lc_for(p, t.coarse_elems), p->lc_min), p->lc_max);
@@ -924,12 +951,7 @@ pt_status autotune(pt_problem* p) {
     p->tuned = true;
     return PT_OK;
   }
-  std::vector<int> cols = {0};
-  for (int c = 1; c <= 16; c *= 2) {
-    const long long L = p->blueM > 0 ? p->blueM + 1 : p->N + 1;
-    const long long bytes = (long long)c * L * 2 * (p->mixed ? 4 : 8) * 2;
-    if (p->lev[0].S % (2 * c) == 0 && bytes <= 200 * 1024 && 2 * c <= p->lev[0].S) cols.push_back(c);
-  }
+  const std::vector<int> cols = tune_cols(p);
   std::vector<int> coarse = {kCoarseMaxElems};
   if (!p->exact1d)
     for (int e : {256, 4096})
@@ -1004,7 +1026,14 @@ pt_status validate(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff
     if (o->spatial_solver == PT_SOLVER_EXACT_1D && grid->dim != 1)
       return fail(PT_EINVAL, "exact spatial solves are available in 1-D only");
     if (o->n_vcycles < 0 || o->n_vcycles > 4) return fail(PT_EINVAL, "n_vcycles must be in [0, 4]");
-    if (o->reserved[0] != 0) return fail(PT_EINVAL, "reserved options must be zero");
+    if (o->mass != 0 && o->mass != 1) return fail(PT_EINVAL, "mass must be 0 (identity) or 1 (P1)");
+    if (o->mass == 1) {
+      if (grid->dim > 2) return fail(PT_EINVAL, "the P1 mass matrix is available in 1-D and 2-D");
+      if (o->precision != PT_PREC_FP64) return fail(PT_EINVAL, "the P1 mass matrix is FP64 only");
+      if (o->krylov != 0) return fail(PT_EINVAL, "the P1 mass matrix is not available with krylov");
+      if (grid->dim == 2 && o->h_solver == 2)
+        return fail(PT_EINVAL, "exact H_k solves are not available with the 2-D P1 mass");
+    }
     if (o->krylov < 0 || o->krylov > 64) return fail(PT_EINVAL, "krylov must be in [0, 64]");
     if (o->tau_steps) {
       double sum = 0.0;
@@ -1039,7 +1068,9 @@ pt_status setup_precision(pt_problem* p) {
     if (!p->W3) return st;
   }
   if (!p->exact1d) {
-    const bool fused = p->dim == 2;  // fused 2-D kernels keep no level-0 iterate and no residuals
+    // fused 2-D kernels keep no level-0 iterate and no residuals; with the P1 mass the H_k
+    // V-cycles run on the generic level kernels, which do
+    const bool fused = p->dim == 2 && !p->mass;
     for (int l = 0; l <= p->lc_max && l < p->nlev; ++l) {
       if (l > 0) {
         p->mg_b[l] = alloc_padded<T>(p, p->lev[l], p->N, &st);
@@ -1075,7 +1106,7 @@ pt_status setup_precision(pt_problem* p) {
   if ((st = upload<T>(p, p->cthH, cthH)) != PT_OK) return st;
   // Abar with a constant coefficient: its Jacobi factor w / (mu_k + 2 dim tau a0 / h^2) per level
   p->hvar = !(std::fabs(p->cthbar) <= 1e-14 * std::fabs(p->coeff.a0));
-  if (!p->exact1d && p->dim == 2 && !p->hvar) {
+  if (!p->exact1d && p->dim == 2 && !p->hvar && !p->mass) {
     for (int l = 0; l < p->lc_max; ++l) {
       std::vector<double> dv(p->N);
       const double a0s = p->tau * p->coeff.a0 / (p->lev[l].h * p->lev[l].h);
@@ -1085,7 +1116,8 @@ pt_status setup_precision(pt_problem* p) {
     }
   }
   // exact H_k solves by spatial sine transforms (constant reference coefficient, 2-D and 3-D)
-  p->hdst = !p->exact1d && p->dim >= 2 && !p->hvar && p->opt.h_solver != 1 && p->n + 1 <= kDstiMaxM;
+  // (not with the 2-D P1 mass: its diagonal coupling is not diagonalised by the sine transforms)
+  p->hdst = !p->exact1d && p->dim >= 2 && !p->hvar && p->opt.h_solver != 1 && p->n + 1 <= kDstiMaxM && !p->mass;
   if (p->hdst) {
     const int M = p->n + 1;
     std::vector<double> tw(2 * M), sn(M / 2 + 1), lam(M, 0.0), mud(mu.begin(), mu.end());
@@ -1220,6 +1252,18 @@ int staging_slices(const pt_problem* p) {
   return (int)std::min<size_t>((size_t)p->N, avail / (sizeof(double) * (size_t)p->ns));
 }
 
+// F = M (tau_n f_n + u0 on the first step): the load of the nodal values and the M u_I of
+// §2 (after eq. 2.4) for the P1 mass; nothing to do for M = I.  W1 (FP64 with the P1 mass) holds
+// the product before it is copied back.
+pt_status apply_mass_to_F(pt_problem* p) {
+  if (!p->mass) return PT_OK;
+  const Level& L = p->lev[0];
+  launch_apply_mass(p->F, (double*)p->W1, geom<double>(p, 0), p->N, p->st);
+  PT_CHECK_LAUNCH();
+  PT_CUDA(cudaMemcpyAsync(p->F, p->W1, sizeof(double) * (size_t)L.S * p->N, cudaMemcpyDeviceToDevice, p->st));
+  return PT_OK;
+}
+
 pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, int u0_dev,
                    const unsigned long long* seed = nullptr) {
   const size_t fbytes = sizeof(double) * (size_t)p->ns * p->N;
@@ -1246,7 +1290,7 @@ pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, 
       PT_CHECK_LAUNCH();
     }
     if (tu) PT_CUDA(cudaFreeAsync(tu, p->st));
-    return PT_OK;
+    return apply_mass_to_F(p);
   }
   if (f && !f_dev) {
     PT_CUDA(cudaMallocAsync(&tf, fbytes, p->st));
@@ -1263,7 +1307,7 @@ pt_status load_rhs(pt_problem* p, const double* f, int f_dev, const double* u0, 
   PT_CHECK_LAUNCH();
   if (tf) PT_CUDA(cudaFreeAsync(tf, p->st));
   if (tu) PT_CUDA(cudaFreeAsync(tu, p->st));
-  return PT_OK;
+  return apply_mass_to_F(p);
 }
 
 pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* coeff, const double* f,
@@ -1298,6 +1342,7 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
     rho_max = std::max(rho_max, p->tau / v);
   }
   p->mixed = p->opt.precision == PT_PREC_MIXED;
+  p->mass = p->opt.mass;
   p->nv_h = p->opt.n_vcycles > 0 ? p->opt.n_vcycles : 2;
   p->exact1d = p->opt.spatial_solver == PT_SOLVER_EXACT_1D;
   if (p->opt.omega > 0.0) {
@@ -1380,7 +1425,8 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
   if (!(p->u = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->p = alloc_padded<double>(p, L0, p->N, &st))) return st;
   if (!(p->F = alloc_padded<double>(p, L0, p->N, &st))) return st;
-  if (!p->mixed && p->dim == 2 && L0.P >= 32 && !(p->bres = alloc_padded<double>(p, L0, p->N, &st))) return st;
+  if (!p->mixed && !p->mass && p->dim == 2 && L0.P >= 32 && !(p->bres = alloc_padded<double>(p, L0, p->N, &st)))
+    return st;
   if (p->mixed) {
     float** ir[5] = {&p->ir_du, &p->ir_dp, &p->ir_R1, &p->ir_R2, &p->ir_bp};
     for (float** b : ir)
@@ -1473,7 +1519,7 @@ namespace pt {
 pt_status problem_begin(pt_problem* p, double tol, int max_it) {
   pt_status st = ensure_hist(p, max_it);
   if (st != PT_OK) return st;
-  if (p->opt.autotune && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+  if (p->opt.autotune >= 0 && !p->tuned && (st = autotune(p)) != PT_OK) return st;
   if ((st = enqueue_reset(p, tol, max_it)) != PT_OK) return st;
   if ((st = ensure_graph(p, graph_iterations(p))) != PT_OK) return st;
   PT_CUDA(cudaStreamSynchronize(p->st));
@@ -1586,7 +1632,7 @@ pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_o
   PT_CUDA(cudaSetDevice(p->device));
   pt_status st = ensure_hist(p, max_it);
   if (st != PT_OK) return st;
-  if (p->opt.autotune && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+  if (p->opt.autotune > 0 && !p->tuned && (st = autotune(p)) != PT_OK) return st;
   st = p->opt.krylov > 0 ? krylov_solve(p, tol, max_it, iters, res_hist) : uzawa(p, tol, max_it, iters, res_hist);
   if (st != PT_OK && st != PT_ENOTCONV && st != PT_EDIVERGED) return st;
   if (u_out) {
@@ -1641,7 +1687,7 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
   for (int i = 0; i < count; ++i) {
     pt_problem* p = ps[i];
     if ((st = ensure_hist(p, max_it[i])) != PT_OK) return st;
-    if (p->opt.autotune && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+    if (p->opt.autotune >= 0 && !p->tuned && (st = autotune(p)) != PT_OK) return st;
     if ((st = enqueue_reset(p, tol[i], max_it[i])) != PT_OK) return st;
     max_rounds = std::max(max_rounds, max_it[i] + 1);
   }
@@ -1652,9 +1698,13 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
       if ((st = ensure_graph(ps[i], graph_iterations(ps[i]))) != PT_OK) return st;
   // device list of the solve states and a pinned copy of their done flags
   cudaStream_t bst = nullptr;
+  cudaStream_t cst = nullptr;
   SolveState** dstates = nullptr;
   int* ddone = nullptr;
   int* hdone = nullptr;
+  int* didx = nullptr;      // active problem indices (device loop)
+  int* drounds = nullptr;   // rounds run by the device loop in the current launch
+  int* hrounds = nullptr;
   cudaGraph_t parent = nullptr;
   cudaGraphExec_t exec = nullptr;
   auto cleanup = [&]() {
@@ -1662,8 +1712,12 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
     if (parent) cudaGraphDestroy(parent);
     if (dstates) cudaFree(dstates);
     if (ddone) cudaFree(ddone);
+    if (didx) cudaFree(didx);
+    if (drounds) cudaFree(drounds);
     if (hdone) cudaFreeHost(hdone);
+    if (hrounds) cudaFreeHost(hrounds);
     if (bst) cudaStreamDestroy(bst);
+    if (cst) cudaStreamDestroy(cst);
   };
 #define PT_BATCH_CUDA(call)                                                          \
   do {                                                                               \
@@ -1674,16 +1728,27 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
     }                                                                                \
   } while (0)
   PT_BATCH_CUDA(cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking));
+  PT_BATCH_CUDA(cudaStreamCreateWithFlags(&cst, cudaStreamNonBlocking));
   std::vector<SolveState*> hstates(count);
   for (int i = 0; i < count; ++i) hstates[i] = ps[i]->state;
   PT_BATCH_CUDA(cudaMalloc(&dstates, sizeof(SolveState*) * count));
   PT_BATCH_CUDA(cudaMalloc(&ddone, sizeof(int) * count));
+  PT_BATCH_CUDA(cudaMalloc(&didx, sizeof(int) * count));
+  PT_BATCH_CUDA(cudaMalloc(&drounds, sizeof(int)));
   PT_BATCH_CUDA(cudaMallocHost(&hdone, sizeof(int) * count));
+  PT_BATCH_CUDA(cudaMallocHost(&hrounds, sizeof(int)));
   PT_BATCH_CUDA(cudaMemcpyAsync(dstates, hstates.data(), sizeof(SolveState*) * count, cudaMemcpyHostToDevice, bst));
   std::vector<int> active(count);
   for (int i = 0; i < count; ++i) active[i] = i;
   unsigned long long kernels_per_round = 0;
-  // one graph holding one iteration of every unfinished problem
+  // Device-side loop: the parent graph is one conditional WHILE node whose body holds one
+  // iteration of every active problem (each problem's captured iteration graph as a child node)
+  // and the control kernel, so a whole run of rounds is a single graph launch; the loop ends on
+  // the device once a quarter of the active set has finished (all of it when one is left), or
+  // after the round limit.  Then the host drops the finished problems and launches again.  If
+  // the driver cannot build conditional nodes, one plain graph launch per round is used instead.
+  const int limit = max_rounds + 2;
+  bool device_loop = graphs;
   auto rebuild = [&]() -> cudaError_t {
     if (exec) cudaGraphExecDestroy(exec);
     if (parent) cudaGraphDestroy(parent);
@@ -1691,10 +1756,49 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
     parent = nullptr;
     kernels_per_round = 0;
     cudaError_t e = cudaGraphCreate(&parent, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t body = parent;
+    cudaGraphConditionalHandle handle = 0;
+    if (device_loop) {
+      e = cudaGraphConditionalHandleCreate(&handle, parent, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cnode;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, parent, nullptr, nullptr, 0, &cp);
+      if (e != cudaSuccess) {  // no conditional nodes: per-round launches
+        cudaGetLastError();
+        device_loop = false;
+        cudaGraphDestroy(parent);
+        if ((e = cudaGraphCreate(&parent, 0)) != cudaSuccess) return e;
+        body = parent;
+      } else {
+        body = cp.conditional.phGraph_out[0];
+      }
+    }
+    std::vector<cudaGraphNode_t> nodes(active.size());
     for (size_t a = 0; e == cudaSuccess && a < active.size(); ++a) {
-      cudaGraphNode_t node;
-      e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, ps[active[a]]->graph);
+      e = cudaGraphAddChildGraphNode(&nodes[a], body, nullptr, 0, ps[active[a]]->graph);
       kernels_per_round += ps[active[a]]->graph_kernels;
+    }
+    if (e == cudaSuccess && device_loop) {
+      std::vector<int> idx(active.begin(), active.end());
+      e = cudaMemcpyAsync(didx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, bst);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(bst);
+      const int n_act = (int)active.size();
+      const int keep_above = n_act == 1 ? 0 : n_act - (n_act + 3) / 4;
+      capture_begin();
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(cst, body, nodes.data(), nullptr, nodes.size(),
+                                          cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        launch_batch_control(dstates, didx, n_act, keep_above, drounds, limit, handle, cst);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cst, &captured);
+      }
+      capture_end();
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, parent, 0);
     return e;
@@ -1703,7 +1807,11 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
   int check = ps[0]->opt.check_every > 0 ? ps[0]->opt.check_every : 4;
   int rounds = 0;
   while (!active.empty()) {
-    if (graphs) {
+    if (graphs && device_loop) {
+      PT_BATCH_CUDA(cudaMemsetAsync(drounds, 0, sizeof(int), bst));
+      PT_BATCH_CUDA(cudaGraphLaunch(exec, bst));
+      PT_BATCH_CUDA(cudaMemcpyAsync(hrounds, drounds, sizeof(int), cudaMemcpyDeviceToHost, bst));
+    } else if (graphs) {
       PT_BATCH_CUDA(cudaGraphLaunch(exec, bst));
       note_launch((int)kernels_per_round);
     } else {
@@ -1715,24 +1823,32 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
       }
       PT_BATCH_CUDA(cudaGetLastError());
     }
-    ++rounds;
-    if (rounds % check == 0 || rounds > max_rounds) {
+    if (graphs && device_loop) {
+      // the loop ran hrounds rounds on the device
       launch_gather_done(dstates, count, ddone, bst);
       PT_BATCH_CUDA(cudaMemcpyAsync(hdone, ddone, sizeof(int) * count, cudaMemcpyDeviceToHost, bst));
       PT_BATCH_CUDA(cudaStreamSynchronize(bst));
-      std::vector<int> still;
-      for (int i : active)
-        if (!hdone[i]) still.push_back(i);
-      const size_t finished = active.size() - still.size();
-      if (still.empty()) break;
-      if (rounds > max_rounds + 2) {
-        cleanup();
-        return fail(PT_ECUDA, "batch did not stop at max_it");
-      }
-      if (finished > 0 && finished * 4 >= active.size()) {  // drop finished problems from the graph
-        active.swap(still);
-        if (graphs) PT_BATCH_CUDA(rebuild());
-      }
+      rounds += *hrounds;
+      note_launch((int)((kernels_per_round + 1) * (unsigned long long)*hrounds));
+    } else {
+      ++rounds;
+      if (!(rounds % check == 0 || rounds > max_rounds)) continue;
+      launch_gather_done(dstates, count, ddone, bst);
+      PT_BATCH_CUDA(cudaMemcpyAsync(hdone, ddone, sizeof(int) * count, cudaMemcpyDeviceToHost, bst));
+      PT_BATCH_CUDA(cudaStreamSynchronize(bst));
+    }
+    std::vector<int> still;
+    for (int i : active)
+      if (!hdone[i]) still.push_back(i);
+    const size_t finished = active.size() - still.size();
+    if (still.empty()) break;
+    if (rounds > max_rounds + 2) {
+      cleanup();
+      return fail(PT_ECUDA, "batch did not stop at max_it");
+    }
+    if (finished > 0 && (device_loop || finished * 4 >= active.size())) {  // drop finished problems
+      active.swap(still);
+      if (graphs) PT_BATCH_CUDA(rebuild());
     }
   }
   PT_BATCH_CUDA(cudaStreamSynchronize(bst));
@@ -1808,6 +1924,24 @@ pt_status pt_apply_B(pt_problem* p, const double* u_dev, double* out_dev) {
   if (st != PT_OK) return st;
   if ((st = pack_into<double>(p, u_dev, p->tmpA)) != PT_OK) return st;
   launch_apply_B(p->tmpA, p->tmpB, geom<double>(p, 0), p->cth_d, steps_d(p), p->N, p->st);
+  PT_CHECK_LAUNCH();
+  return unpack_from<double>(p, p->tmpB, out_dev);
+}
+
+pt_status pt_apply_S(pt_problem* p, const double* u_dev, double* out_dev) {
+  g_err.clear();
+  if (!p || !u_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
+  if (p->mixed) return fail(PT_EINVAL, "pt_apply_S needs an FP64 problem");
+  PT_CUDA(cudaSetDevice(p->device));
+  pt_status st = ensure_tmp(p);
+  if (st != PT_OK) return st;
+  if ((st = pack_into<double>(p, u_dev, p->tmpA)) != PT_OK) return st;
+  const StencilGeom<double> g = geom<double>(p, 0);
+  // S u = K^T A~^-1 K u + (K + K^T + A) u = K^T (A~^-1 K u + u) + B u
+  launch_apply_K(p->tmpA, (double*)p->W1, g, steps_d(p).rho, p->N, p->st);
+  apply_precond_A<double>(p, (const double*)p->W1, p->W2, 0, 0, nullptr);
+  launch_apply_B(p->tmpA, p->tmpB, g, p->cth_d, steps_d(p), p->N, p->st);
+  launch_add_KT(p->tmpB, (const double*)p->W2, p->tmpA, g, p->N, p->st);
   PT_CHECK_LAUNCH();
   return unpack_from<double>(p, p->tmpB, out_dev);
 }

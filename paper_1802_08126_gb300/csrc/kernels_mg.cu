@@ -20,9 +20,9 @@ namespace {
 
 template <int DIM, typename T>
 __device__ __forceinline__ T diag_at(StencilGeom<T> g, T sig, T s, T cth, int x, int y, int z,
-                                     T* am, T* ap) {
+                                     T* am, T* ap, int mass) {
   face_coefs<DIM, T>(g.tab, g.P, x, y, z, cth, g.a0, am, ap);
-  return sig + s * g.h2inv * face_sum<DIM, T>(am, ap);
+  return sig * mass_diag<DIM, T>(mass) + s * g.h2inv * face_sum<DIM, T>(am, ap);
 }
 
 // x = w D^-1 b   (pre-smoothing from a zero iterate)
@@ -37,7 +37,7 @@ __global__ void k_jacobi0(const T* __restrict__ b, T* __restrict__ x, StencilGeo
     T v = (T)0;
     if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
       T am[3], ap[3];
-      const T D = diag_at<DIM, T>(g, op.sig[t], op.s, op.cth[t], xx, y, z, am, ap);
+      const T D = diag_at<DIM, T>(g, op.sig[t], op.s, op.cth[t], xx, y, z, am, ap, op.mass);
       v = op.omega * b[i] / D;
     }
     x[i] = v;
@@ -58,7 +58,8 @@ __global__ void k_residual(const T* __restrict__ b, const T* __restrict__ x, T* 
       T am[3], ap[3];
       face_coefs<DIM, T>(g.tab, g.P, xx, y, z, op.cth[t], g.a0, am, ap);
       const T xc = x[i];
-      v = b[i] - (op.sig[t] * xc + op.s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
+      v = b[i] - (op.sig[t] * mass_apply<DIM, T>(op.mass, x, i, xc, g.P) +
+                  op.s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
     }
     r[i] = v;
   }
@@ -76,7 +77,7 @@ __global__ void k_jacobi_update(const T* x, const T* __restrict__ r, void* out, 
     int xx, y, z;
     if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
       T am[3], ap[3];
-      const T D = diag_at<DIM, T>(g, op.sig[t], op.s, op.cth[t], xx, y, z, am, ap);
+      const T D = diag_at<DIM, T>(g, op.sig[t], op.s, op.cth[t], xx, y, z, am, ap, op.mass);
       store_out<T>(out, i, mode, out_fp64, x[i] + op.omega * r[i] / D);
     } else if (mode == 0) {
       store_out<T>(out, i, 0, out_fp64, (T)0);
@@ -244,7 +245,7 @@ __global__ void k_coarse_vcycle(const T* __restrict__ bglob, long long Sg, void*
       int xx, y, z;
       if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
         T am[3], ap[3];
-        const T D = diag_at<DIM, T>(g, sig, s, cth, xx, y, z, am, ap);
+        const T D = diag_at<DIM, T>(g, sig, s, cth, xx, y, z, am, ap, op.mass);
         x[i] = w * b[i] / D;
       }
     }
@@ -256,7 +257,8 @@ __global__ void k_coarse_vcycle(const T* __restrict__ bglob, long long Sg, void*
         T am[3], ap[3];
         face_coefs<DIM, T>(g.tab, g.P, xx, y, z, cth, g.a0, am, ap);
         const T xc = x[i];
-        r[i] = b[i] - (sig * xc + s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
+        r[i] = b[i] - (sig * mass_apply<DIM, T>(op.mass, x, i, xc, g.P) +
+                       s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
       }
     }
     __syncthreads();
@@ -301,7 +303,7 @@ __global__ void k_coarse_vcycle(const T* __restrict__ bglob, long long Sg, void*
     const StencilGeom<T> g = geom(l);
     if (threadIdx.x == 0) {
       T am[3], ap[3];
-      const T D = diag_at<DIM, T>(g, sig, s, cth, 0, 0, 0, am, ap);
+      const T D = diag_at<DIM, T>(g, sig, s, cth, 0, 0, 0, am, ap, op.mass);
       X(l)[0] = B(l)[0] / D;
     }
     __syncthreads();
@@ -327,7 +329,8 @@ __global__ void k_coarse_vcycle(const T* __restrict__ bglob, long long Sg, void*
         T am[3], ap[3];
         face_coefs<DIM, T>(g.tab, g.P, xx, y, z, cth, g.a0, am, ap);
         const T xc = x[i];
-        r[i] = b[i] - (sig * xc + s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
+        r[i] = b[i] - (sig * mass_apply<DIM, T>(op.mass, x, i, xc, g.P) +
+                       s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P));
       }
     }
     __syncthreads();
@@ -336,7 +339,7 @@ __global__ void k_coarse_vcycle(const T* __restrict__ bglob, long long Sg, void*
       int xx, y, z;
       if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
         T am[3], ap[3];
-        const T D = diag_at<DIM, T>(g, sig, s, cth, xx, y, z, am, ap);
+        const T D = diag_at<DIM, T>(g, sig, s, cth, xx, y, z, am, ap, op.mass);
         x[i] = x[i] + w * r[i] / D;
       }
     }
@@ -372,13 +375,14 @@ __global__ void k_tridiag(const T* __restrict__ r, void* out, int mode, int out_
   T* cp = work + (long long)b * 2 * g.P;
   T* dp = cp + g.P;
   const T sig = op.sig[b], cth = op.cth[b], sh = op.s * g.h2inv;
+  const T so = op.mass ? sig * (T)(1.0 / 6.0) : (T)0;  // P1 mass: sig/6 off the diagonal
   T prev_c = (T)0, prev_d = (T)0;
   for (int i = 0; i < n; ++i) {
     T am[1], ap[1];
     face_coefs<1, T>(g.tab, g.P, i, 0, 0, cth, g.a0, am, ap);
-    const T lo = i > 0 ? -sh * am[0] : (T)0;
-    const T up = i < n - 1 ? -sh * ap[0] : (T)0;
-    const T di = sig + sh * (am[0] + ap[0]);
+    const T lo = i > 0 ? so - sh * am[0] : (T)0;
+    const T up = i < n - 1 ? so - sh * ap[0] : (T)0;
+    const T di = sig * mass_diag<1, T>(op.mass) + sh * (am[0] + ap[0]);
     const T denom = di - lo * prev_c;
     prev_c = up / denom;
     prev_d = (r[base + i] - lo * prev_d) / denom;
@@ -414,10 +418,11 @@ __global__ void k_tridiag_pcr(const T* __restrict__ r, void* out, int mode, int 
   if (i < n) {
     T am[1], ap[1];
     const T sh = op.s * g.h2inv;
+    const T so = op.mass ? op.sig[b] * (T)(1.0 / 6.0) : (T)0;  // P1 mass: sig/6 off the diagonal
     face_coefs<1, T>(g.tab, P, i, 0, 0, op.cth[b], g.a0, am, ap);
-    ai = i > 0 ? -sh * am[0] : (T)0;
-    ci = i < n - 1 ? -sh * ap[0] : (T)0;
-    bi = op.sig[b] + sh * (am[0] + ap[0]);
+    ai = i > 0 ? so - sh * am[0] : (T)0;
+    ci = i < n - 1 ? so - sh * ap[0] : (T)0;
+    bi = op.sig[b] * mass_diag<1, T>(op.mass) + sh * (am[0] + ap[0]);
     ri = r[base + i];
   }
   sa[i] = ai;

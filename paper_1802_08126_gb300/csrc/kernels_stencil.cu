@@ -9,6 +9,66 @@ namespace pt {
 
 namespace {
 
+// (K (x) M) u at padded index i of slot t: M (u_t - u_{t-1}), u_{-1} := 0 (§2, eq. 2.3-2.4),
+// M the identity or the P1 mass (g.mass)
+template <int DIM>
+__device__ __forceinline__ double kdiff(const StencilGeom<double>& g, const double* __restrict__ u,
+                                        long long i, long long t, double uc) {
+  if (g.mass == 0) return uc - (t > 0 ? u[i - g.S] : 0.0);
+  double v = mass_p1<DIM, double>(u, i, uc, g.P);
+  if (t > 0) v -= mass_p1<DIM, double>(u, i - g.S, u[i - g.S], g.P);
+  return v;
+}
+
+// out = M v slice by slice (interior points; ghosts written zero)
+template <int DIM>
+__global__ void k_apply_mass(const double* __restrict__ v, double* __restrict__ out, StencilGeom<double> g,
+                             long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    out[i] = decode<DIM>(i, g.logP, g.n, t, x, y, z) ? mass_apply<DIM, double>(g.mass, v, i, v[i], g.P) : 0.0;
+  }
+}
+
+// out = rho_t M (u_t - u_{t-1}): the A~ input rho_t (K u)_t of the Schur complement apply
+template <int DIM>
+__global__ void k_apply_K(const double* __restrict__ u, double* __restrict__ out, StencilGeom<double> g,
+                          const double* __restrict__ rho, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    out[i] = decode<DIM>(i, g.logP, g.n, t, x, y, z) ? rho[t] * kdiff<DIM>(g, u, i, t, u[i]) : 0.0;
+  }
+}
+
+// acc += (K^T (x) M)(z + u): M (w_t - w_{t+1}), w = z + u, w_{N} := 0
+template <int DIM>
+__global__ void k_add_KT(double* __restrict__ acc, const double* __restrict__ zv, const double* __restrict__ u,
+                         StencilGeom<double> g, int N, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t;
+    int x, y, z;
+    if (!decode<DIM>(i, g.logP, g.n, t, x, y, z)) continue;
+    double w = mass_apply<DIM, double>(g.mass, zv, i, zv[i], g.P) + mass_apply<DIM, double>(g.mass, u, i, u[i], g.P);
+    if (t + 1 < N) {
+      const long long j = i + g.S;
+      w -= mass_apply<DIM, double>(g.mass, zv, j, zv[j], g.P) + mass_apply<DIM, double>(g.mass, u, j, u[j], g.P);
+    }
+    acc[i] += w;
+  }
+}
+
+// x = a x
+__global__ void k_scale(double* __restrict__ x, double a, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
 template <int DIM>
 __global__ void k_pack(const double* __restrict__ src, const double* __restrict__ u0,
                        double* __restrict__ dst, double scale, const double* __restrict__ scale_t, int n,
@@ -99,9 +159,8 @@ __global__ void k_apply_B(const double* __restrict__ u, double* __restrict__ out
       double am[3], ap[3];
       face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
       const double uc = u[i];
-      const double um = t > 0 ? u[i - g.S] : 0.0;
       const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
-      v = (uc - um) + sp.tau[t] * Au;
+      v = kdiff<DIM>(g, u, i, t, uc) + sp.tau[t] * Au;
     }
     out[i] = v;
   }
@@ -125,8 +184,7 @@ __global__ void k_resid_p(const double* __restrict__ u, const double* __restrict
       face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
       const double pc = p[i];
       const double Ap = stencil_sum<DIM, double>(p, i, pc, am, ap, g.P) * g.h2inv;
-      const double um = t > 0 ? u[i - g.S] : 0.0;
-      v = ((u[i] - um) - sp.tau[t] * Ap - F[i]) * sp.rho[t];
+      v = (kdiff<DIM>(g, u, i, t, u[i]) - sp.tau[t] * Ap - F[i]) * sp.rho[t];
     }
     rp[i] = (Tp)v;
   }
@@ -152,11 +210,19 @@ __global__ void k_resid_u(const double* __restrict__ u, const double* __restrict
       face_coefs<DIM, double>(g.tab, g.P, x, y, z, cth[t], g.a0, am, ap);
       const double uc = u[i];
       const double Au = stencil_sum<DIM, double>(u, i, uc, am, ap, g.P) * g.h2inv;
-      const double um = t > 0 ? u[i - g.S] : 0.0;
-      const double bres = F[i] - (uc - um) - sp.tau[t] * Au;
-      const double next = t + 1 < N ? p[i + g.S] + u[i + g.S] : 0.0;
-      v = bres - (p[i] + uc) + next;
+      const double bres = F[i] - kdiff<DIM>(g, u, i, t, uc) - sp.tau[t] * Au;
       acc += bres * bres;
+      if (g.mass == 0) {
+        const double next = t + 1 < N ? p[i + g.S] + u[i + g.S] : 0.0;
+        v = bres - (p[i] + uc) + next;
+      } else {  // M (w_t - w_{t+1}), w = p + u
+        double mw = mass_p1<DIM, double>(p, i, p[i], g.P) + mass_p1<DIM, double>(u, i, uc, g.P);
+        if (t + 1 < N) {
+          const long long j = i + g.S;
+          mw -= mass_p1<DIM, double>(p, j, p[j], g.P) + mass_p1<DIM, double>(u, j, u[j], g.P);
+        }
+        v = bres - mw;
+      }
     }
     ru[i] = (Tp)v;
   }
@@ -306,6 +372,23 @@ __global__ void k_gather_done(SolveState* const* __restrict__ states, int count,
     out[i] = states[i]->done == 1;
 }
 
+// Control of the device-side batch loop (the body of a conditional WHILE graph node holds one
+// iteration of every active problem and this kernel): counts the active problems that have not
+// finished, advances the round counter, and keeps the loop going while more than `keep_above`
+// are unfinished and fewer than `limit` rounds have run (the limit bounds the loop on the device
+// whatever the states say).  One block.
+__global__ void k_batch_control(SolveState* const* __restrict__ states, const int* __restrict__ idx, int count,
+                                int keep_above, int* __restrict__ rounds, int limit,
+                                cudaGraphConditionalHandle handle) {
+  int open = 0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) open += states[idx[i]]->done != 1;
+  const double total = block_sum((double)open);
+  if (threadIdx.x == 0) {
+    const int r = ++(*rounds);
+    cudaGraphSetConditional(handle, ((int)total > keep_above && r < limit) ? 1u : 0u);
+  }
+}
+
 // x[i] *= f[i >> logS]: one factor per slot of 2^logS elements
 template <typename T>
 __global__ void k_scale_slices(T* __restrict__ x, const T* __restrict__ f, int logS, long long total) {
@@ -438,6 +521,31 @@ void launch_apply_A_scaled(const T* z, T* out, StencilGeom<T> g, T cth, T scale,
   PT_DISPATCH_DIM(g.dim, k_apply_A_scaled<D, T><<<grid_for(total), kThreads, 0, st>>>(z, out, g, cth, scale, total, done));
 }
 
+void launch_apply_mass(const double* v, double* out, StencilGeom<double> g, int N, cudaStream_t st) {
+  const long long total = g.S * N;
+  double d = N;
+  for (int k = 0; k < g.dim; ++k) d *= g.n;
+  LaunchScope ls("apply_mass", st, 16.0 * d);
+  PT_DISPATCH_DIM(g.dim, k_apply_mass<D><<<grid_for(total), kThreads, 0, st>>>(v, out, g, total));
+}
+
+void launch_apply_K(const double* u, double* out, StencilGeom<double> g, const double* rho, int N, cudaStream_t st) {
+  const long long total = g.S * N;
+  LaunchScope ls("apply_K", st, 16.0 * (double)total);
+  PT_DISPATCH_DIM(g.dim, k_apply_K<D><<<grid_for(total), kThreads, 0, st>>>(u, out, g, rho, total));
+}
+
+void launch_add_KT(double* acc, const double* z, const double* u, StencilGeom<double> g, int N, cudaStream_t st) {
+  const long long total = g.S * N;
+  LaunchScope ls("add_KT", st, 32.0 * (double)total);
+  PT_DISPATCH_DIM(g.dim, k_add_KT<D><<<grid_for(total), kThreads, 0, st>>>(acc, z, u, g, N, total));
+}
+
+void launch_scale(double* x, double a, long long total, cudaStream_t st) {
+  LaunchScope ls("scale", st, 16.0 * (double)total);
+  k_scale<<<grid_for(total), kThreads, 0, st>>>(x, a, total);
+}
+
 void launch_norm2_partials(const double* v, long long count, double* partials, cudaStream_t st) {
   LaunchScope ls("norm2", st, 8.0 * (double)count);
   k_norm2_partials<<<kReduceBlocks, kThreads, 0, st>>>(v, count, partials);
@@ -452,6 +560,12 @@ void launch_finalize_fnorm(const double* partials, SolveState* state, double tol
                            cudaStream_t st) {
   LaunchScope ls("finalize", st, 8.0 * kReduceBlocks);
   k_finalize_fnorm<<<1, kReduceBlocks, 0, st>>>(partials, state, tol, max_it);
+}
+
+void launch_batch_control(SolveState* const* states, const int* idx, int count, int keep_above, int* rounds,
+                          int limit, cudaGraphConditionalHandle handle, cudaStream_t st) {
+  LaunchScope ls("batch_control", st, 0.0);
+  k_batch_control<<<1, 256, 0, st>>>(states, idx, count, keep_above, rounds, limit, handle);
 }
 
 void launch_gather_done(SolveState* const* states, int count, int* out, cudaStream_t st) {

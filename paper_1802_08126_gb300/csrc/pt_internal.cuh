@@ -80,6 +80,7 @@ struct StencilGeom {
   const T* tab;   // level tables: node_x, face_x, node_y, face_y, node_z, face_z (P each)
   T a0;
   T h2inv;        // 1/h^2
+  int mass = 0;   // mass matrix M of eq. 2.1 in K (x) M: 0 = identity, 1 = P1 mass over h^d (dim <= 2)
 };
 
 // Per-step factors of the time grid (§2, eq. 2.1), [N] each: the step lengths tau_n, and against
@@ -98,10 +99,11 @@ struct Steps {
 // Batched operator L_b = sig[b] I + s * A(cth[b]) on one level, used by the V-cycle.
 template <typename T>
 struct OpBatch {
-  const T* sig;   // [B] identity shift (0 for tau_n A_n, mu_k for H_k)
+  const T* sig;   // [B] mass shift (0 for tau_n A_n, mu_k for H_k = mu_k M + tau Abar)
   const T* cth;   // [B] coefficient time factors (times c)
   T s;            // scale of A (tau)
   T omega;        // Jacobi weight
+  int mass = 0;   // M in sig M + s A: 0 = identity, 1 = P1 mass over h^d (dim <= 2)
 };
 
 // ---- stencil / residual kernels (kernels_stencil.cu) --------------------------------------
@@ -164,6 +166,12 @@ void launch_scale_slices(T* x, const T* f, int logS, long long total, cudaStream
 
 // partial sums of ||v||^2 (padded vector, ghosts are zero)
 void launch_norm2_partials(const double* v, long long count, double* partials, cudaStream_t st);
+// out = M v per slice (g.mass: identity or P1 mass), x = a x
+void launch_apply_mass(const double* v, double* out, StencilGeom<double> g, int N, cudaStream_t st);
+void launch_scale(double* x, double a, long long total, cudaStream_t st);
+// out = rho_t (K (x) M) u;  acc += (K^T (x) M)(z + u)   (the Schur complement apply, eq. 2.5)
+void launch_apply_K(const double* u, double* out, StencilGeom<double> g, const double* rho, int N, cudaStream_t st);
+void launch_add_KT(double* acc, const double* z, const double* u, StencilGeom<double> g, int N, cudaStream_t st);
 
 // Device state of one solve.
 struct SolveState {
@@ -218,6 +226,10 @@ void launch_finalize_fnorm(const double* partials, SolveState* state, double tol
 
 // out[i] = states[i]->done for a batch of solves
 void launch_gather_done(SolveState* const* states, int count, int* out, cudaStream_t st);
+// the control kernel of the device-side batch loop (see pt_solve_batch): rounds += 1; continue
+// while more than keep_above of states[idx[0..count)] are unfinished and rounds < limit
+void launch_batch_control(SolveState* const* states, const int* idx, int count, int keep_above, int* rounds,
+                          int limit, cudaGraphConditionalHandle handle, cudaStream_t st);
 
 // elementwise y += a * x over count padded entries (x in Tp)
 template <typename Tp>

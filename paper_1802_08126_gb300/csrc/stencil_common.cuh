@@ -85,6 +85,34 @@ __device__ __forceinline__ T stencil_sum(const V* __restrict__ v, long long i, T
   return s;
 }
 
+// (M v)_i for the P1 finite-element mass matrix over h^d (the M of eq. 2.1 when it is not the
+// identity): 1-D [1/6, 2/3, 1/6]; 2-D, every grid square cut along its lower-left to upper-right
+// diagonal: 1/2 at the point and 1/12 at the four axis neighbours and at the upper-right and
+// lower-left diagonal ones.  Out-of-grid neighbours are the padded layout's zero ghosts (the
+// lower-left one of the first point of a slice is a guard or the previous slice's ghost column).
+template <int DIM, typename T, typename V>
+__device__ __forceinline__ T mass_p1(const V* __restrict__ v, long long i, T vc, int P) {
+  if (DIM == 1) return (T)(2.0 / 3.0) * vc + (T)(1.0 / 6.0) * ((T)v[i - 1] + (T)v[i + 1]);
+  if (DIM == 2) {
+    const T s = ((T)v[i - 1] + (T)v[i + 1]) + ((T)v[i - P] + (T)v[i + P]) +
+                ((T)v[i - P - 1] + (T)v[i + P + 1]);
+    return (T)0.5 * vc + (T)(1.0 / 12.0) * s;
+  }
+  return vc;  // (no P1 form in 3-D)
+}
+
+// diagonal entry of that mass matrix
+template <int DIM, typename T>
+__device__ __forceinline__ T mass_diag(int mass) {
+  return mass == 0 ? (T)1 : (DIM == 1 ? (T)(2.0 / 3.0) : (DIM == 2 ? (T)0.5 : (T)1));
+}
+
+// (M v)_i with M the identity (mass == 0) or the P1 mass
+template <int DIM, typename T, typename V>
+__device__ __forceinline__ T mass_apply(int mass, const V* __restrict__ v, long long i, T vc, int P) {
+  return mass == 0 ? vc : mass_p1<DIM, T, V>(v, i, vc, P);
+}
+
 template <int DIM, typename T>
 __device__ __forceinline__ T face_sum(const T* am, const T* ap) {
   T s = am[0] + ap[0];

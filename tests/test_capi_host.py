@@ -40,7 +40,8 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
-def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, krylov=0, precision=0, steps=None):
+def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, mass=0, krylov=0, precision=0, steps=None,
+            h_solver=0):
     g = _lib.Grid()
     g.dim = dim
     for d in range(3):
@@ -50,7 +51,8 @@ def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, kry
     o = _lib.Options()
     o.spatial_solver = solver
     o.n_vcycles = nv
-    o.reserved[0] = reserved
+    o.mass = mass
+    o.h_solver = h_solver
     o.krylov = krylov
     o.precision = precision
     if steps is not None:
@@ -64,7 +66,9 @@ def _create(lib, dim=2, n=7, N=8, c=0.5, a0=1.0, solver=0, nv=0, reserved=0, kry
 
 
 @pytest.mark.parametrize("kw", [dict(n=6), dict(N=3000), dict(N=0), dict(dim=4), dict(c=1.0),
-                                dict(solver=1, dim=2), dict(nv=5), dict(reserved=1), dict(krylov=65),
+                                dict(solver=1, dim=2), dict(nv=5), dict(mass=2), dict(mass=-1), dict(krylov=65),
+                                dict(mass=1, dim=3), dict(mass=1, precision=1), dict(mass=1, krylov=4),
+                                dict(mass=1, h_solver=2),
                                 dict(krylov=-1), dict(krylov=10, precision=1),
                                 dict(steps=[0.125] * 7 + [0.0]), dict(steps=[0.125] * 7 + [-0.125]),
                                 dict(steps=[0.125] * 7 + [float("nan")]), dict(steps=[0.125] * 7 + [0.126]),
@@ -79,6 +83,7 @@ def test_invalid_arguments_rejected_on_host(lib, kw):
 def test_null_pointers_rejected(lib):
     assert lib.pt_solve(None, 1e-8, 10, None, 0, None, None) == _lib.PT_EINVAL
     assert lib.pt_apply_B(None, None, None) == _lib.PT_EINVAL
+    assert lib.pt_apply_S(None, None, None) == _lib.PT_EINVAL
     lib.pt_problem_destroy(None)
     assert lib.pt_status_string(3) == b"PT_ENOTCONV"
 
