@@ -402,7 +402,7 @@ def headline_config(prob, tol, omega, ws, precision="fp64", solver="mg"):
     return {"workload": WORKLOAD, "grid": list(prob.n), "precision": precision, "N_t": prob.N, "T": prob.T,
             "dofs_per_gpu": prob.dofs, "tol": tol, "omega": omega,
             "spatial_solver": spatial_solver_label(prob.dim, solver, "auto"),
-            "l2": "inputs larger than L2 (%d MiB per space-time vector)" % (prob.dofs * 8 >> 20),
+            "l2": "inputs larger than L2 (%d MB per space-time vector)" % (prob.dofs * 8 >> 20),
             "parallelism": "replicas" if ws > 1 else "single"}
 
 

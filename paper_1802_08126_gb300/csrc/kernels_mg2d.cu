@@ -341,19 +341,14 @@ __global__ void __launch_bounds__(256) k_mg2s_down(const T* __restrict__ bf, T* 
   Faces<T, VAR> fm, fc, fn;
   row(yfirst, ld_b(yfirst), bm, xm, fm);
   row(yfirst + 1, ld_b(yfirst + 1), bc_, xc, fc);
-  // load queue: b of rows y+1 .. y+4 at row y (the strip needs b up to row ylast + 1)
-  auto ld_bq = [&](int y) -> T { return y <= ylast + 1 ? ld_b(y) : (T)0; };
-  T bq0 = ld_bq(yfirst + 2), bq1 = ld_bq(yfirst + 3), bq2 = ld_bq(yfirst + 4), bq3 = ld_bq(yfirst + 5);
+  T b_next = ld_b(yfirst + 2);  // b of the row after next, loaded one iteration ahead
   T h1 = (T)0, h2 = (T)0;  // horizontal restrictions of the two previous rows
   const bool out_lane = (lane & 1) == 0 && lane >= 2 && lane <= 28;
   const int X = X0 + (lane >> 1) - 1;  // coarse column of an output lane (x = 2X + 1)
   for (int y = yfirst + 1; y <= ylast; ++y) {
-    const T b_new = ld_bq(y + 5);
-    row(y + 1, bq0, bn, xn, fn);
-    bq0 = bq1;
-    bq1 = bq2;
-    bq2 = bq3;
-    bq3 = b_new;
+    const T b_after = ld_b(y + 2);
+    row(y + 1, b_next, bn, xn, fn);
+    b_next = b_after;
     // residual of x1 at row y
     const T xW = __shfl_up_sync(0xffffffffu, xc, 1);
     const T xE = __shfl_down_sync(0xffffffffu, xc, 1);
@@ -475,25 +470,14 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
   Faces<T, VAR> fm, fc, fn;
   row(y0 - 1, ld_b(y0 - 1), bm, xm, jm, dm_, fm);
   row(y0, ld_b(y0), bcv, xc, jc, dc_, fc);
-  // load queues: b of rows y+1 .. y+4 and the accumulation target of rows y .. y+2 at row y (the
-  // strip needs b up to its last row + 1 and the target up to its last row)
-  const int ylim = y0 + kStripUpRows;
-  auto ld_bq = [&](int y) -> T { return y <= ylim ? ld_b(y) : (T)0; };
-  auto ld_oq = [&](int y) -> double { return y < ylim ? ld_o(y) : 0.0; };
-  T bq0 = ld_bq(y0 + 1), bq1 = ld_bq(y0 + 2), bq2 = ld_bq(y0 + 3), bq3 = ld_bq(y0 + 4);
-  double oq0 = ld_oq(y0), oq1 = ld_oq(y0 + 1), oq2 = ld_oq(y0 + 2);
+  T b_next = ld_b(y0 + 1);
+  double o_next = ld_o(y0);
   for (int y = y0; y < y0 + kStripUpRows && y < Pf; ++y) {
-    const T b_new = ld_bq(y + 5);
-    const double o_new = ld_oq(y + 3);
-    const double o_cur = oq0;
-    row(y + 1, bq0, bn, xn, jn, dn_, fn);
-    bq0 = bq1;
-    bq1 = bq2;
-    bq2 = bq3;
-    bq3 = b_new;
-    oq0 = oq1;
-    oq1 = oq2;
-    oq2 = o_new;
+    const T b_after = ld_b(y + 2);
+    const double o_cur = o_next;
+    o_next = ld_o(y + 1);
+    row(y + 1, b_next, bn, xn, jn, dn_, fn);
+    b_next = b_after;
     const T xW = __shfl_up_sync(0xffffffffu, xc, 1);
     const T xE = __shfl_down_sync(0xffffffffu, xc, 1);
     if (wlane) {
