@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-3d", action="store_true", help="leave out the 3-D entry")
     ap.add_argument("--batch-sample", type=int, default=64,
                     help="problems of the batch distribution in the default line's batch entry (0: none)")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="run exactly this many iterations of one solve of the workload and exit (for ncu)")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -687,6 +689,12 @@ def main():
     u0 = S.initial(prob)
     P = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision=prec, omega=args.omega,
                     solver=solver)
+    if args.profile_iters > 0:
+        # a fixed number of iterations (launch lists and counter captures), no measurement
+        P.solve(0.0, args.profile_iters)
+        torch.cuda.synchronize()
+        P.close()
+        return 0
     for _ in range(args.warmup):
         st, it, _ = P.solve(args.tol, args.max_it)
         if st != 0:
