@@ -520,6 +520,252 @@ __global__ void __launch_bounds__(256) k_mg2s_up(const T* __restrict__ bf, const
   (void)fm;
 }
 
+// ---- FP32 forms of the two strip kernels (the V-cycles of the mixed-precision path) ----
+// Same sweep, geometry and arithmetic order as k_mg2s_down / k_mg2s_up with a variable
+// coefficient and the Jacobi factor formed per point, with the per-row work cut down: the lane's
+// x-tables and interpolation weights are loaded once, indices are 32-bit offsets within the
+// slice, the output mode is a template parameter, and the Jacobi factor w / D uses the fast
+// reciprocal (the same factor in the down and the up kernel of a level, so the V-cycle stays
+// symmetric).
+
+// per-lane constants of a fine column x: x-face table values, the y-face factor and the
+// coarse columns and weights of the linear interpolation along x
+struct LaneCols {
+  float fxl, fxr, gxn;  // g_x at the lower / upper x-face, (s/h^2) c g_t(t) g_x(x) for the y-faces
+  int c0, c1;           // coarse columns of the interpolation (clamped in range)
+  float w0, w1;         // their weights (0 outside the coarse interior)
+};
+
+__device__ __forceinline__ LaneCols lane_cols(const Mg2Args<float>& a, int x, float cths) {
+  const int Pf = 1 << a.logPf;
+  LaneCols c;
+  const bool xin = x >= 0 && x < a.nf;
+  c.fxl = xin ? a.tab[Pf + x] : 0.f;
+  c.fxr = xin ? a.tab[Pf + x + 1] : 0.f;
+  c.gxn = xin ? cths * a.tab[x] : 0.f;
+  int c0, c1;
+  float w0, w1;
+  if (x & 1) {  // fine 2X + 1 sits on coarse X
+    c0 = (x - 1) >> 1;
+    c1 = c0;
+    w0 = 1.f;
+    w1 = 0.f;
+  } else {      // fine 2X sits between coarse X - 1 and X
+    c0 = (x >> 1) - 1;
+    c1 = x >> 1;
+    w0 = 0.5f;
+    w1 = 0.5f;
+  }
+  if (!xin) w0 = w1 = 0.f;
+  if (c0 < 0 || c0 >= a.nc) {
+    w0 = 0.f;
+    c0 = 0;
+  }
+  if (c1 < 0 || c1 >= a.nc) {
+    w1 = 0.f;
+    c1 = 0;
+  }
+  c.c0 = c0;
+  c.c1 = c1;
+  c.w0 = w0;
+  c.w1 = w1;
+  return c;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_mg2s_up_f32(const float* __restrict__ bf, const float* __restrict__ ec,
+                                                     float* __restrict__ out, Mg2Args<float> a, int wpr, int strips,
+                                                     long long nwarps, const int* done) {
+  if (stop_requested(done)) return;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (wg >= nwarps) return;
+  const int lane = threadIdx.x & 31;
+  const int wx = (int)(wg % wpr);
+  const long long rest = wg / wpr;
+  const int strip = (int)(rest % strips);
+  const int b = (int)(rest / strips);
+  const int x = kStripUpCols * wx - 1 + lane;  // fine column; lanes 1..30 write
+  const int y0 = kStripUpRows * strip;
+  const int nf = a.nf, nc = a.nc, Pf = 1 << a.logPf, Pc = 1 << a.logPc;
+  const bool xin = x >= 0 && x < nf;
+  const float* __restrict__ bs = bf + (long long)b * a.Sf;
+  float* __restrict__ os = out + (long long)b * a.Sf;
+  const float* __restrict__ es = ec + (long long)b * a.Sc;
+  const float sig = a.sig[b];
+  const float cths = a.s_h2 * a.cth[b];
+  const float a0s = a.a0s, omega = a.omega;
+  const float* ny = a.tab + 2 * Pf;
+  const float* fy = a.tab + 3 * Pf;
+  const LaneCols lc = lane_cols(a, x, cths);
+  // x-interpolated coarse row Yc at this lane's column
+  auto crow = [&](int Yc) -> float {
+    if (Yc < 0 || Yc >= nc) return 0.f;
+    const float* er = es + Yc * Pc;
+    return fmaf(lc.w0, er[lc.c0], lc.w1 * er[lc.c1]);
+  };
+  float ex_lo = 0.f;  // crow of the coarse row below the next even row
+  int k_lo = -1000;
+  auto ld_b = [&](int y) -> float { return (xin && y >= 0 && y < nf) ? bs[y * Pf + x] : 0.f; };
+  const bool wlane = lane >= 1 && lane <= 30 && x < Pf;
+  auto ld_o = [&](int y) -> float { return (MODE == 1 && wlane && xin && y < nf) ? os[y * Pf + x] : 0.f; };
+  float fy_carry = (y0 - 1 >= 0 && y0 - 1 <= nf) ? fy[y0 - 1] : 0.f;  // y-face table below the first row
+  // one fine row: faces, Jacobi factor, and x2 = w D^-1 b + P e
+  auto row = [&](int y, float bv_in, float& bv, float& x2, float& jf, float& xl, float& xr, float& yl,
+                 float& yu) {
+    const bool yin = y >= 0 && y < nf;
+    const float gy = yin ? cths * ny[y] : 0.f;
+    const float fyu = (y + 1 >= 0 && y + 1 <= nf) ? fy[y + 1] : 0.f;
+    xl = fmaf(gy, lc.fxl, a0s);
+    xr = fmaf(gy, lc.fxr, a0s);
+    yl = fmaf(lc.gxn, fy_carry, a0s);
+    yu = fmaf(lc.gxn, fyu, a0s);
+    fy_carry = fyu;
+    float pe;
+    if (y & 1) {
+      const int k = (y - 1) >> 1;
+      ex_lo = (k_lo == k) ? ex_lo : crow(k);
+      k_lo = k;
+      pe = ex_lo;
+    } else {
+      const int k = y >> 1;
+      const float lo = (k_lo == k - 1) ? ex_lo : crow(k - 1);
+      const float hi = crow(k);
+      pe = 0.5f * (lo + hi);
+      ex_lo = hi;
+      k_lo = k;
+    }
+    const bool in = xin && yin;
+    bv = in ? bv_in : 0.f;
+    jf = __fdividef(omega, sig + ((xl + xr) + (yl + yu)));
+    x2 = in ? fmaf(bv, jf, pe) : 0.f;
+  };
+  float bm, xm, jm, xlm, xrm, ylm, yum;
+  float bc, xc, jc, xlc, xrc, ylc, yuc;
+  float bn, xn, jn, xln, xrn, yln, yun;
+  row(y0 - 1, ld_b(y0 - 1), bm, xm, jm, xlm, xrm, ylm, yum);
+  row(y0, ld_b(y0), bc, xc, jc, xlc, xrc, ylc, yuc);
+  float b_next = ld_b(y0 + 1);
+  float o_next = ld_o(y0);
+  const int yend = min(y0 + kStripUpRows, Pf);
+  for (int y = y0; y < yend; ++y) {
+    const float b_after = ld_b(y + 2);
+    const float o_cur = o_next;
+    o_next = ld_o(y + 1);
+    row(y + 1, b_next, bn, xn, jn, xln, xrn, yln, yun);
+    b_next = b_after;
+    const float xW = __shfl_up_sync(0xffffffffu, xc, 1);
+    const float xE = __shfl_down_sync(0xffffffffu, xc, 1);
+    if (wlane) {
+      const int gi = y * Pf + x;
+      if (xin && y < nf) {
+        const float Lx = sig * xc + xlc * (xc - xW) + xrc * (xc - xE) + ylc * (xc - xm) + yuc * (xc - xn);
+        const float v = xc + jc * (bc - Lx);
+        os[gi] = MODE == 1 ? o_cur + v : v;
+      } else if (MODE == 0) {
+        os[gi] = 0.f;
+      }
+    }
+    xm = xc;
+    bc = bn;
+    xc = xn;
+    jc = jn;
+    xlc = xln;
+    xrc = xrn;
+    ylc = yln;
+    yuc = yun;
+  }
+  (void)bm;
+  (void)jm;
+  (void)xlm;
+  (void)xrm;
+  (void)ylm;
+  (void)yum;
+}
+
+__global__ void __launch_bounds__(256) k_mg2s_down_f32(const float* __restrict__ bf, float* __restrict__ bcg,
+                                                       Mg2Args<float> a, int wpr, int strips, long long nwarps,
+                                                       const int* done) {
+  if (stop_requested(done)) return;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (wg >= nwarps) return;
+  const int lane = threadIdx.x & 31;
+  const int wx = (int)(wg % wpr);
+  const long long rest = wg / wpr;
+  const int strip = (int)(rest % strips);
+  const int b = (int)(rest / strips);
+  const int X0 = kStripDownCols * wx, Y0 = kStripDownRows * strip;
+  const int x = 2 * X0 - 1 + lane;  // fine column of this lane
+  const int nf = a.nf, Pf = 1 << a.logPf, Pc = 1 << a.logPc;
+  const bool xin = x >= 0 && x < nf;
+  const float* __restrict__ bs = bf + (long long)b * a.Sf;
+  float* __restrict__ cs = bcg + (long long)b * a.Sc;
+  const float sig = a.sig[b];
+  const float cths = a.s_h2 * a.cth[b];
+  const float a0s = a.a0s, omega = a.omega;
+  const float* ny = a.tab + 2 * Pf;
+  const float* fy = a.tab + 3 * Pf;
+  const LaneCols lc = lane_cols(a, x, cths);
+  const int yfirst = 2 * Y0 - 1, ylast = 2 * (Y0 + kStripDownRows);
+  float fy_carry = (yfirst >= 0 && yfirst <= nf) ? fy[yfirst] : 0.f;
+  auto ld_b = [&](int y) -> float { return (xin && y >= 0 && y < nf) ? bs[y * Pf + x] : 0.f; };
+  // x1 = w D^-1 b and the faces of row y
+  auto row = [&](int y, float bv_in, float& bv, float& x1, float& xl, float& xr, float& yl, float& yu) {
+    const bool yin = y >= 0 && y < nf;
+    const float gy = yin ? cths * ny[y] : 0.f;
+    const float fyu = (y + 1 >= 0 && y + 1 <= nf) ? fy[y + 1] : 0.f;
+    xl = fmaf(gy, lc.fxl, a0s);
+    xr = fmaf(gy, lc.fxr, a0s);
+    yl = fmaf(lc.gxn, fy_carry, a0s);
+    yu = fmaf(lc.gxn, fyu, a0s);
+    fy_carry = fyu;
+    const bool in = xin && yin;
+    bv = in ? bv_in : 0.f;
+    x1 = in ? bv * __fdividef(omega, sig + ((xl + xr) + (yl + yu))) : 0.f;
+  };
+  float bm, xm, xlm, xrm, ylm, yum;
+  float bc, xc, xlc, xrc, ylc, yuc;
+  float bn, xn, xln, xrn, yln, yun;
+  row(yfirst, ld_b(yfirst), bm, xm, xlm, xrm, ylm, yum);
+  row(yfirst + 1, ld_b(yfirst + 1), bc, xc, xlc, xrc, ylc, yuc);
+  float b_next = ld_b(yfirst + 2);
+  float h1 = 0.f, h2 = 0.f;  // horizontal restrictions of the two previous rows
+  const bool out_lane = (lane & 1) == 0 && lane >= 2 && lane <= 28;
+  const int X = X0 + (lane >> 1) - 1;  // coarse column of an output lane (x = 2X + 1)
+  for (int y = yfirst + 1; y <= ylast; ++y) {
+    const float b_after = ld_b(y + 2);
+    row(y + 1, b_next, bn, xn, xln, xrn, yln, yun);
+    b_next = b_after;
+    const float xW = __shfl_up_sync(0xffffffffu, xc, 1);
+    const float xE = __shfl_down_sync(0xffffffffu, xc, 1);
+    float r = 0.f;
+    if (xin && y >= 0 && y < nf) {
+      const float Lx = sig * xc + xlc * (xc - xW) + xrc * (xc - xE) + ylc * (xc - xm) + yuc * (xc - xn);
+      r = bc - Lx;
+    }
+    const float rW = __shfl_up_sync(0xffffffffu, r, 1);
+    const float rE = __shfl_down_sync(0xffffffffu, r, 1);
+    const float h = 0.25f * (rW + rE) + 0.5f * r;
+    if (y >= 2 * Y0 + 2 && ((y - 2 * Y0) & 1) == 0) {
+      const int Y = (y >> 1) - 1;
+      if (out_lane && X < a.nc && Y < a.nc) cs[Y * Pc + X] = 0.25f * (h2 + h) + 0.5f * h1;
+    }
+    h2 = h1;
+    h1 = h;
+    xm = xc;
+    bc = bn;
+    xc = xn;
+    xlc = xln;
+    xrc = xrn;
+    ylc = yln;
+    yuc = yun;
+  }
+  (void)bm;
+  (void)xlm;
+  (void)xrm;
+  (void)ylm;
+  (void)yum;
+}
+
 // (w D^-1, D) for every interior point of one level (FP64 variable-coefficient cache)
 template <typename T>
 __global__ void k_make_jinv(T* __restrict__ jinv, StencilGeom<T> g, OpBatch<T> op, long long total) {
@@ -581,6 +827,13 @@ void vcycle2d(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int 
       const int strips = (a.nc + kStripDownRows - 1) / kStripDownRows;
       const long long nw = (long long)wpr * strips * B;
       const unsigned blocks = (unsigned)((nw + 7) / 8);
+      if constexpr (std::is_same<T, float>::value) {
+        if (dm == 2) {
+          k_mg2s_down_f32<<<blocks, 256, 0, st>>>(bl, bc, a, wpr, strips, nw, done);
+          bl = bc;
+          continue;
+        }
+      }
       if (dm == 0)
         k_mg2s_down<T, false, 0><<<blocks, 256, 0, st>>>(bl, bc, a, wpr, strips, nw, done);
       else if (dm == 1)
@@ -613,6 +866,15 @@ void vcycle2d(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, int 
       const int strips = (Pf + kStripUpRows - 1) / kStripUpRows;
       const long long nw = (long long)wpr * strips * B;
       const unsigned blocks = (unsigned)((nw + 7) / 8);
+      if constexpr (std::is_same<T, float>::value) {
+        if (dm == 2 && !of) {
+          if (om == 1)
+            k_mg2s_up_f32<1><<<blocks, 256, 0, st>>>(bf, e, (float*)o, a, wpr, strips, nw, done);
+          else
+            k_mg2s_up_f32<0><<<blocks, 256, 0, st>>>(bf, e, (float*)o, a, wpr, strips, nw, done);
+          continue;
+        }
+      }
       if (dm == 0)
         k_mg2s_up<T, false, 0><<<blocks, 256, 0, st>>>(bf, e, o, om, of, a, wpr, strips, nw, done);
       else if (dm == 1)
