@@ -187,10 +187,7 @@ def fp64_flops_per_launch(name, dim, n, N):
         return N * n * 2 * fft_M + 1.0 * pts  # precomputed block-solve factor
     if name == "dsti_rows":
         return N * n * fft_M
-    if name in ("dst_forward", "dst_forward_ru", "dst_inverse"):  # N-point transform of every spatial point
-        # + twiddles (dst_forward_ru also forms r_u = b - K^T (p + u) while loading: 4 adds)
-        if name == "dst_forward_ru":
-            return n * n * (2.5 * N * math.log2(N) + 10.0 * N)
+    if name in ("dst_forward", "dst_inverse"):  # N-point transform of every spatial point + twiddles
         return n * n * (2.5 * N * math.log2(N) + 6.0 * N)
     if name == "hsolve_y":          # per (k, x-frequency) column: two Thomas eliminations (6 flops
         return 16.0 * pts            # each: multiply-add, multiply) and the tridiagonal product (4)

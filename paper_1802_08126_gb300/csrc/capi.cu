@@ -14,7 +14,6 @@
 #include <mutex>
 #include <sstream>
 #include <string>
-#include <type_traits>
 #include <vector>
 
 #include "pt_internal.cuh"
@@ -431,19 +430,8 @@ void enqueue_iteration(pt_problem* p) {
                       (const float*)p->cthA, steps_f(p), p->N, p->state, p->st);
     launch_ir_finalize(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->ir_dp, 1, 0, done);
-    if (dst_fuses_ru(dp)) {
-      // r_u' = b' - K^T (dp + du) formed by the transform's loads (R2 instead of b' on the FP64 step)
-      FusedRu<T> fr;
-      fr.b = (const T*)p->ir_bp;
-      fr.b_alt = (const T*)p->ir_R2;
-      fr.use_alt = &p->state->outer;
-      fr.wa = (const T*)p->ir_dp;
-      fr.wb = (const T*)p->ir_du;
-      launch_dst_forward<T>(W1, L0.S, p->dim, p->n, L0.logP, dp, done, p->st, &fr);
-    } else {
-      launch_ir_resid_u(p->ir_bp, p->ir_R2, p->ir_du, p->ir_dp, (float*)W1, L0.S, p->N, p->state, p->st);
-      launch_dst_forward<T>(W1, L0.S, p->dim, p->n, L0.logP, dp, done, p->st);
-    }
+    launch_ir_resid_u(p->ir_bp, p->ir_R2, p->ir_du, p->ir_dp, (float*)W1, L0.S, p->N, p->state, p->st);
+    launch_dst_forward<T>(W1, L0.S, p->dim, p->n, L0.logP, dp, done, p->st);
     T* yhat = block_solve<T>(p, done);
     launch_dst_inverse<T>(yhat, p->ir_du, 2, p->omega, L0.S, p->dim, p->n, L0.logP, dp, done, p->st);
     return;
@@ -456,17 +444,6 @@ void enqueue_iteration(pt_problem* p) {
                             (const double*)p->jinvA[0], steps_d(p), p->st);
     launch_finalize_residual(p->partials, p->state, p->hist, p->st);
     apply_precond_A<T>(p, W1, p->p, 1, 1, done);
-    if (std::is_same<T, double>::value && dst_fuses_ru(dp)) {
-      // r_u = bres - K^T (p + u) formed by the transform's loads
-      FusedRu<T> fr;
-      fr.b = (const T*)(const void*)p->bres;
-      fr.wa = (const T*)(const void*)p->p;
-      fr.wb = (const T*)(const void*)p->u;
-      launch_dst_forward<T>(W1, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st, &fr);
-      T* yhat = block_solve<T>(p, done);
-      launch_dst_inverse<T>(yhat, p->u, 1, p->omega, p->lev[0].S, p->dim, p->n, p->lev[0].logP, dp, done, p->st);
-      return;
-    }
     launch_resid_u_from_bres<T>(p->bres, p->u, p->p, W1, L0.S, p->N, p->dim, p->n, done, p->st);
   } else if (p->mixed) {
     // outer residual in FP64 first (and the convergence test), then the p-update and r_u

@@ -272,26 +272,9 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
 constexpr int kStockMaxN = 2048;
 constexpr int kStockThreads = 256;  // (FP32: 4 CTAs per SM, FP64: 2 -- the register budget)
 
-// the input pair of columns (c, c+1) at slot t: x itself, or r_u = b - w_t + w_{t+1}
-template <typename T, typename T2>
-__device__ __forceinline__ T2 load_input(const T* x, long long S, int N, long long t, long long c,
-                                         const FusedRu<T>& fr, bool alt) {
-  if (fr.wa == nullptr) return *(const T2*)(x + t * S + c);
-  const long long i = t * S + c;
-  const T2 bb = *(const T2*)((alt ? fr.b_alt : fr.b) + i);
-  const T2 a0 = *(const T2*)(fr.wa + i), w0 = *(const T2*)(fr.wb + i);
-  T2 v = mk<T2>(bb.x - (a0.x + w0.x), bb.y - (a0.y + w0.y));
-  if (t + 1 < N) {
-    const T2 a1 = *(const T2*)(fr.wa + i + S), w1 = *(const T2*)(fr.wb + i + S);
-    v.x += a1.x + w1.x;
-    v.y += a1.y + w1.y;
-  }
-  return v;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_forward_s(T* x, long long S, ColGeom cg, DstPlan<T> plan,
-                                                                 int F, const int* done, FusedRu<T> fr) {
+                                                                 int F, const int* done) {
   using T2 = typename Vec2<T>::type;
   if (stop_requested(done)) return;
   const int N = plan.N, logN = plan.logN;
@@ -301,7 +284,6 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* sm = (T2*)smem_raw;
   const long long c0 = (long long)blockIdx.x * 2 * F;
-  const bool alt = fr.use_alt != nullptr && *((volatile const int*)fr.use_alt) != 0;
   // load: slot m = N-1-t holds (w_a, w_b); the m = 0 entry is doubled.  Four loads in flight
   // per thread (the loads are latency-bound at this occupancy).
   for (int idx0 = threadIdx.x; idx0 < N * F; idx0 += 4 * blockDim.x) {
@@ -309,7 +291,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = idx0 + q * blockDim.x;
-      if (idx < N * F) v[q] = load_input<T, T2>(x, S, N, idx / F, c0 + 2 * (idx % F), fr, alt);
+      if (idx < N * F) v[q] = *(const T2*)(x + (long long)(idx / F) * S + c0 + 2 * (idx % F));
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -529,13 +511,8 @@ int plan_stride(const DstPlan<T>& plan) {
 }
 
 template <typename T>
-bool dst_fuses_ru(const DstPlan<T>& plan) {
-  return stockham_ok(plan);
-}
-
-template <typename T>
 void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> plan, const int* done,
-                        cudaStream_t st, const FusedRu<T>* ru) {
+                        cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
   const int L = plan_stride(plan);
   const int C = plan.C > 0 ? plan.C : dst_cols<T>(L, S);
@@ -544,15 +521,13 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
   const ColGeom cg{dim, n, logP};
   double interior = plan.N;
   for (int d = 0; d < dim; ++d) interior *= n;
-  // (fused: b, wa and wb read once each, the transform written once)
-  LaunchScope ls(ru ? "dst_forward_ru" : "dst_forward", st, (ru ? 4.0 : 2.0) * sizeof(T) * interior);
+  LaunchScope ls("dst_forward", st, 2.0 * sizeof(T) * interior);
   if (stockham_ok(plan)) {
     set_smem_limit((const void*)k_dst_forward_s<T>, 200 * 1024);
     const int F = stockham_cols(plan, S);
     const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
     const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2);
-    k_dst_forward_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(x, S, cg, plan, F, done,
-                                                                       ru ? *ru : FusedRu<T>());
+    k_dst_forward_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(x, S, cg, plan, F, done);
   } else if (plan.M > 0) {
     set_smem_limit((const void*)k_dst_forward<T, true>, 200 * 1024);
     k_dst_forward<T, true><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
@@ -606,12 +581,8 @@ void launch_dst_forward_plain(double* x, long long S, int ncols, DstPlan<double>
   k_dst_forward<double, false><<<(int)(S / (2 * C)), kThreads, smem, st>>>(x, S, cg, plan, C, nullptr);
 }
 
-template void launch_dst_forward<float>(float*, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t,
-                                        const FusedRu<float>*);
-template void launch_dst_forward<double>(double*, long long, int, int, int, DstPlan<double>, const int*, cudaStream_t,
-                                         const FusedRu<double>*);
-template bool dst_fuses_ru<float>(const DstPlan<float>&);
-template bool dst_fuses_ru<double>(const DstPlan<double>&);
+template void launch_dst_forward<float>(float*, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);
+template void launch_dst_forward<double>(double*, long long, int, int, int, DstPlan<double>, const int*, cudaStream_t);
 template void launch_dst_inverse<float>(const float*, void*, int, double, long long, int, int, int, DstPlan<float>, const int*, cudaStream_t);
 template void launch_dst_inverse<double>(const double*, void*, int, double, long long, int, int, int, DstPlan<double>, const int*, cudaStream_t);
 

@@ -268,35 +268,27 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
     const bool xin = x < n;
     const float fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
     const float gxc = ct * nx[x];
-    // slice base pointers; offsets within a slice (< P^2) are 32-bit
-    const long long sb = (long long)t * S;
-    const float* __restrict__ dus = du + sb;
-    const float* __restrict__ dps = dp + sb;
-    const float* __restrict__ R1s = R1 + sb;
-    const float* __restrict__ R2s = R2 + sb;
-    float* __restrict__ bps = bp + sb;
-    float* __restrict__ rps = rp + sb;
-    const float* __restrict__ dprev = t > 0 ? du + sb - S : nullptr;
-    auto at = [&](int y) { return y * P + x; };
-    float d_m = dus[at(y0) - P], d_c = dus[at(y0)];
-    float q_m = dps[at(y0) - P], q_c = dps[at(y0)];
+    const long long base = (long long)t * S + x;
+    auto at = [&](int y) { return base + (long long)y * P; };
+    float d_m = du[at(y0) - P], d_c = du[at(y0)];
+    float q_m = dp[at(y0) - P], q_c = dp[at(y0)];
     float ayl = fmaf(gxc, fy[y0], a0s);
     // operands of the next row are loaded one iteration ahead (latency)
     auto ld_row = [&](int y, float& dv, float& qv) {
       dv = 0.f;
       qv = 0.f;
       if (y < P) {
-        dv = dus[at(y)];
-        qv = dps[at(y)];
+        dv = du[at(y)];
+        qv = dp[at(y)];
       }
     };
     auto ld_ctr = [&](int y, float& r1, float& r2, float& dt) {
       r1 = r2 = dt = 0.f;
       if (xin && y < n) {
-        const int i = at(y);
-        r1 = R1s[i];
-        r2 = R2s[i];
-        dt = dprev ? dprev[i] : 0.f;
+        const long long i = at(y);
+        r1 = R1[i];
+        r2 = R2[i];
+        dt = t > 0 ? du[i - S] : 0.f;
       }
     };
     float dpn, qpn, r1c, r2c, dtc;
@@ -312,18 +304,20 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
       float dW = __shfl_up_sync(0xffffffffu, d_c, 1), dE = __shfl_down_sync(0xffffffffu, d_c, 1);
       float qW = __shfl_up_sync(0xffffffffu, q_c, 1), qE = __shfl_down_sync(0xffffffffu, q_c, 1);
       if (lane == 0 && yin) {
-        dW = dus[at(y) - 1];
-        qW = dps[at(y) - 1];
+        dW = du[at(y) - 1];
+        qW = dp[at(y) - 1];
       }
       if (lane == 31 && yin && x + 1 < P) {
-        dE = dus[at(y) + 1];
-        qE = dps[at(y) + 1];
+        dE = du[at(y) + 1];
+        qE = dp[at(y) + 1];
       }
       const float ayu = fmaf(gxc, fy[y + 1 < P ? y + 1 : y], a0s);
       float b = 0.f, r = 0.f;
       if (xin && yin) {
+        const long long i = at(y);
         const float gy = ct * ny[y];
         const float axl = fmaf(gy, fxl, a0s), axr = fmaf(gy, fxr, a0s);
+        (void)i;
         const float Kd = d_c - dtm;
         const float sd = axl * (d_c - dW) + axr * (d_c - dE) + ayl * (d_c - d_m) + ayu * (d_c - d_p);
         const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - q_m) + ayu * (q_c - q_p);
@@ -332,8 +326,8 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
         acc = fmaf(b, b, acc);
       }
       if (y < P) {
-        bps[at(y)] = b;
-        rps[at(y)] = r;
+        bp[at(y)] = b;
+        rp[at(y)] = r;
       }
       d_m = d_c;
       d_c = d_p;

@@ -299,29 +299,11 @@ struct DstPlan {
   const T* twS = nullptr;    // [N] e^{-2 pi i e / N} (power-of-two N: radix-8 Stockham kernels)
 };
 
-// The second Uzawa residual of eq. 3.1 in the form r_u = b - K^T w, w = wa + wb (b = F - B u and
-// w = p + u in FP64; b' or R2 and w = dp + du in the FP32 refinement iterations), read by the
-// forward transform instead of a stored r_u: (K^T w)_t = w_t - w_{t+1}, w_{N+1} := 0.  b_alt
-// replaces b while *use_alt != 0 (the FP64 step of the refinement).
-template <typename T>
-struct FusedRu {
-  const T* b = nullptr;
-  const T* b_alt = nullptr;
-  const int* use_alt = nullptr;
-  const T* wa = nullptr;
-  const T* wb = nullptr;
-};
-
 // in-place forward transform: x_k <- sum_n x_n sin((2k-1) n pi/(2N)) for every interior column
-// (ghost columns of the grid with n interior points per axis are written as zero).  With `ru`
-// (power-of-two N <= 2048 only, see dst_fuses_ru) the input x_n is r_u of FusedRu, formed while
-// loading, and x is only written.
+// (ghost columns of the grid with n interior points per axis are written as zero)
 template <typename T>
 void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> plan, const int* done,
-                        cudaStream_t st, const FusedRu<T>* ru = nullptr);
-// whether launch_dst_forward takes a FusedRu for this plan
-template <typename T>
-bool dst_fuses_ru(const DstPlan<T>& plan);
+                        cudaStream_t st);
 
 // inverse + update: u_n += omega * sum_k y_k sin((2k-1) n pi/(2N)); u in FP64 (mode 1), u of
 // type T (mode 2), or out = transform (mode 0, out of type T)
