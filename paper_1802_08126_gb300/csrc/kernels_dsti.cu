@@ -156,8 +156,18 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_rows(T* __restrict__ x,
 // Columns along a strided axis (1: y, stride M; 2: z, stride M^2), in place.  A block takes 2C
 // consecutive columns (x .. x + 2C - 1) of one plane of one slice; warp w transforms columns
 // 2w, 2w+1.  With `scale`, the column pair gets S diag(g) S, g the exact block-solve factor.
+// Per-warp buffer stride (complex elements) of the column kernel: two transforms of length W and
+// a pad.  FP32: the pad makes the stride 4 banks mod 32, so that the tile copies (a warp moves
+// two positions of 16 consecutive columns) hit 32 distinct banks; FP64: one element.
+template <typename T>
+__host__ __device__ __forceinline__ int cols_stride(int W) {
+  if (sizeof(T) == 8) return 2 * W + 1;
+  const int q = ((2 - 2 * W) % 16 + 16) % 16;
+  return 2 * W + (q == 0 ? 16 : q);
+}
+
 template <typename T, int LOGMC>
-__global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x, int logM_rt, int dim, int axis,
+__global__ void __launch_bounds__(kWarpsMax * 32, (sizeof(T) == 4 && LOGMC > 0 && LOGMC <= 8) ? 4 : 1) k_dsti_cols(T* __restrict__ x, int logM_rt, int dim, int axis,
                                                               long long S, int scale, DstiTabs<T> tb) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -175,7 +185,8 @@ __global__ void __launch_bounds__(kWarpsMax * 32) k_dsti_cols(T* __restrict__ x,
   // column base: y axis -> o = z, z axis -> o = y
   const long long base = (long long)slice * S + (axis == 1 ? (long long)o * M * M : (long long)o * M) + x0;
   T2* bufs = (T2*)smem_raw;
-  auto bufA = [&](int w) { return bufs + (size_t)w * (2 * W + 1); };
+  const int BS = cols_stride<T>(W);
+  auto bufA = [&](int w) { return bufs + (size_t)w * BS; };
   // load the tile (columns fastest, coalesced); position M-1 is never read by the transform
   for (int idx = threadIdx.x; idx < 2 * C * (M - 1); idx += blockDim.x) {
     const int pos = idx / (2 * C), c = idx - pos * 2 * C;
@@ -302,7 +313,8 @@ void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int ax
   const int M = n + 1;
   int C = warps_for<T>(M);
   while (2 * C > M && C > 1) C >>= 1;
-  const size_t smem = (size_t)C * (2 * padded_len(M) + 1) * sizeof(T2);
+  while (C > 1 && (size_t)C * cols_stride<T>(padded_len(M)) * sizeof(T2) > 200 * 1024) C >>= 1;
+  const size_t smem = (size_t)C * cols_stride<T>(padded_len(M)) * sizeof(T2);
   const long long planes = dim == 3 ? M : 1;
   const dim3 grid((unsigned)((M / (2 * C)) * planes), (unsigned)B);
   double d = B;
