@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
   const int N = plan.N, logN = plan.logN;
   const int nthr = N >= 8 ? N >> 3 : 1;
   const int Lp = padded_len(N);
+  const int logF = __ffs(F) - 1;  // F is a power of two: shifts instead of divisions
   const T2* __restrict__ pre = (const T2*)plan.pre;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* sm = (T2*)smem_raw;
@@ -291,13 +292,13 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = idx0 + q * blockDim.x;
-      if (idx < N * F) v[q] = *(const T2*)(x + (long long)(idx / F) * S + c0 + 2 * (idx % F));
+      if (idx < N * F) v[q] = *(const T2*)(x + (long long)(idx >> logF) * S + c0 + 2 * (idx & (F - 1)));
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = idx0 + q * blockDim.x;
       if (idx < N * F) {
-        const int f = idx % F, m = N - 1 - idx / F;
+        const int f = idx & (F - 1), m = N - 1 - (idx >> logF);
         if (m == 0) {
           v[q].x *= (T)2;
           v[q].y *= (T)2;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
   // stored conjugated
   const int halfp = (N >> 1) + 1;
   for (int idx = threadIdx.x; idx < F * halfp; idx += blockDim.x) {
-    const int f = idx % F, m = idx / F;
+    const int f = idx & (F - 1), m = idx >> logF;
     T2* col = sm + (size_t)f * Lp;
     if (m == 0) {
       col[0].y = -col[0].y;
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_f
   }
   // output: rhat_{j+1} = (-1)^j C3_j / 2, C3_{2i} = v_i, C3_{2i+1} = v_{N-1-i}; v = conj(spectrum)
   for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
-    const int f = idx % F, j = idx / F;
+    const int f = idx & (F - 1), j = idx >> logF;
     const int vi = (j & 1) ? (N - 1 - (j >> 1)) : (j >> 1);
     const T2 r = sm[(size_t)f * Lp + pd(vi)];
     const T sc = (j & 1) ? (T)-0.5 : (T)0.5;
@@ -353,6 +354,10 @@ __device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gmem_src)
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -367,6 +372,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
   const int N = plan.N, logN = plan.logN;
   const int nthr = N >= 8 ? N >> 3 : 1;
   const int Lp = padded_len(N);
+  const int logF = __ffs(F) - 1;  // F is a power of two: shifts instead of divisions
   const T2* __restrict__ pre = (const T2*)plan.pre;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* sm = (T2*)smem_raw;
@@ -374,9 +380,16 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
   // mode 2 (FP32 accumulate): prefetch the target tile [N][F] behind the transform tile
   T2* tgt = sm + (size_t)F * Lp;
   if (mode == 2 && sizeof(T2) == 8) {
-    for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
-      const int f = idx % F, t = idx / F;
-      cp_async_8(tgt + idx, (const T*)out + (long long)t * S + c0 + 2 * f);
+    if (F >= 2) {  // two neighbouring column pairs per 16-byte copy (addresses 16-byte aligned: F even)
+      for (int idx = 2 * threadIdx.x; idx < N * F; idx += 2 * blockDim.x) {
+        const int f = idx & (F - 1), t = idx >> logF;
+        cp_async_16(tgt + idx, (const T*)out + (long long)t * S + c0 + 2 * f);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < N * F; idx += blockDim.x) {
+        const int f = idx & (F - 1), t = idx >> logF;
+        cp_async_8(tgt + idx, (const T*)out + (long long)t * S + c0 + 2 * f);
+      }
     }
   }
   // load: z_j = (-1)^j y_{j+1};  v_{j/2} = z_j (j even), v_{N-1-(j-1)/2} = z_j (j odd)
@@ -385,13 +398,13 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = idx0 + q * blockDim.x;
-      if (idx < N * F) v[q] = *(const T2*)(y + (long long)(idx / F) * S + c0 + 2 * (idx % F));
+      if (idx < N * F) v[q] = *(const T2*)(y + (long long)(idx >> logF) * S + c0 + 2 * (idx & (F - 1)));
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = idx0 + q * blockDim.x;
       if (idx < N * F) {
-        const int f = idx % F, j = idx / F;
+        const int f = idx & (F - 1), j = idx >> logF;
         int s;
         if (j & 1) {
           s = N - 1 - (j >> 1);
@@ -418,7 +431,7 @@ __global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_i
   //       X[m] = Re(e^{-i pi m/(2N)} V[m]);  u_{N-m} = X[m]  (time slot N-1-m)
   const int halfp = (N >> 1) + 1;
   for (int idx = threadIdx.x; idx < F * halfp; idx += blockDim.x) {
-    const int f = idx % F, m = idx / F;
+    const int f = idx & (F - 1), m = idx >> logF;
     const bool ga = ghost_col(cg, c0 + 2 * f), gb = ghost_col(cg, c0 + 2 * f + 1);
     const int q = m == 0 ? 0 : N - m;
     const T2* col = sm + (size_t)f * Lp;
