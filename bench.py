@@ -65,8 +65,8 @@ def parse():
                          "to the continuous-batching server (finished solves replaced at once)")
     ap.add_argument("--requests", type=int, default=1000, help="serve: requests per arrival rate")
     ap.add_argument("--rates", default="0.25,0.5,0.75,0.9,1.1", help="serve: arrival rates as fractions of capacity")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="batch / serve: launch configurations left at their defaults (no tuning)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch / serve: tune the launch configurations (pt_options.autotune = 1)")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
     ap.add_argument("--no-3d", action="store_true", help="leave out the 3-D entry")
     ap.add_argument("--batch-sample", type=int, default=64,
@@ -479,7 +479,7 @@ def run_batch(args, rank, ws, dist):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             tickets = [sv.submit(p.dim, p.n, p.N, p.T, p.coeff, None, seed=p.seed, tol=args.tol,
-                                 max_it=args.max_it, precision="mixed", autotune=-1 if args.no_autotune else 0)
+                                 max_it=args.max_it, precision="mixed", autotune=1 if args.autotune else 0)
                        for p in probs]
             for t in tickets:
                 stt, it = sv.wait(t)
@@ -496,7 +496,7 @@ def run_batch(args, rank, ws, dist):
             est = ptu.estimate_bytes(probs[i].dim, probs[i].n, probs[i].N, "mixed")
             if Ps and used + est > budget:
                 break
-            Ps.append(make_batch_problem(ptu, probs[i], autotune=-1 if args.no_autotune else 0))
+            Ps.append(make_batch_problem(ptu, probs[i], autotune=1 if args.autotune else 0))
             used += est
             i += 1
         torch.cuda.synchronize()
@@ -522,7 +522,7 @@ def run_batch(args, rank, ws, dist):
                        "dofs_per_gpu": total_dofs, "tol": args.tol, "waves": waves, "mode": args.batch_mode,
                        "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
                        "converged": int(sum(1 for x in statuses if x == 0)), "precision": "mixed",
-                       "autotune": not args.no_autotune, "loop": "device (conditional graph node)",
+                       "autotune": bool(args.autotune), "loop": "device (conditional graph node)",
                        "l2": "inputs larger than L2 for most problems"},
             "gpu_launches": int(launches), "clocks": clk,
         }
@@ -573,7 +573,7 @@ def run_serve(args, rank, ws, dist):
                     time.sleep(delay)
                 tickets.append(sv.submit(p.dim, p.n, p.N, p.T, p.coeff, None, seed=p.seed, tol=args.tol,
                                          max_it=args.max_it, precision="mixed",
-                                         autotune=-1 if args.no_autotune else 0))
+                                         autotune=1 if args.autotune else 0))
             ok = 0
             for t in tickets:
                 st, it = sv.wait(t)
@@ -589,7 +589,7 @@ def run_serve(args, rank, ws, dist):
         "n_gpus": 1, "steps": len(results), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": "serve_heat2d_mixed", "requests_per_rate": args.requests, "tol": args.tol,
-                   "autotune": not args.no_autotune,
+                   "autotune": bool(args.autotune),
                    "capacity_dofs_per_s": capacity, "mean_request_dofs": mean_dofs},
         "rates": results,
     }

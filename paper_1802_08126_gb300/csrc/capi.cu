@@ -1519,7 +1519,7 @@ namespace pt {
 pt_status problem_begin(pt_problem* p, double tol, int max_it) {
   pt_status st = ensure_hist(p, max_it);
   if (st != PT_OK) return st;
-  if (p->opt.autotune >= 0 && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+  if (p->opt.autotune > 0 && !p->tuned && (st = autotune(p)) != PT_OK) return st;
   if ((st = enqueue_reset(p, tol, max_it)) != PT_OK) return st;
   if ((st = ensure_graph(p, graph_iterations(p))) != PT_OK) return st;
   PT_CUDA(cudaStreamSynchronize(p->st));
@@ -1687,7 +1687,7 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
   for (int i = 0; i < count; ++i) {
     pt_problem* p = ps[i];
     if ((st = ensure_hist(p, max_it[i])) != PT_OK) return st;
-    if (p->opt.autotune >= 0 && !p->tuned && (st = autotune(p)) != PT_OK) return st;
+    if (p->opt.autotune > 0 && !p->tuned && (st = autotune(p)) != PT_OK) return st;
     if ((st = enqueue_reset(p, tol[i], max_it[i])) != PT_OK) return st;
     max_rounds = std::max(max_rounds, max_it[i] + 1);
   }

@@ -36,9 +36,7 @@ def test_batch_of_uneven_problems_equals_solo_solves():
     precs = ["mixed", "fp64"] * (len(probs) // 2)
     solo = []
     for p, pr in zip(probs, precs):
-        # (the batch tunes its launch configurations by default; the solo solves take the same
-        # cached choices, so the two must agree bit for bit)
-        with make(p, pr, autotune=True) as P:
+        with make(p, pr) as P:
             st, it, _ = P.solve(1e-10, 600)
             solo.append((st, it, state_u(P, p)))
     Ps = [make(p, pr) for p, pr in zip(probs, precs)]
@@ -54,15 +52,16 @@ def test_batch_of_uneven_problems_equals_solo_solves():
 
 
 def test_batch_device_loop_matches_plain_launches_and_autotune_off():
-    """The batch's device-side loop (one graph launch per quarter of the active set finishing)
-    gives the same iterates as the same batch without tuning solved by plain per-round launches
-    of the same kernels, up to the rounding of the launch configuration."""
+    """The batch's device-side loop (one graph launch per quarter of the active set finishing),
+    here with tuned launch configurations, gives the same iterates as the same batch untuned and
+    solved by plain per-round launches of the same kernels, up to the rounding of the launch
+    configuration."""
     import paper_1802_08126_gb300 as ptu
     probs = [S.batch_problem(i) for i in range(6, 12)]
     probs = [S.Problem(p.name, p.dim, [min(p.n[0], 63)] * 2, min(p.N, 300), p.T, p.coeff, p.f_kind, p.seed)
              for p in probs]
     out = []
-    for kw, plain in ((dict(), False), (dict(autotune=False), True)):
+    for kw, plain in ((dict(autotune=True), False), (dict(autotune=False), True)):
         Ps = [make(p, "mixed", **kw) for p in probs]
         ptu.profile_enable(plain)  # kernels timed one by one: the batch takes per-round host launches
         try:

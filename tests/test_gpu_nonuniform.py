@@ -180,8 +180,7 @@ def test_server_copies_the_steps():
     import paper_1802_08126_gb300 as ptu
     prob = steps(S.heat2d_uniform(31, 16), seed=5)
     f = S.source(prob)
-    # (the server tunes its launch configurations; the solo solve takes the same cached choice)
-    with problem(prob, autotune=True) as P:
+    with problem(prob) as P:
         u_solo = np.zeros((prob.N, prob.ns))
         P.solve(1e-10, 1000, u_out=u_solo)
     sv = ptu.Server()

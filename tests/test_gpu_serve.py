@@ -17,11 +17,9 @@ def _built():
 
 
 def solo(prob, precision="mixed", tol=1e-9):
-    """The stand-alone solve, with the same tuned launch configuration the server picks (the
-    autotuner's choice is cached per problem class, and the server tunes by default)."""
     import paper_1802_08126_gb300 as ptu
     with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, None, S.initial(prob),
-                     precision=precision, autotune=True) as P:
+                     precision=precision) as P:
         P.set_rhs_uniform(prob.seed, S.initial(prob)) if prob.f_kind == "uniform" else P.set_rhs(S.source(prob), S.initial(prob))
         st, it, _ = P.solve(tol, 2000)
         u = np.zeros((prob.N, prob.ns))
