@@ -603,14 +603,16 @@ __global__ void __launch_bounds__(256) k_mg2s_up_f32(const float* __restrict__ b
     const float* er = es + Yc * Pc;
     return fmaf(lc.w0, er[lc.c0], lc.w1 * er[lc.c1]);
   };
-  float ex_lo = 0.f;  // crow of the coarse row below the next even row
-  int k_lo = -1000;
   auto ld_b = [&](int y) -> float { return (xin && y >= 0 && y < nf) ? bs[y * Pf + x] : 0.f; };
   const bool wlane = lane >= 1 && lane <= 30 && x < Pf;
   auto ld_o = [&](int y) -> float { return (MODE == 1 && wlane && xin && y < nf) ? os[y * Pf + x] : 0.f; };
   float fy_carry = (y0 - 1 >= 0 && y0 - 1 <= nf) ? fy[y0 - 1] : 0.f;  // y-face table below the first row
-  // one fine row: faces, Jacobi factor, and x2 = w D^-1 b + P e
-  auto row = [&](int y, float bv_in, float& bv, float& x2, float& jf, float& xl, float& xr, float& yl,
+  // Rows go in pairs (y0 is even): fine row 2k+1 sits on coarse row k, fine row 2k+2 between k and
+  // k+1, so the interpolation in y needs one new coarse row every two fine rows.  cprev = the
+  // x-interpolated coarse row below the next odd fine row.
+  float cprev = crow((y0 >> 1) - 1);
+  // one fine row: faces, Jacobi factor, and x2 = w D^-1 b + P e (pe: the interpolated correction)
+  auto row = [&](int y, float bv_in, float pe, float& bv, float& x2, float& jf, float& xl, float& xr, float& yl,
                  float& yu) {
     const bool yin = y >= 0 && y < nf;
     const float gy = yin ? cths * ny[y] : 0.f;
@@ -620,39 +622,27 @@ __global__ void __launch_bounds__(256) k_mg2s_up_f32(const float* __restrict__ b
     yl = fmaf(lc.gxn, fy_carry, a0s);
     yu = fmaf(lc.gxn, fyu, a0s);
     fy_carry = fyu;
-    float pe;
-    if (y & 1) {
-      const int k = (y - 1) >> 1;
-      ex_lo = (k_lo == k) ? ex_lo : crow(k);
-      k_lo = k;
-      pe = ex_lo;
-    } else {
-      const int k = y >> 1;
-      const float lo = (k_lo == k - 1) ? ex_lo : crow(k - 1);
-      const float hi = crow(k);
-      pe = 0.5f * (lo + hi);
-      ex_lo = hi;
-      k_lo = k;
-    }
     const bool in = xin && yin;
     bv = in ? bv_in : 0.f;
     jf = __fdividef(omega, sig + ((xl + xr) + (yl + yu)));
     x2 = in ? fmaf(bv, jf, pe) : 0.f;
   };
+  auto pe_odd = [&]() { return cprev; };
+  auto pe_even = [&](int y) {
+    const float cnext = crow(y >> 1);
+    const float pe = 0.5f * (cprev + cnext);
+    cprev = cnext;
+    return pe;
+  };
   float bm, xm, jm, xlm, xrm, ylm, yum;
   float bc, xc, jc, xlc, xrc, ylc, yuc;
   float bn, xn, jn, xln, xrn, yln, yun;
-  row(y0 - 1, ld_b(y0 - 1), bm, xm, jm, xlm, xrm, ylm, yum);
-  row(y0, ld_b(y0), bc, xc, jc, xlc, xrc, ylc, yuc);
+  row(y0 - 1, ld_b(y0 - 1), pe_odd(), bm, xm, jm, xlm, xrm, ylm, yum);
+  row(y0, ld_b(y0), pe_even(y0), bc, xc, jc, xlc, xrc, ylc, yuc);
   float b_next = ld_b(y0 + 1);
   float o_next = ld_o(y0);
-  const int yend = min(y0 + kStripUpRows, Pf);
-  for (int y = y0; y < yend; ++y) {
-    const float b_after = ld_b(y + 2);
-    const float o_cur = o_next;
-    o_next = ld_o(y + 1);
-    row(y + 1, b_next, bn, xn, jn, xln, xrn, yln, yun);
-    b_next = b_after;
+  // output of row y from the rows y-1 (m), y (c), y+1 (n); then the window moves down one row
+  auto emit = [&](int y, float o_cur) {
     const float xW = __shfl_up_sync(0xffffffffu, xc, 1);
     const float xE = __shfl_down_sync(0xffffffffu, xc, 1);
     if (wlane) {
@@ -673,6 +663,25 @@ __global__ void __launch_bounds__(256) k_mg2s_up_f32(const float* __restrict__ b
     xrc = xrn;
     ylc = yln;
     yuc = yun;
+  };
+  const int yend = min(y0 + kStripUpRows, Pf);
+  for (int y = y0; y < yend; y += 2) {
+    {  // row y (even): its lower neighbour row y+1 is odd
+      const float b_after = ld_b(y + 2);
+      const float o_cur = o_next;
+      o_next = ld_o(y + 1);
+      row(y + 1, b_next, pe_odd(), bn, xn, jn, xln, xrn, yln, yun);
+      b_next = b_after;
+      emit(y, o_cur);
+    }
+    if (y + 1 < yend) {  // row y+1 (odd): its lower neighbour row y+2 is even
+      const float b_after = ld_b(y + 3);
+      const float o_cur = o_next;
+      o_next = ld_o(y + 2);
+      row(y + 2, b_next, pe_even(y + 2), bn, xn, jn, xln, xrn, yln, yun);
+      b_next = b_after;
+      emit(y + 1, o_cur);
+    }
   }
   (void)bm;
   (void)jm;
