@@ -65,11 +65,11 @@ __global__ void k_residual(const T* __restrict__ b, const T* __restrict__ x, T* 
   }
 }
 
-// out (mode) x + w D^-1 r
+// Post-smoothing in one pass: out (mode) x + w D^-1 (b - L x), the residual never stored.  out
+// must not alias x.
 template <int DIM, typename T>
-__global__ void k_jacobi_update(const T* x, const T* __restrict__ r, void* out, int mode,
-                                int out_fp64, StencilGeom<T> g, OpBatch<T> op, long long total,
-                                const int* done) {
+__global__ void k_post_smooth(const T* __restrict__ b, const T* __restrict__ x, void* out, int mode,
+                              int out_fp64, StencilGeom<T> g, OpBatch<T> op, long long total, const int* done) {
   if (stop_requested(done)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -78,7 +78,10 @@ __global__ void k_jacobi_update(const T* x, const T* __restrict__ r, void* out, 
     if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) {
       T am[3], ap[3];
       const T D = diag_at<DIM, T>(g, op.sig[t], op.s, op.cth[t], xx, y, z, am, ap, op.mass);
-      store_out<T>(out, i, mode, out_fp64, x[i] + op.omega * r[i] / D);
+      const T xc = x[i];
+      const T Lx = op.sig[t] * mass_apply<DIM, T>(op.mass, x, i, xc, g.P) +
+                   op.s * g.h2inv * stencil_sum<DIM, T>(x, i, xc, am, ap, g.P);
+      store_out<T>(out, i, mode, out_fp64, xc + op.omega * (b[i] - Lx) / D);
     } else if (mode == 0) {
       store_out<T>(out, i, 0, out_fp64, (T)0);
     }
@@ -546,7 +549,8 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     bl = (const T*)plan.buf[l + 1].b;
   }
   coarse_launch<DIM, T>(plan, op, bl, out, mode, out_fp64, done, st);
-  // upward sweep over the global levels
+  // upward sweep over the global levels: x = x1 + P e, then the post-smoothing in one pass into
+  // the level's r buffer (levels > 0; it is the next finer level's coarse correction) or `out`
   for (int l = plan.lc - 1; l >= 0; --l) {
     const StencilGeom<T> g = geom(l);
     const long long total = g.S * B;
@@ -554,24 +558,20 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     T* x = (T*)plan.buf[l].x;
     T* r = (T*)plan.buf[l].r;
     const Level& C = plan.lev[l + 1];
+    const T* ec = (const T*)(l + 1 == plan.lc ? plan.buf[l + 1].x : plan.buf[l + 1].r);
     const double df = level_dofs<DIM>(g.n, B), dc = level_dofs<DIM>(C.n, B), s = sizeof(T);
     {
       LaunchScope ls("mg_prolong_add", st, s * (2 * df + dc));
-      k_prolong_add<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, (const T*)plan.buf[l + 1].x, g,
-                                                                  C.logP, C.S, total, done);
-    }
-    {
-      LaunchScope ls("mg_residual", st, 3 * s * df);
-      k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, g, op, total, done);
+      k_prolong_add<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, ec, g, C.logP, C.S, total, done);
     }
     if (l == 0) {
       const double ob = out_fp64 ? (mode == 1 ? 16.0 : 8.0) : (mode == 1 ? 2 * s : s);
-      LaunchScope ls("mg_jacobi_update", st, (2 * s + ob) * df);
-      k_jacobi_update<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, r, out, mode, out_fp64, g, op,
-                                                                    total, done);
+      LaunchScope ls("mg_post_smooth", st, (2 * s + ob) * df);
+      k_post_smooth<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, out, mode, out_fp64, g, op, total,
+                                                                  done);
     } else {
-      LaunchScope ls("mg_jacobi_update", st, 3 * s * df);
-      k_jacobi_update<DIM, T><<<grid_for(total), kThreads, 0, st>>>(x, r, x, 0, 0, g, op, total, done);
+      LaunchScope ls("mg_post_smooth", st, 3 * s * df);
+      k_post_smooth<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, 0, 0, g, op, total, done);
     }
   }
 }
