@@ -1431,6 +1431,7 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
     float** ir[5] = {&p->ir_du, &p->ir_dp, &p->ir_R1, &p->ir_R2, &p->ir_bp};
     for (float** b : ir)
       if (!(*b = alloc_padded<float>(p, L0, p->N, &st))) return st;
+    if (p->dim == 2) prepare_ir_inner_2d();
   }
   st = p->mixed ? setup_precision<float>(p) : setup_precision<double>(p);
   if (st != PT_OK) return st;

@@ -15,6 +15,7 @@
 // sigma_t = tau_t / tau in the multiply-add that subtracts the stencil from the residual, and the A~
 // input is written as rho_t r_p (rho_t = tau / tau_t), which is -rho_t bres - (tau A_t)(p + u): no
 // FP64 operation more than for uniform steps.
+#include "bulk_pipe.cuh"
 #include "stencil_common.cuh"
 
 namespace pt {
@@ -340,15 +341,203 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// Streamed form for P >= 256.  A CTA owns a segment of kSegW columns and walks strips of R rows
+// of one slot; a producer warp copies, row after row, the du and dp rows (with a 16-byte halo on
+// each side) and the R1, R2 and previous-slot du rows into a ring of kStages shared-memory stages
+// (one bulk copy per array and row), and eight consumer warps, one column per thread, take the
+// x-neighbours from the stage and the y-neighbours from registers.  Stage j of a strip holds the
+// du / dp row y0 - 1 + j and the R1 / R2 / du(t-1) row y0 - 2 + j, so the stage that completes the
+// 5-point stencil of row y also brings that row's other operands.  The arithmetic is that of
+// k_ir_inner_2d, term by term.  The grid is persistent (one wave) and every CTA takes the tasks
+// blockIdx.x, blockIdx.x + gridDim.x, ... in order, so the producer runs ahead across strips.
+constexpr int kSegW = 256;
+constexpr int kStages = 6;
+constexpr int kHaloF = 4;
+constexpr int kRowDU = kSegW + 2 * kHaloF;
+
+struct IrStage {
+  float du[kRowDU];
+  float dp[kRowDU];
+  float r1[kSegW];
+  float r2[kSegW];
+  float dt[kSegW];
+};
+static_assert(sizeof(IrStage) % 16 == 0, "bulk copies need 16-byte aligned stage buffers");
+
+__device__ __forceinline__ void report_timeout(SolveState* st) {
+  st->status = PT_ETIMEOUT;
+  __threadfence();
+  st->done = 1;
+}
+
+__global__ void __launch_bounds__(kSegW + 32, 4) k_ir_inner_2d_rows(
+    const float* __restrict__ du, const float* __restrict__ dp, const float* __restrict__ R1,
+    const float* __restrict__ R2, float* __restrict__ bp, float* __restrict__ rp, double* __restrict__ partials,
+    const float* __restrict__ tabf, const float* __restrict__ cthf, float a0s, float s_h2, int n, int logP,
+    int logR, long long S, int N, Steps<float> sp, SolveState* st) {
+  if (*((volatile const int*)&st->done) != 0 || *((volatile const int*)&st->outer) != 0) return;
+  __shared__ __align__(128) IrStage stage[kStages];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ int abort_flag;
+  const int P = 1 << logP, R = 1 << logR;
+  const int logSeg = logP - 8, logStrips = logP - logR;
+  const long long ntasks = (long long)N << (logSeg + logStrips);
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kSegW / 32);
+    }
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (blockIdx.x == 0)
+    for (int i = gridDim.x + tid; i < kReduceBlocks; i += blockDim.x) partials[i] = 0.0;
+  __syncthreads();
+  float acc = 0.f;
+  if (tid >= kSegW) {
+    // producer warp: one lane issues the copies
+    if (lane == 0) {
+      bool ok = true;
+      unsigned c = 0;
+      for (long long task = blockIdx.x; task < ntasks && ok; task += gridDim.x) {
+        const int x0 = (int)(task & ((1 << logSeg) - 1)) << 8;
+        const long long rest = task >> logSeg;
+        const int y0 = (int)(rest & ((1 << logStrips) - 1)) << logR;
+        const int t = (int)(rest >> logStrips);
+        const long long slot = (long long)t * S;
+        for (int j = 0; j < R + 2; ++j, ++c) {
+          const int s = (int)(c % kStages);
+          const unsigned r = c / kStages;
+          if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int y = y0 - 1 + j, yr = y - 1;
+          const bool cp_d = y <= P - 1, cp_r = j >= 2 && yr < n, cp_t = cp_r && t > 0;
+          const unsigned bytes = (cp_d ? 2u * kRowDU * 4u : 0u) + (cp_r ? 2u * kSegW * 4u : 0u) +
+                                 (cp_t ? (unsigned)kSegW * 4u : 0u);
+          mbar_arrive_expect_tx(&full[s], bytes);
+          IrStage& g = stage[s];
+          if (cp_d) {
+            const long long o = slot + (long long)y * P + x0 - kHaloF;
+            bulk_g2s(g.du, du + o, kRowDU * 4u, &full[s]);
+            bulk_g2s(g.dp, dp + o, kRowDU * 4u, &full[s]);
+          }
+          if (cp_r) {
+            const long long o = slot + (long long)yr * P + x0;
+            bulk_g2s(g.r1, R1 + o, kSegW * 4u, &full[s]);
+            bulk_g2s(g.r2, R2 + o, kSegW * 4u, &full[s]);
+            if (cp_t) bulk_g2s(g.dt, du + o - S, kSegW * 4u, &full[s]);
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        report_timeout(st);
+      }
+      // every stage's last fill has landed before the CTA may exit
+      for (int s = 0; s < kStages && (unsigned)s < c; ++s) {
+        const unsigned fills = (c - (unsigned)s + kStages - 1) / kStages;
+        if (!mbar_wait(&full[s], (fills - 1) & 1, nullptr)) report_timeout(st);
+      }
+    }
+    __syncwarp();  // the warp reaches the final block barrier converged
+  } else {
+    const float* nx = tabf;
+    const float* fx = tabf + P;
+    const float* ny = tabf + 2 * P;
+    const float* fy = tabf + 3 * P;
+    bool ok = true;
+    unsigned c = 0;
+    for (long long task = blockIdx.x; task < ntasks && ok; task += gridDim.x) {
+      const int x0 = (int)(task & ((1 << logSeg) - 1)) << 8;
+      const long long rest = task >> logSeg;
+      const int y0 = (int)(rest & ((1 << logStrips) - 1)) << logR;
+      const int t = (int)(rest >> logStrips);
+      const int x = x0 + tid;
+      const bool xin = x < n;
+      const float ct = s_h2 * cthf[t];
+      const float sg = sp.sig[t], rh = sp.rho[t];
+      const float fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
+      const float gxc = ct * nx[x];
+      float* bpt = bp + (long long)t * S + x;
+      float* rpt = rp + (long long)t * S + x;
+      float d_m = 0.f, d_c = 0.f, dW = 0.f, dE = 0.f, q_m = 0.f, q_c = 0.f, qW = 0.f, qE = 0.f;
+      float ayl = fmaf(gxc, fy[y0], a0s);
+      for (int j = 0; j < R + 2; ++j, ++c) {
+        const int s = (int)(c % kStages);
+        // every lane waits (the barrier's completion makes the copied bytes visible to it); the
+        // warp leaves together if any lane gave up
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (c / kStages) & 1, &abort_flag))) {
+          ok = false;
+          break;
+        }
+        const IrStage& g = stage[s];
+        const float d_pW = g.du[kHaloF - 1 + tid], d_p = g.du[kHaloF + tid], d_pE = g.du[kHaloF + 1 + tid];
+        const float q_pW = g.dp[kHaloF - 1 + tid], q_p = g.dp[kHaloF + tid], q_pE = g.dp[kHaloF + 1 + tid];
+        const float r1 = g.r1[tid], r2 = g.r2[tid];
+        const float dtm = t > 0 ? g.dt[tid] : 0.f;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (j >= 2) {
+          const int y = y0 + j - 2;
+          const bool yin = y < n;
+          const float ayu = fmaf(gxc, fy[y + 1 < P ? y + 1 : y], a0s);
+          float b = 0.f, r = 0.f;
+          if (xin && yin) {
+            const float gy = ct * ny[y];
+            const float axl = fmaf(gy, fxl, a0s), axr = fmaf(gy, fxr, a0s);
+            const float Kd = d_c - dtm;
+            const float sd = axl * (d_c - dW) + axr * (d_c - dE) + ayl * (d_c - d_m) + ayu * (d_c - d_p);
+            const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - q_m) + ayu * (q_c - q_p);
+            b = fmaf(-sg, sd, r2 - Kd);
+            r = (fmaf(-sg, sq, Kd) - r1) * rh;
+            acc = fmaf(b, b, acc);
+          }
+          bpt[y * P] = b;
+          rpt[y * P] = r;
+          ayl = ayu;
+        }
+        d_m = d_c;
+        d_c = d_p;
+        dW = d_pW;
+        dE = d_pE;
+        q_m = q_c;
+        q_c = q_p;
+        qW = q_pW;
+        qE = q_pE;
+      }
+    }
+    if (!ok) {
+      abort_flag = 1;
+      if (lane == 0) report_timeout(st);
+    }
+  }
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 }  // namespace
+
+void prepare_ir_inner_2d() { resident_grid((const void*)k_ir_inner_2d_rows, kSegW + 32, 0, kReduceBlocks); }
 
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s) {
+                        int n, int logP, long long S, int N, Steps<float> sp, SolveState* st, cudaStream_t s) {
   const int P = 1 << logP;
-  const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * N, 0.0, kInnerStep);
+  if (P >= kSegW) {
+    const int grid = resident_grid((const void*)k_ir_inner_2d_rows, kSegW + 32, 0, kReduceBlocks);
+    // strips of 64 rows, shorter while there would be fewer than four tasks per CTA
+    int logR = 6;
+    while (logR > 4 && ((long long)N << (logP - 8 + logP - logR)) < 4LL * grid) --logR;
+    k_ir_inner_2d_rows<<<grid, kSegW + 32, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf,
+                                                    (float)(s_h2 * a0), (float)s_h2, n, logP, logR, S, N, sp, st);
+    return;
+  }
+  const long long nwarps = (long long)(P / 32) * (P / kRows) * N;
   k_ir_inner_2d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
                                               (float)s_h2, n, logP, S, nwarps, sp, st);
 }

@@ -82,6 +82,26 @@ cudaError_t set_smem_limit(const void* func, int bytes) {
   return e;
 }
 
+std::map<std::pair<int, const void*>, int> g_resident;
+
+int resident_grid(const void* func, int threads, size_t smem, int cap) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cap;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto it = g_resident.find({dev, func});
+  if (it == g_resident.end()) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      per_sm = 0;
+      sms = 0;
+    }
+    it = g_resident.emplace(std::make_pair(dev, func), per_sm * sms).first;
+  }
+  const int g = it->second;
+  return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
 thread_local int g_capturing = 0;
 thread_local unsigned long long g_captured = 0;
 thread_local int g_step_kind = kAnyStep;

@@ -55,6 +55,10 @@ bool profiling_enabled();
 // the record of which pairs are done is guarded by a mutex (launches may come from several
 // host threads, e.g. the serving worker and a caller).  Returns the CUDA status of the call.
 cudaError_t set_smem_limit(const void* func, int bytes);
+// Number of CTAs of kernel `func` (threads per CTA, dynamic shared memory) resident at once on
+// the current device -- SM count x occupancy, computed once per (device, kernel) -- clamped to
+// [1, cap].  A persistent grid of this size runs in one wave.
+int resident_grid(const void* func, int threads, size_t smem, int cap);
 // Launches between capture_begin and capture_end (same thread) are recorded into a CUDA graph:
 // they are not counted as executed; capture_end returns how many were recorded.
 void capture_begin();
@@ -204,9 +208,11 @@ void launch_ir_outer_2d(const double* u, const double* p, const double* F, float
                         double* partials, const double* tab, const float* tabf, const double* cth, double a0,
                         double tau, double h, int n, int logP, long long S, int N, Steps<double> sp,
                         const SolveState* st, cudaStream_t s);
+// Occupancy query of the streamed 2-D kernel, done at problem setup (outside any stream capture).
+void prepare_ir_inner_2d();
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s);
+                        int n, int logP, long long S, int N, Steps<float> sp, SolveState* st, cudaStream_t s);
 void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
                         int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s);

@@ -137,7 +137,8 @@ def test_exact_1d_solves_follow_oracle():
 # 31^3 takes the 3-D strip kernels of the refinement, 31^2 the 2-D ones, 7^3 the generic ones
 @pytest.mark.parametrize("prob", [steps(S.heat2d_uniform(31, 32)), steps(S.heat3d_bumps(31, 8)),
                                   steps(S.heat3d_bumps(7, 16)), steps(S.heat2d_uniform(15, 8)),
-                                  const_coeff(steps(S.heat2d_uniform(63, 16)))], ids=lambda p: p.name)
+                                  const_coeff(steps(S.heat2d_uniform(63, 16))), steps(S.heat2d_uniform(255, 6))],
+                         ids=lambda p: p.name)
 def test_mixed_precision_refines_to_fp64_solution(prob):
     with problem(prob, precision="mixed") as P:
         u = np.zeros((prob.N, prob.ns))

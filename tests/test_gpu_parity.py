@@ -235,8 +235,10 @@ def test_multigrid_solve_history_and_solution(prob, hsol):
     assert rel_err(u, ref) <= FP64_TOL
 
 
-# 31^3 takes the 3-D strip kernels of the refinement (n + 1 >= 32)
-@pytest.mark.parametrize("prob", [S.heat2d_uniform(31, 32), S.heat3d_bumps(7, 16), S.heat3d_bumps(31, 8)],
+# 31^3 takes the 3-D strip kernels of the refinement (n + 1 >= 32); 255^2 and 511^2 the row-streamed
+# FP32 step (one and two 256-column segments per row)
+@pytest.mark.parametrize("prob", [S.heat2d_uniform(31, 32), S.heat3d_bumps(7, 16), S.heat3d_bumps(31, 8),
+                                  S.heat2d_uniform(255, 6), S.heat2d_uniform(511, 3)],
                          ids=lambda p: p.name)
 def test_mixed_precision_refines_to_fp64_solution(prob):
     f, u0 = S.source(prob), S.initial(prob)
