@@ -85,3 +85,58 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 
 }  // namespace pt
+
+namespace pt {
+
+// Ring of NS stages filled by one producer thread and drained by `consumers` warps.  The producer
+// and every consumer walk the same sequence of fills, counting them in `c`: fill c goes to stage
+// c % NS, and is that stage's fill number c / NS (the parity of the barrier phases).
+template <int NS>
+struct RowRing {
+  uint64_t full[NS];
+  uint64_t empty[NS];
+  int abort;
+
+  // one thread, then __syncthreads() before any use
+  __device__ __forceinline__ void init(int consumer_warps) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], (unsigned)consumer_warps);
+    }
+    abort = 0;
+    mbar_init_fence();
+  }
+  // producer: wait until fill c may overwrite its stage; false if the wait gave up
+  __device__ __forceinline__ bool acquire(unsigned c) {
+    const unsigned r = c / NS;
+    return r == 0 || mbar_wait(&empty[c % NS], (r - 1) & 1, &abort);
+  }
+  // producer: the bulk copies of fill c bring `bytes` in total (issue them after this call)
+  __device__ __forceinline__ uint64_t* commit(unsigned c, unsigned bytes) {
+    uint64_t* b = &full[c % NS];
+    mbar_arrive_expect_tx(b, bytes);
+    return b;
+  }
+  // consumer warp (all lanes): wait for fill c; false for the whole warp if any lane gave up
+  __device__ __forceinline__ bool wait(unsigned c) {
+    return __all_sync(0xffffffffu, mbar_wait(&full[c % NS], (c / NS) & 1, &abort));
+  }
+  // consumer warp (all lanes, after their reads of fill c)
+  __device__ __forceinline__ void release(unsigned c) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[c % NS]);
+  }
+  // any thread: make every other wait on this ring give up
+  __device__ __forceinline__ void give_up() { *(volatile int*)&abort = 1; }
+  // producer, after its last fill (c fills issued): every copy has landed before the CTA exits
+  __device__ __forceinline__ bool drain(unsigned c) {
+    bool ok = true;
+    for (unsigned s = 0; s < (unsigned)NS && s < c; ++s) {
+      const unsigned fills = (c - s + NS - 1) / NS;
+      ok = mbar_wait(&full[s], (fills - 1) & 1, nullptr) && ok;
+    }
+    return ok;
+  }
+};
+
+}  // namespace pt

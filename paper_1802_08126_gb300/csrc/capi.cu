@@ -81,7 +81,9 @@ struct pt_problem {
   void* dsti_sn = nullptr;                      // [(n+1)/2 + 1] sin(pi j / (n+1)) / 2
   double* dsti_lam = nullptr;                   // [n+1] (4 a0/h^2) sin^2(pi k h / 2) at k-1, 0 at n
   double* dsti_mu = nullptr;                    // [N] mu_k
-  void* dsti_g = nullptr;                       // padded, type T: block-solve factor of each point
+  void* dsti_g = nullptr;                       // padded, type T: block-solve factor of each point (FP64)
+  void* dsti_lamT = nullptr;                    // FP32: lam and mu_k / tau in FP32, the factor formed per point
+  void* dsti_muT = nullptr;
   void* hy_w = nullptr;                         // 2-D: padded LU pivots (type T) of the y-tridiagonal H_k
   int nv_h = 2;                                 // V-cycles per H_k solve
   void* mg_b[kMaxLevels] = {};
@@ -231,6 +233,7 @@ MGPlan<T> mg_plan(const pt_problem* p) {
   m.tab = sizeof(T) == 8 ? (const T*)(const void*)p->tab_d : (const T*)(const void*)p->tab_f;
   m.a0 = (T)p->coeff.a0;
   m.B = p->N;
+  m.fault = &p->state->fault;
   return m;
 }
 
@@ -374,8 +377,10 @@ T* block_solve(pt_problem* p, const int* done) {
     if (p->dim == 3)
       launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_g, false,
                           p->st);
+    const DstiFactor f = {p->dsti_lamT, p->dsti_muT,
+                          (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim) / (p->tau * p->tau)};
     launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, last, p->dsti_tw, p->dsti_sn, p->dsti_g, true,
-                        p->st);
+                        p->st, p->dsti_g ? nullptr : &f);
     if (p->dim == 3)
       launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_g, false,
                           p->st);
@@ -1149,6 +1154,14 @@ pt_status setup_precision(pt_problem* p) {
       p->hy_w = w;
       launch_hsolve_trid_table<T>(w, p->dsti_lam, p->dsti_mu, p->tau, p->coeff.a0 / (L.h * L.h), p->n, L.logP,
                                   L.S, p->N, p->st);
+    } else if (sizeof(T) == 4) {
+      // FP32: the factor is formed per point in the column kernel from lam and mu_k / tau in FP32
+      std::vector<double> m(mud);
+      for (double& v : m) v /= p->tau;
+      if (!(p->dsti_lamT = alloc_bytes(p, sizeof(T) * lam.size(), &st))) return st;
+      if (!(p->dsti_muT = alloc_bytes(p, sizeof(T) * m.size(), &st))) return st;
+      if ((st = upload<T>(p, p->dsti_lamT, lam)) != PT_OK) return st;
+      if ((st = upload<T>(p, p->dsti_muT, m)) != PT_OK) return st;
     } else {
       // the point-wise block-solve factor, computed once in FP64 (c0 as in block_solve)
       const double c0 = (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim);
@@ -1485,6 +1498,19 @@ pt_status comp_dst_inverse(pt_problem* p, const double* y, double* out) {
   return unpack_from<T>(p, (const T*)p->W2, out);
 }
 
+// Operator calls outside a solve: a streamed kernel whose bounded wait ran out has set the state's
+// fault flag (no finalize kernel follows to turn it into the solve status), so it is read here,
+// after the call's work has finished, and cleared.
+pt_status take_fault(pt_problem* p, pt_status st) {
+  if (st != PT_OK) return st;
+  int fault = 0;
+  PT_CUDA(cudaMemcpyAsync(&fault, &p->state->fault, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  PT_CUDA(cudaStreamSynchronize(p->st));
+  if (fault == 0) return PT_OK;
+  PT_CUDA(cudaMemsetAsync(&p->state->fault, 0, sizeof(int), p->st));
+  return fail(PT_ETIMEOUT, "a bounded wait inside a streamed kernel ran out");
+}
+
 template <typename T>
 pt_status comp_precond_A(pt_problem* p, const double* r, double* out) {
   pt_status st;
@@ -1558,7 +1584,8 @@ size_t estimate_problem_bytes(const pt_grid* g, int N_t, const pt_options* o) {
   double per = 24.0 + 3.0 * s;              // u, p, F and three work vectors
   if (mixed) per += 20.0;                   // FP32 corrections and residuals of the refinement
   if (!mixed && d == 2) per += 8.0;         // stored outer residual
-  if (d >= 2) per += s;                     // block-solve factor table (exact H_k solves)
+  if (d >= 2 && !mixed) per += s;           // FP64 block-solve factor / pivot table (exact H_k
+                                            // solves; FP32 forms the factor per point)
   per += (d == 2 ? 2.0 : 3.0) * s * lev;    // multigrid right-hand sides, iterates (and residuals)
   if (d != 2) per += 2.0 * s;               // generic path: level-0 iterate and residual
   if (d == 2 && !mixed) per += 16.0 * (1.0 + lev);  // cached (Jacobi factor, diagonal) pairs
@@ -1965,14 +1992,14 @@ pt_status pt_precond_A(pt_problem* p, const double* r_dev, double* out_dev) {
   g_err.clear();
   if (!p || !r_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
   PT_CUDA(cudaSetDevice(p->device));
-  return p->mixed ? comp_precond_A<float>(p, r_dev, out_dev) : comp_precond_A<double>(p, r_dev, out_dev);
+  return take_fault(p, p->mixed ? comp_precond_A<float>(p, r_dev, out_dev) : comp_precond_A<double>(p, r_dev, out_dev));
 }
 
 pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev) {
   g_err.clear();
   if (!p || !r_dev || !out_dev) return fail(PT_EINVAL, "NULL argument");
   PT_CUDA(cudaSetDevice(p->device));
-  return p->mixed ? comp_precond_H<float>(p, r_dev, out_dev) : comp_precond_H<double>(p, r_dev, out_dev);
+  return take_fault(p, p->mixed ? comp_precond_H<float>(p, r_dev, out_dev) : comp_precond_H<double>(p, r_dev, out_dev));
 }
 
 }  // extern "C"

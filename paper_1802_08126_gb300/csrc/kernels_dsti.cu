@@ -112,6 +112,11 @@ struct DstiTabs {
   const typename Vec2<T>::type* tw;  // [M]   e^{-2 pi i e / M}
   const T* sn;                       // [M/2 + 1] sin(pi j / M) / 2
   const T* g;                        // padded like the data: the block-solve factor, 0 at ghosts
+  // or, with g == nullptr, the same factor formed per point as c l / (m_k + l)^2 from l = the sum
+  // of the axes' eigenvalues lam[.] (a0 L_h in the sine basis), m_k = mu_k / tau and c = c0 / tau^2
+  const T* lam;                      // [M], lam[M - 1] = 0
+  const T* m;                        // [N]
+  T c;
 };
 
 // Rows (x, contiguous): every line pair of every slice, in place.  Lines 2q and 2q+1.
@@ -202,12 +207,25 @@ __global__ void __launch_bounds__(kWarpsMax * 32, (sizeof(T) == 4 && LOGMC > 0 &
   T2* Z = fft_any<LOGMC>(B, A, logM, tb.tw, lane);
   T2* O = Z == A ? B : A;
   if (scale) {
-    // g from the precomputed table (same padded layout as the data, zero on ghosts)
-    const T* gcol = tb.g + base + 2 * warp;
-    dsti_post<LOGMC, T, T2>(Z, M, lane, [&](int pos, T2 v) {
-      const T2 g = *(const T2*)(gcol + pos * stride);
-      O[pd(pos)] = mk<T2>(v.x * g.x, v.y * g.y);
-    });
+    if (tb.g) {
+      // g from the precomputed table (same padded layout as the data, zero on ghosts)
+      const T* gcol = tb.g + base + 2 * warp;
+      dsti_post<LOGMC, T, T2>(Z, M, lane, [&](int pos, T2 v) {
+        const T2 g = *(const T2*)(gcol + pos * stride);
+        O[pd(pos)] = mk<T2>(v.x * g.x, v.y * g.y);
+      });
+    } else {
+      // g formed here (FP32): the ghost column, plane and position are zeroed at the store
+      const T lo = dim == 3 ? tb.lam[o] : (T)0;
+      const T m = tb.m[slice], c = tb.c;
+      const T la = tb.lam[xa] + lo, lb = tb.lam[xa + 1] + lo;
+      dsti_post<LOGMC, T, T2>(Z, M, lane, [&](int pos, T2 v) {
+        const T lp = tb.lam[pos];
+        const T l_a = la + lp, l_b = lb + lp;
+        const T d_a = m + l_a, d_b = m + l_b;
+        O[pd(pos)] = mk<T2>(v.x * __fdividef(c * l_a, d_a * d_a), v.y * __fdividef(c * l_b, d_b * d_b));
+      });
+    }
     __syncwarp();
     T2* P2 = O == A ? B : A;  // second transform of the scaled spectrum
     dsti_pre<LOGMC, T, T2>(P2, M, tb.sn, lane, [&](int pos) { return O[pd(pos)]; });
@@ -262,11 +280,14 @@ int warps_for(int M) {
 }
 
 template <typename T>
-DstiTabs<T> tabs(const void* tw, const void* sn, const void* g) {
+DstiTabs<T> tabs(const void* tw, const void* sn, const void* g, const DstiFactor* f = nullptr) {
   DstiTabs<T> t;
   t.tw = (const typename Vec2<T>::type*)tw;
   t.sn = (const T*)sn;
   t.g = (const T*)g;
+  t.lam = f ? (const T*)f->lam : nullptr;
+  t.m = f ? (const T*)f->m : nullptr;
+  t.c = f ? (T)f->c : (T)0;
   return t;
 }
 
@@ -308,7 +329,7 @@ void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const 
 
 template <typename T>
 void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
-                      const void* sn, const void* gtab, bool scale, cudaStream_t st) {
+                      const void* sn, const void* gtab, bool scale, cudaStream_t st, const DstiFactor* factor) {
   using T2 = typename Vec2<T>::type;
   const int M = n + 1;
   int C = warps_for<T>(M);
@@ -322,7 +343,7 @@ void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int ax
   LaunchScope ls(scale ? "dsti_cols_scale" : "dsti_cols", st, 2.0 * sizeof(T) * d);
   auto go = [&](auto kern) {
     set_smem_limit((const void*)kern, 210 * 1024);
-    kern<<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, tabs<T>(tw, sn, gtab));
+    kern<<<grid, C * 32, smem, st>>>(x, logP, dim, axis, S, scale ? 1 : 0, tabs<T>(tw, sn, gtab, factor));
   };
   // FP32: compile-time lengths (instruction-bound, the unrolled form measured 11 % faster);
   // FP64: bound by the FP64 pipe either way, the run-time-length kernel (fewer registers)
@@ -345,9 +366,9 @@ template void launch_dsti_rows<float>(float*, int, int, int, long long, int, con
 template void launch_dsti_rows<double>(double*, int, int, int, long long, int, const void*, const void*,
                                        cudaStream_t);
 template void launch_dsti_cols<float>(float*, int, int, int, long long, int, int, const void*, const void*,
-                                      const void*, bool, cudaStream_t);
+                                      const void*, bool, cudaStream_t, const DstiFactor*);
 template void launch_dsti_cols<double>(double*, int, int, int, long long, int, int, const void*, const void*,
-                                       const void*, bool, cudaStream_t);
+                                       const void*, bool, cudaStream_t, const DstiFactor*);
 
 }  // namespace pt
 

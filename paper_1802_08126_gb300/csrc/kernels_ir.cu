@@ -149,6 +149,13 @@ __global__ void k_ir_resid_u(const float* __restrict__ bp, const float* __restri
 // at or below the tolerance (or the iteration limit) asks for an FP64 step at the same index.
 __global__ void k_ir_finalize(const double* __restrict__ partials, SolveState* state, double* __restrict__ hist) {
   if (vload(&state->done) != 0) return;
+  if (vload(&state->fault) != 0) {
+    if (threadIdx.x == 0) {
+      state->status = PT_ETIMEOUT;
+      state->done = 1;
+    }
+    return;
+  }
   double v = partials[threadIdx.x];
   v = block_sum(v);
   if (threadIdx.x == 0) {

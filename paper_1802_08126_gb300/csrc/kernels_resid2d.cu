@@ -364,11 +364,7 @@ struct IrStage {
 };
 static_assert(sizeof(IrStage) % 16 == 0, "bulk copies need 16-byte aligned stage buffers");
 
-__device__ __forceinline__ void report_timeout(SolveState* st) {
-  st->status = PT_ETIMEOUT;
-  __threadfence();
-  st->done = 1;
-}
+__device__ __forceinline__ void report_timeout(SolveState* st) { *(volatile int*)&st->fault = 1; }
 
 __global__ void __launch_bounds__(kSegW + 32, 4) k_ir_inner_2d_rows(
     const float* __restrict__ du, const float* __restrict__ dp, const float* __restrict__ R1,
@@ -377,20 +373,12 @@ __global__ void __launch_bounds__(kSegW + 32, 4) k_ir_inner_2d_rows(
     int logR, long long S, int N, Steps<float> sp, SolveState* st) {
   if (*((volatile const int*)&st->done) != 0 || *((volatile const int*)&st->outer) != 0) return;
   __shared__ __align__(128) IrStage stage[kStages];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-  __shared__ int abort_flag;
+  __shared__ __align__(8) RowRing<kStages> ring;
   const int P = 1 << logP, R = 1 << logR;
   const int logSeg = logP - 8, logStrips = logP - logR;
   const long long ntasks = (long long)N << (logSeg + logStrips);
   const int tid = threadIdx.x, lane = tid & 31;
-  if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kSegW / 32);
-    }
-    abort_flag = 0;
-    mbar_init_fence();
-  }
+  if (tid == 0) ring.init(kSegW / 32);
   if (blockIdx.x == 0)
     for (int i = gridDim.x + tid; i < kReduceBlocks; i += blockDim.x) partials[i] = 0.0;
   __syncthreads();
@@ -407,9 +395,7 @@ __global__ void __launch_bounds__(kSegW + 32, 4) k_ir_inner_2d_rows(
         const int t = (int)(rest >> logStrips);
         const long long slot = (long long)t * S;
         for (int j = 0; j < R + 2; ++j, ++c) {
-          const int s = (int)(c % kStages);
-          const unsigned r = c / kStages;
-          if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, &abort_flag)) {
+          if (!ring.acquire(c)) {
             ok = false;
             break;
           }
@@ -417,30 +403,24 @@ __global__ void __launch_bounds__(kSegW + 32, 4) k_ir_inner_2d_rows(
           const bool cp_d = y <= P - 1, cp_r = j >= 2 && yr < n, cp_t = cp_r && t > 0;
           const unsigned bytes = (cp_d ? 2u * kRowDU * 4u : 0u) + (cp_r ? 2u * kSegW * 4u : 0u) +
                                  (cp_t ? (unsigned)kSegW * 4u : 0u);
-          mbar_arrive_expect_tx(&full[s], bytes);
-          IrStage& g = stage[s];
+          uint64_t* bar = ring.commit(c, bytes);
+          IrStage& g = stage[c % kStages];
           if (cp_d) {
             const long long o = slot + (long long)y * P + x0 - kHaloF;
-            bulk_g2s(g.du, du + o, kRowDU * 4u, &full[s]);
-            bulk_g2s(g.dp, dp + o, kRowDU * 4u, &full[s]);
+            bulk_g2s(g.du, du + o, kRowDU * 4u, bar);
+            bulk_g2s(g.dp, dp + o, kRowDU * 4u, bar);
           }
           if (cp_r) {
             const long long o = slot + (long long)yr * P + x0;
-            bulk_g2s(g.r1, R1 + o, kSegW * 4u, &full[s]);
-            bulk_g2s(g.r2, R2 + o, kSegW * 4u, &full[s]);
-            if (cp_t) bulk_g2s(g.dt, du + o - S, kSegW * 4u, &full[s]);
+            bulk_g2s(g.r1, R1 + o, kSegW * 4u, bar);
+            bulk_g2s(g.r2, R2 + o, kSegW * 4u, bar);
+            if (cp_t) bulk_g2s(g.dt, du + o - S, kSegW * 4u, bar);
           }
         }
       }
-      if (!ok) {
-        abort_flag = 1;
-        report_timeout(st);
-      }
-      // every stage's last fill has landed before the CTA may exit
-      for (int s = 0; s < kStages && (unsigned)s < c; ++s) {
-        const unsigned fills = (c - (unsigned)s + kStages - 1) / kStages;
-        if (!mbar_wait(&full[s], (fills - 1) & 1, nullptr)) report_timeout(st);
-      }
+      if (!ok) ring.give_up();
+      if (!ring.drain(c)) ok = false;
+      if (!ok) report_timeout(st);
     }
     __syncwarp();  // the warp reaches the final block barrier converged
   } else {
@@ -466,20 +446,16 @@ __global__ void __launch_bounds__(kSegW + 32, 4) k_ir_inner_2d_rows(
       float d_m = 0.f, d_c = 0.f, dW = 0.f, dE = 0.f, q_m = 0.f, q_c = 0.f, qW = 0.f, qE = 0.f;
       float ayl = fmaf(gxc, fy[y0], a0s);
       for (int j = 0; j < R + 2; ++j, ++c) {
-        const int s = (int)(c % kStages);
-        // every lane waits (the barrier's completion makes the copied bytes visible to it); the
-        // warp leaves together if any lane gave up
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (c / kStages) & 1, &abort_flag))) {
+        if (!ring.wait(c)) {
           ok = false;
           break;
         }
-        const IrStage& g = stage[s];
+        const IrStage& g = stage[c % kStages];
         const float d_pW = g.du[kHaloF - 1 + tid], d_p = g.du[kHaloF + tid], d_pE = g.du[kHaloF + 1 + tid];
         const float q_pW = g.dp[kHaloF - 1 + tid], q_p = g.dp[kHaloF + tid], q_pE = g.dp[kHaloF + 1 + tid];
         const float r1 = g.r1[tid], r2 = g.r2[tid];
         const float dtm = t > 0 ? g.dt[tid] : 0.f;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        ring.release(c);
         if (j >= 2) {
           const int y = y0 + j - 2;
           const bool yin = y < n;
@@ -510,7 +486,7 @@ __global__ void __launch_bounds__(kSegW + 32, 4) k_ir_inner_2d_rows(
       }
     }
     if (!ok) {
-      abort_flag = 1;
+      ring.give_up();
       if (lane == 0) report_timeout(st);
     }
   }

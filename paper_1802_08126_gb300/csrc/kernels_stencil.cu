@@ -327,6 +327,13 @@ __global__ void k_norm2_partials(const double* __restrict__ v, long long count,
 __global__ void k_finalize_residual(const double* __restrict__ partials, SolveState* state,
                                     double* __restrict__ hist) {
   if (state->done) return;
+  if (state->fault) {
+    if (threadIdx.x == 0) {
+      state->status = PT_ETIMEOUT;
+      state->done = 1;
+    }
+    return;
+  }
   double v = partials[threadIdx.x];
   v = block_sum(v);
   if (threadIdx.x == 0) {
@@ -364,6 +371,7 @@ __global__ void k_finalize_fnorm(const double* __restrict__ partials, SolveState
     state->tol = tol;
     state->max_it = max_it;
     state->last_res = 1.0;
+    state->fault = 0;
   }
 }
 

@@ -188,6 +188,8 @@ struct SolveState {
   double tol;
   int max_it;
   int outer;     // mixed precision: this iteration starts with the FP64 refinement step
+  int fault;     // set by a streamed kernel whose bounded wait ran out; the next finalize ends the
+                 // solve with PT_ETIMEOUT
 };
 
 // Mixed precision as iterative refinement (kernels_ir.cu): FP64 step every kOuter iterations
@@ -256,6 +258,7 @@ struct MGPlan {
   T a0;
   MGLevelBufs buf[kMaxLevels];
   int B;              // slices in the batch
+  int* fault;         // SolveState::fault of the owning problem (bounded waits of streamed kernels)
 };
 
 // One V(1,1) cycle with zero initial guess on all B slices: x = V(b).
@@ -327,9 +330,18 @@ constexpr int kDstiMaxM = 4096;
 template <typename T>
 void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const void* tw, const void* sn,
                       cudaStream_t st);
+// Without gtab (FP32), the scaled call forms the factor per point from DstiFactor, as
+// c l / (m_k + l)^2 with m_k = mu_k / tau and c = c0 / tau^2: lam [n+1] and m [B] in the kernel's
+// type.
+struct DstiFactor {
+  const void* lam;
+  const void* m;
+  double c;
+};
 template <typename T>
 void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
-                      const void* sn, const void* gtab, bool scale, cudaStream_t st);
+                      const void* sn, const void* gtab, bool scale, cudaStream_t st,
+                      const DstiFactor* factor = nullptr);
 // FP64 2-D: y-part of the exact block solve by tridiagonal eliminations (kernels_dsti.cu);
 // w padded like the data: the LU pivots 1/d'_i of every (k, x-frequency) column.
 template <typename T>
