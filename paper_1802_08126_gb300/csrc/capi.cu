@@ -371,14 +371,27 @@ T* block_solve(pt_problem* p, const int* done) {
       launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
       return W1;
     }
+    const DstiFactor f = {p->dsti_lamT, p->dsti_muT,
+                          (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim) / (p->tau * p->tau)};
+    if (dsti_plane_ok<T>(p->dim, p->n)) {
+      // whole planes in shared memory: one pass (2-D) or the xy passes around the z-axis pass (3-D)
+      if (p->dim == 2) {
+        launch_dsti_plane<T>(W1, 2, p->n, L.logP, L.S, p->N, 0, p->dsti_tw, p->dsti_sn, p->dsti_g, p->st,
+                             p->dsti_g ? nullptr : &f);
+      } else {
+        launch_dsti_plane<T>(W1, 3, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, nullptr, p->st, nullptr);
+        launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 2, p->dsti_tw, p->dsti_sn, p->dsti_g, true,
+                            p->st, p->dsti_g ? nullptr : &f);
+        launch_dsti_plane<T>(W1, 3, p->n, L.logP, L.S, p->N, 2, p->dsti_tw, p->dsti_sn, nullptr, p->st, nullptr);
+      }
+      return W1;
+    }
     // x, (y,) the last axis forward-scale-inverse, (y,) x: S_x S_y S_z diag(g) S_z S_y S_x
     const int last = p->dim - 1;
     launch_dsti_rows<T>(W1, p->dim, p->n, L.logP, L.S, p->N, p->dsti_tw, p->dsti_sn, p->st);
     if (p->dim == 3)
       launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, p->dsti_g, false,
                           p->st);
-    const DstiFactor f = {p->dsti_lamT, p->dsti_muT,
-                          (2.0 * p->tau / p->N) * std::pow(2.0 / L.P, p->dim) / (p->tau * p->tau)};
     launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, last, p->dsti_tw, p->dsti_sn, p->dsti_g, true,
                         p->st, p->dsti_g ? nullptr : &f);
     if (p->dim == 3)

@@ -249,6 +249,127 @@ __global__ void __launch_bounds__(kWarpsMax * 32, (sizeof(T) == 4 && LOGMC > 0 &
   }
 }
 
+// Whole planes in shared memory (M <= 128): the plane of one slot (2-D) or of one (slot, z) (3-D)
+// is loaded once, transformed along x (rows) and y (columns) by the per-warp transforms above,
+// and stored once.  MODE 0 (2-D): the whole exact block solve S_x S_y diag(g) S_y S_x; MODE 1
+// (3-D): S_y S_x before the z-axis pass; MODE 2 (3-D): S_x S_y after it.  The row pitch M + 2
+// keeps the column-pair reads of a warp (32 rows, one pair each) free of bank conflicts.
+template <int M>
+__host__ __device__ constexpr int plane_pitch() {
+  return M + 2;
+}
+
+// warps per CTA of the plane kernel: 16 for the largest planes (two CTAs per SM fit in shared
+// memory either way, so the wider CTA doubles the warps per SM), 8 otherwise
+template <int LOGM>
+__host__ __device__ constexpr int plane_warps() {
+  return LOGM >= 7 ? 16 : kWarpsMax;
+}
+
+template <typename T, int LOGM, int MODE>
+__global__ void __launch_bounds__(plane_warps<LOGM>() * 32) k_dsti_plane(T* __restrict__ x, long long S, int planes,
+                                                                         DstiTabs<T> tb) {
+  using T2 = typename Vec2<T>::type;
+  constexpr int M = 1 << LOGM, W = padded_len(M), PITCH = plane_pitch<M>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* pl = (T*)smem_raw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T2* A = (T2*)(pl + M * PITCH) + (size_t)warp * (2 * W + 1);
+  T2* B = A + W;
+  const int slice = (int)(blockIdx.x / planes), z = (int)(blockIdx.x - (long long)slice * planes);
+  const long long base = (long long)slice * S + (long long)z * M * M;
+  T* xp = x + base;
+  if (MODE != 0 && z == M - 1) {  // the ghost plane stays zero
+    for (int i = threadIdx.x; i < M * M; i += blockDim.x) xp[i] = (T)0;
+    return;
+  }
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) pl[(i >> LOGM) * PITCH + (i & (M - 1))] = xp[i];
+  __syncthreads();
+  // x: line pairs (2q, 2q + 1), in place (the row's values are in the warp's buffer before the
+  // spectrum is written back)
+  auto rows = [&]() {
+    for (int q = warp; q < M / 2; q += nw) {
+      T* ra = pl + 2 * q * PITCH;
+      T* rb = ra + PITCH;
+      dsti_pre<LOGM, T, T2>(A, M, tb.sn, lane, [&](int pos) { return mk<T2>(ra[pos], rb[pos]); });
+      __syncwarp();
+      T2* Z = fft_any<LOGM>(A, B, LOGM, tb.tw, lane);
+      T2* O = Z == A ? B : A;
+      // (through the padded buffer: the lanes' output chunks written straight into the row would
+      // collide in the shared-memory banks)
+      dsti_post<LOGM, T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
+      __syncwarp();
+#pragma unroll
+      for (int pos = lane; pos < M; pos += 32) {
+        const T2 v = O[pd(pos)];
+        ra[pos] = v.x;
+        rb[pos] = v.y;
+      }
+      __syncwarp();
+    }
+  };
+  // y: column pairs (2q, 2q + 1); MODE 0 also scales by the block-solve factor and transforms back
+  auto cols = [&]() {
+    for (int q = warp; q < M / 2; q += nw) {
+      const int xa = 2 * q;
+      T2* col = (T2*)(pl + xa);
+      auto at = [&](int pos) -> T2& { return *(T2*)((T*)col + pos * PITCH); };
+      dsti_pre<LOGM, T, T2>(A, M, tb.sn, lane, [&](int pos) { return at(pos); });
+      __syncwarp();
+      T2* Z = fft_any<LOGM>(A, B, LOGM, tb.tw, lane);
+      if (MODE == 0) {
+        T2* O = Z == A ? B : A;  // the scaled spectrum
+        if (tb.g) {
+          const T* gcol = tb.g + base + xa;
+          dsti_post<LOGM, T, T2>(Z, M, lane, [&](int pos, T2 v) {
+            const T2 g = *(const T2*)(gcol + pos * M);
+            O[pd(pos)] = mk<T2>(v.x * g.x, v.y * g.y);
+          });
+        } else {
+          const T m = tb.m[slice], c = tb.c;
+          const T la = tb.lam[xa], lb = tb.lam[xa + 1];
+          dsti_post<LOGM, T, T2>(Z, M, lane, [&](int pos, T2 v) {
+            const T lp = tb.lam[pos];
+            const T l_a = la + lp, l_b = lb + lp;
+            const T d_a = m + l_a, d_b = m + l_b;
+            O[pd(pos)] = mk<T2>(v.x * __fdividef(c * l_a, d_a * d_a), v.y * __fdividef(c * l_b, d_b * d_b));
+          });
+        }
+        __syncwarp();
+        T2* P2 = O == A ? B : A;
+        dsti_pre<LOGM, T, T2>(P2, M, tb.sn, lane, [&](int pos) { return O[pd(pos)]; });
+        __syncwarp();
+        Z = fft_any<LOGM>(P2, O, LOGM, tb.tw, lane);
+      }
+      T2* O = Z == A ? B : A;
+      dsti_post<LOGM, T, T2>(Z, M, lane, [&](int pos, T2 v) { O[pd(pos)] = v; });
+      __syncwarp();
+#pragma unroll
+      for (int pos = lane; pos < M; pos += 32) at(pos) = O[pd(pos)];
+      __syncwarp();
+    }
+  };
+  if (MODE == 2) {
+    cols();
+    __syncthreads();
+    rows();
+  } else {
+    rows();
+    __syncthreads();
+    cols();
+    if (MODE == 0) {
+      __syncthreads();
+      rows();
+    }
+  }
+  __syncthreads();
+  // store, the ghost row and column exactly zero
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) {
+    const int yy = i >> LOGM, xx = i & (M - 1);
+    xp[i] = (yy == M - 1 || xx == M - 1) ? (T)0 : pl[yy * PITCH + xx];
+  }
+}
+
 // g = c0 l / (mu_k + tau l)^2 at every padded point (0 at ghosts), l = sum of the axes' lam
 template <typename T>
 __global__ void k_dsti_scale_table(T* __restrict__ g, const double* __restrict__ lam, const double* __restrict__ mu,
@@ -328,6 +449,45 @@ void launch_dsti_rows(T* x, int dim, int n, int logP, long long S, int B, const 
 }
 
 template <typename T>
+bool dsti_plane_ok(int dim, int n) {
+  return n + 1 <= kPlaneMaxM && n + 1 >= 32 && (dim == 3 || sizeof(T) == 4);
+}
+
+template <typename T>
+void launch_dsti_plane(T* x, int dim, int n, int logP, long long S, int B, int mode, const void* tw, const void* sn,
+                       const void* gtab, cudaStream_t st, const DstiFactor* factor) {
+  using T2 = typename Vec2<T>::type;
+  const int M = n + 1;
+  const int planes = dim == 3 ? M : 1;
+  const int wpb = logP >= 7 ? plane_warps<7>() : plane_warps<6>();
+  const size_t smem = (size_t)M * (M + 2) * sizeof(T) + (size_t)wpb * (2 * padded_len(M) + 1) * sizeof(T2);
+  double d = B;
+  for (int k = 0; k < dim; ++k) d *= n;
+  LaunchScope ls(mode == 0 ? "dsti_plane_solve" : "dsti_plane", st, 2.0 * sizeof(T) * d);
+  const dim3 grid((unsigned)((long long)B * planes));
+  auto go = [&](auto kern) {
+    set_smem_limit((const void*)kern, 210 * 1024);
+    kern<<<grid, wpb * 32, smem, st>>>(x, S, planes, tabs<T>(tw, sn, gtab, factor));
+  };
+  // (mode 0 is the FP32 2-D form only: the FP64 2-D block solve takes its y-part by eliminations)
+#define PT_PLANE(LM)                                                   \
+  if (mode == 1)                                                       \
+    go(k_dsti_plane<T, LM, 1>);                                        \
+  else if (mode == 2)                                                  \
+    go(k_dsti_plane<T, LM, 2>);                                        \
+  else if constexpr (sizeof(T) == 4)                                   \
+    go(k_dsti_plane<T, LM, 0>);
+  if (logP == 5) {
+    PT_PLANE(5)
+  } else if (logP == 6) {
+    PT_PLANE(6)
+  } else {
+    PT_PLANE(7)
+  }
+#undef PT_PLANE
+}
+
+template <typename T>
 void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
                       const void* sn, const void* gtab, bool scale, cudaStream_t st, const DstiFactor* factor) {
   using T2 = typename Vec2<T>::type;
@@ -365,6 +525,12 @@ template void launch_dsti_rows<float>(float*, int, int, int, long long, int, con
                                       cudaStream_t);
 template void launch_dsti_rows<double>(double*, int, int, int, long long, int, const void*, const void*,
                                        cudaStream_t);
+template bool dsti_plane_ok<float>(int, int);
+template bool dsti_plane_ok<double>(int, int);
+template void launch_dsti_plane<float>(float*, int, int, int, long long, int, int, const void*, const void*,
+                                       const void*, cudaStream_t, const DstiFactor*);
+template void launch_dsti_plane<double>(double*, int, int, int, long long, int, int, const void*, const void*,
+                                        const void*, cudaStream_t, const DstiFactor*);
 template void launch_dsti_cols<float>(float*, int, int, int, long long, int, int, const void*, const void*,
                                       const void*, bool, cudaStream_t, const DstiFactor*);
 template void launch_dsti_cols<double>(double*, int, int, int, long long, int, int, const void*, const void*,

@@ -342,6 +342,15 @@ template <typename T>
 void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int axis, const void* tw,
                       const void* sn, const void* gtab, bool scale, cudaStream_t st,
                       const DstiFactor* factor = nullptr);
+// Planes that fit in one CTA's shared memory (32 <= n + 1 <= kPlaneMaxM): x and y transforms of a
+// whole plane in one pass.  mode 0 (2-D, FP32): the whole block solve S_x S_y diag(g) S_y S_x
+// (factor as in launch_dsti_cols); mode 1 (3-D): S_y S_x; mode 2 (3-D): S_x S_y.
+constexpr int kPlaneMaxM = 128;
+template <typename T>
+bool dsti_plane_ok(int dim, int n);
+template <typename T>
+void launch_dsti_plane(T* x, int dim, int n, int logP, long long S, int B, int mode, const void* tw, const void* sn,
+                       const void* gtab, cudaStream_t st, const DstiFactor* factor);
 // FP64 2-D: y-part of the exact block solve by tridiagonal eliminations (kernels_dsti.cu);
 // w padded like the data: the LU pivots 1/d'_i of every (k, x-frequency) column.
 template <typename T>

@@ -173,6 +173,27 @@ def test_exact_transform_H_matches_oracle_direct_solves(prob, precision):
     assert rel_err(host(out), T.apply_Hinv(r, T.exact_H_solver())) <= tol
 
 
+# 3-D grids whose xy planes fit in one CTA (n + 1 = 64, 128: the whole-plane x and y transforms
+# around the z pass) and a 2-D grid of the whole-plane block solve, against H_k solves by the
+# sine-transform solver (pinned to the sparse direct solves in tests/test_oracle_spectral.py;
+# the direct solves are too slow at these sizes)
+@pytest.mark.parametrize("prob", [S.heat3d_bumps(63, 2), S.heat3d_bumps(127, 2), S.heat2d_uniform(127, 6)],
+                         ids=lambda p: p.name)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_exact_transform_H_large_grids_match_sine_solves(prob, precision):
+    from tests.conftest import sine_H_solver
+    tol = 1e-11 if precision == "fp64" else 5e-6
+    T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
+    rng = np.random.default_rng(19)
+    r = rng.standard_normal((prob.N, prob.ns))
+    import paper_1802_08126_gb300 as ptu
+    with ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, S.source(prob), None, precision=precision,
+                     h_solver="exact") as P:
+        out = torch.empty_like(dev(r))
+        P.precond_H(dev(r), out)
+    assert rel_err(host(out), T.apply_Hinv(r, sine_H_solver(T))) <= tol
+
+
 # n + 1 <= 1024: parallel cyclic reduction; 2047: the sequential elimination
 @pytest.mark.parametrize("prob,precision", [(S.heat1d_mms(63, 64), "fp64"), (S.heat1d_mms(63, 64), "mixed"),
                                             (S.heat1d_mms(1, 4), "fp64"), (S.heat1d_mms(1, 4), "mixed"),

@@ -161,3 +161,19 @@ def test_uzawa_contraction_bound(use_mg):
         cur = dnorm(pex - pv, uex - u)
         assert cur <= rho_u * prev * (1 + 1e-8) + 1e-13
         prev = cur
+
+
+@pytest.mark.parametrize("prob", [S.heat2d_uniform(15, 4), S.heat3d_bumps(7, 3), S.heat3d_bumps(15, 2)],
+                         ids=lambda p: p.name)
+def test_sine_H_solver_equals_sparse_direct_solves(prob):
+    """The sine-transform H_k solver that the large 3-D GPU tests use agrees with the sparse direct
+    H_k solves of the oracle (§4, eq. 4.4), and so does the whole H~^-1."""
+    from tests.conftest import sine_H_solver
+    T = st.SpaceTime(prob.dim, prob.n, prob.N, prob.T, prob.coeff)
+    direct, sine = T.exact_H_solver(), sine_H_solver(T)
+    r = np.random.default_rng(11).standard_normal((prob.N, prob.ns))
+    for k in range(prob.N):
+        a, b = sine(k, r[k]), direct(k, r[k])
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+    a, b = T.apply_Hinv(r, sine), T.apply_Hinv(r, direct)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
