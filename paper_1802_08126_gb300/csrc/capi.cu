@@ -380,8 +380,8 @@ T* block_solve(pt_problem* p, const int* done) {
                              p->dsti_g ? nullptr : &f);
       } else {
         launch_dsti_plane<T>(W1, 3, p->n, L.logP, L.S, p->N, 1, p->dsti_tw, p->dsti_sn, nullptr, p->st, nullptr);
-        launch_dsti_cols<T>(W1, p->dim, p->n, L.logP, L.S, p->N, 2, p->dsti_tw, p->dsti_sn, p->dsti_g, true,
-                            p->st, p->dsti_g ? nullptr : &f);
+        launch_dsti_plane<T>(W1, 3, p->n, L.logP, L.S, p->N, 3, p->dsti_tw, p->dsti_sn, p->dsti_g, p->st,
+                             p->dsti_g ? nullptr : &f);
         launch_dsti_plane<T>(W1, 3, p->n, L.logP, L.S, p->N, 2, p->dsti_tw, p->dsti_sn, nullptr, p->st, nullptr);
       }
       return W1;

@@ -252,8 +252,10 @@ __global__ void __launch_bounds__(kWarpsMax * 32, (sizeof(T) == 4 && LOGMC > 0 &
 // Whole planes in shared memory (M <= 128): the plane of one slot (2-D) or of one (slot, z) (3-D)
 // is loaded once, transformed along x (rows) and y (columns) by the per-warp transforms above,
 // and stored once.  MODE 0 (2-D): the whole exact block solve S_x S_y diag(g) S_y S_x; MODE 1
-// (3-D): S_y S_x before the z-axis pass; MODE 2 (3-D): S_x S_y after it.  The row pitch M + 2
-// keeps the column-pair reads of a warp (32 rows, one pair each) free of bank conflicts.
+// (3-D): S_y S_x before the z-axis pass; MODE 2 (3-D): S_x S_y after it; MODE 3 (3-D): the z-axis
+// pass S_z diag(g) S_z on the x-z plane of one (slot, y) (rows z at stride M^2, columns x).  The
+// row pitch M + 2 keeps the column-pair reads of a warp (32 rows, one pair each) free of bank
+// conflicts.
 template <int M>
 __host__ __device__ constexpr int plane_pitch() {
   return M + 2;
@@ -267,7 +269,7 @@ __host__ __device__ constexpr int plane_warps() {
 }
 
 template <typename T, int LOGM, int MODE>
-__global__ void __launch_bounds__(plane_warps<LOGM>() * 32) k_dsti_plane(T* __restrict__ x, long long S, int planes,
+__global__ void __launch_bounds__(plane_warps<LOGM>() * 32, (LOGM >= 7 && sizeof(T) == 4) ? 2 : 1) k_dsti_plane(T* __restrict__ x, long long S, int planes,
                                                                          DstiTabs<T> tb) {
   using T2 = typename Vec2<T>::type;
   constexpr int M = 1 << LOGM, W = padded_len(M), PITCH = plane_pitch<M>();
@@ -276,14 +278,18 @@ __global__ void __launch_bounds__(plane_warps<LOGM>() * 32) k_dsti_plane(T* __re
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   T2* A = (T2*)(pl + M * PITCH) + (size_t)warp * (2 * W + 1);
   T2* B = A + W;
+  constexpr bool SCALE = MODE == 0 || MODE == 3;
+  constexpr long long RS = MODE == 3 ? (long long)M * M : M;  // global stride of the plane's rows
+  // z: the plane's coordinate on the third axis (z for modes 1 and 2, y for mode 3)
   const int slice = (int)(blockIdx.x / planes), z = (int)(blockIdx.x - (long long)slice * planes);
-  const long long base = (long long)slice * S + (long long)z * M * M;
+  const long long base = (long long)slice * S + (long long)z * (MODE == 3 ? M : M * M);
   T* xp = x + base;
   if (MODE != 0 && z == M - 1) {  // the ghost plane stays zero
-    for (int i = threadIdx.x; i < M * M; i += blockDim.x) xp[i] = (T)0;
+    for (int i = threadIdx.x; i < M * M; i += blockDim.x) xp[(i >> LOGM) * RS + (i & (M - 1))] = (T)0;
     return;
   }
-  for (int i = threadIdx.x; i < M * M; i += blockDim.x) pl[(i >> LOGM) * PITCH + (i & (M - 1))] = xp[i];
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x)
+    pl[(i >> LOGM) * PITCH + (i & (M - 1))] = xp[(i >> LOGM) * RS + (i & (M - 1))];
   __syncthreads();
   // x: line pairs (2q, 2q + 1), in place (the row's values are in the warp's buffer before the
   // spectrum is written back)
@@ -317,17 +323,18 @@ __global__ void __launch_bounds__(plane_warps<LOGM>() * 32) k_dsti_plane(T* __re
       dsti_pre<LOGM, T, T2>(A, M, tb.sn, lane, [&](int pos) { return at(pos); });
       __syncwarp();
       T2* Z = fft_any<LOGM>(A, B, LOGM, tb.tw, lane);
-      if (MODE == 0) {
+      if (SCALE) {
         T2* O = Z == A ? B : A;  // the scaled spectrum
         if (tb.g) {
           const T* gcol = tb.g + base + xa;
           dsti_post<LOGM, T, T2>(Z, M, lane, [&](int pos, T2 v) {
-            const T2 g = *(const T2*)(gcol + pos * M);
+            const T2 g = *(const T2*)(gcol + pos * RS);
             O[pd(pos)] = mk<T2>(v.x * g.x, v.y * g.y);
           });
         } else {
           const T m = tb.m[slice], c = tb.c;
-          const T la = tb.lam[xa], lb = tb.lam[xa + 1];
+          const T lo = MODE == 3 ? tb.lam[z] : (T)0;
+          const T la = tb.lam[xa] + lo, lb = tb.lam[xa + 1] + lo;
           dsti_post<LOGM, T, T2>(Z, M, lane, [&](int pos, T2 v) {
             const T lp = tb.lam[pos];
             const T l_a = la + lp, l_b = lb + lp;
@@ -349,7 +356,9 @@ __global__ void __launch_bounds__(plane_warps<LOGM>() * 32) k_dsti_plane(T* __re
       __syncwarp();
     }
   };
-  if (MODE == 2) {
+  if (MODE == 3) {
+    cols();
+  } else if (MODE == 2) {
     cols();
     __syncthreads();
     rows();
@@ -366,7 +375,7 @@ __global__ void __launch_bounds__(plane_warps<LOGM>() * 32) k_dsti_plane(T* __re
   // store, the ghost row and column exactly zero
   for (int i = threadIdx.x; i < M * M; i += blockDim.x) {
     const int yy = i >> LOGM, xx = i & (M - 1);
-    xp[i] = (yy == M - 1 || xx == M - 1) ? (T)0 : pl[yy * PITCH + xx];
+    xp[yy * RS + xx] = (yy == M - 1 || xx == M - 1) ? (T)0 : pl[yy * PITCH + xx];
   }
 }
 
@@ -463,7 +472,8 @@ void launch_dsti_plane(T* x, int dim, int n, int logP, long long S, int B, int m
   const size_t smem = (size_t)M * (M + 2) * sizeof(T) + (size_t)wpb * (2 * padded_len(M) + 1) * sizeof(T2);
   double d = B;
   for (int k = 0; k < dim; ++k) d *= n;
-  LaunchScope ls(mode == 0 ? "dsti_plane_solve" : "dsti_plane", st, 2.0 * sizeof(T) * d);
+  LaunchScope ls(mode == 0 ? "dsti_plane_solve" : (mode == 3 ? "dsti_plane_z" : "dsti_plane"), st,
+                 2.0 * sizeof(T) * d);
   const dim3 grid((unsigned)((long long)B * planes));
   auto go = [&](auto kern) {
     set_smem_limit((const void*)kern, 210 * 1024);
@@ -475,6 +485,8 @@ void launch_dsti_plane(T* x, int dim, int n, int logP, long long S, int B, int m
     go(k_dsti_plane<T, LM, 1>);                                        \
   else if (mode == 2)                                                  \
     go(k_dsti_plane<T, LM, 2>);                                        \
+  else if (mode == 3)                                                  \
+    go(k_dsti_plane<T, LM, 3>);                                        \
   else if constexpr (sizeof(T) == 4)                                   \
     go(k_dsti_plane<T, LM, 0>);
   if (logP == 5) {

@@ -344,7 +344,8 @@ void launch_dsti_cols(T* x, int dim, int n, int logP, long long S, int B, int ax
                       const DstiFactor* factor = nullptr);
 // Planes that fit in one CTA's shared memory (32 <= n + 1 <= kPlaneMaxM): x and y transforms of a
 // whole plane in one pass.  mode 0 (2-D, FP32): the whole block solve S_x S_y diag(g) S_y S_x
-// (factor as in launch_dsti_cols); mode 1 (3-D): S_y S_x; mode 2 (3-D): S_x S_y.
+// (factor as in launch_dsti_cols); mode 1 (3-D): S_y S_x; mode 2 (3-D): S_x S_y; mode 3 (3-D):
+// S_z diag(g) S_z on the x-z planes.
 constexpr int kPlaneMaxM = 128;
 template <typename T>
 bool dsti_plane_ok(int dim, int n);
