@@ -573,7 +573,7 @@ __device__ __forceinline__ LaneCols lane_cols(const Mg2Args<float>& a, int x, fl
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_mg2s_up_f32(const float* __restrict__ bf, const float* __restrict__ ec,
+__global__ void __launch_bounds__(256, 5) k_mg2s_up_f32(const float* __restrict__ bf, const float* __restrict__ ec,
                                                      float* __restrict__ out, Mg2Args<float> a, int wpr, int strips,
                                                      long long nwarps, const int* done) {
   if (stop_requested(done)) return;

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) k_ir_inner_2d(
 // k_ir_inner_2d, term by term.  The grid is persistent (one wave) and every CTA takes the tasks
 // blockIdx.x, blockIdx.x + gridDim.x, ... in order, so the producer runs ahead across strips.
 constexpr int kSegW = 256;
-constexpr int kStages = 6;
+constexpr int kStages = 8;
 constexpr int kHaloF = 4;
 constexpr int kRowDU = kSegW + 2 * kHaloF;
 

@@ -123,12 +123,12 @@ def test_apply_B_matches_oracle(prob):
 
 
 # 63^2 and 127^2 reach the warp-strip level kernels (fine levels of width >= 64), 255^2 and 511^2
-# the row-streamed FP32 up-sweep (one and two 256-column segments, the second on two levels);
-# 15^3 and 31^3 the 3-D levels run by the level kernels (slices above 1024 points) before the
-# one-CTA coarse kernel
+# wider 2-D levels; 15^3, 31^3 and 63^3 the 3-D levels run by the level kernels (slices above 1024
+# points: one, two and three levels) before the one-CTA coarse kernel
 @pytest.mark.parametrize("prob", SMALL[:4] + [S.heat2d_uniform(63, 3), S.heat2d_uniform(127, 2),
                                               S.heat2d_uniform(255, 3), S.heat2d_uniform(511, 2),
-                                              S.heat3d_bumps(15, 3), S.heat3d_bumps(31, 2), S.heat1d_mms(2047, 2)],
+                                              S.heat3d_bumps(15, 3), S.heat3d_bumps(31, 2), S.heat3d_bumps(63, 2),
+                                              S.heat1d_mms(2047, 2)],
                          ids=lambda p: p.name)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("cycles", [1, 2, 3])
