@@ -272,8 +272,10 @@ __global__ void k_dst_inverse(const T* __restrict__ y, void* out, int mode, doub
 constexpr int kStockMaxN = 2048;
 constexpr int kStockThreads = 256;  // (FP32: 4 CTAs per SM, FP64: 2 -- the register budget)
 
-template <typename T>
-__global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_forward_s(T* x, long long S, ColGeom cg, DstPlan<T> plan,
+// MINB: CTAs per SM the register budget is sized for (FP32: 3 for N >= 1024, where the unspilled
+// 80-register form measured faster, 4 below; FP64: 2)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kStockThreads, MINB) k_dst_forward_s(T* x, long long S, ColGeom cg, DstPlan<T> plan,
                                                                  int F, const int* done) {
   using T2 = typename Vec2<T>::type;
   if (stop_requested(done)) return;
@@ -363,8 +365,8 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kStockThreads, sizeof(T) == 4 ? 4 : 2) k_dst_inverse_s(const T* __restrict__ y, void* out, int mode,
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kStockThreads, MINB) k_dst_inverse_s(const T* __restrict__ y, void* out, int mode,
                                                                  double omega, long long S, ColGeom cg,
                                                                  DstPlan<T> plan, int F, const int* done) {
   using T2 = typename Vec2<T>::type;
@@ -536,11 +538,21 @@ void launch_dst_forward(T* x, long long S, int dim, int n, int logP, DstPlan<T> 
   for (int d = 0; d < dim; ++d) interior *= n;
   LaunchScope ls("dst_forward", st, 2.0 * sizeof(T) * interior);
   if (stockham_ok(plan)) {
-    set_smem_limit((const void*)k_dst_forward_s<T>, 200 * 1024);
     const int F = stockham_cols(plan, S);
     const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
     const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2);
-    k_dst_forward_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(x, S, cg, plan, F, done);
+    auto go = [&](auto kern) {
+      set_smem_limit((const void*)kern, 200 * 1024);
+      kern<<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(x, S, cg, plan, F, done);
+    };
+    if constexpr (sizeof(T) == 8) {
+      go(k_dst_forward_s<T, 2>);
+    } else {
+      if (plan.N >= 1024)
+        go(k_dst_forward_s<T, 3>);
+      else
+        go(k_dst_forward_s<T, 4>);
+    }
   } else if (plan.M > 0) {
     set_smem_limit((const void*)k_dst_forward<T, true>, 200 * 1024);
     k_dst_forward<T, true><<<blocks, kThreads, smem, st>>>(x, S, cg, plan, C, done);
@@ -564,12 +576,22 @@ void launch_dst_inverse(const T* y, void* out, int mode, double omega, long long
   LaunchScope ls("dst_inverse", st,
                  (sizeof(T) + (mode == 1 ? 16.0 : mode == 2 ? 2.0 * sizeof(T) : (double)sizeof(T))) * interior);
   if (stockham_ok(plan)) {
-    set_smem_limit((const void*)k_dst_inverse_s<T>, 200 * 1024);
     const int F = stockham_cols(plan, S);
     const int nthr = plan.N >= 8 ? plan.N >> 3 : 1;
     const size_t sm = (size_t)F * padded_len(plan.N) * sizeof(T2) +
                       (mode == 2 && sizeof(T2) == 8 ? (size_t)F * plan.N * sizeof(T2) : 0);
-    k_dst_inverse_s<T><<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(y, out, mode, omega, S, cg, plan, F, done);
+    auto go = [&](auto kern) {
+      set_smem_limit((const void*)kern, 200 * 1024);
+      kern<<<(unsigned)(S / (2 * F)), F * nthr, sm, st>>>(y, out, mode, omega, S, cg, plan, F, done);
+    };
+    if constexpr (sizeof(T) == 8) {
+      go(k_dst_inverse_s<T, 2>);
+    } else {
+      if (plan.N >= 1024)
+        go(k_dst_inverse_s<T, 3>);
+      else
+        go(k_dst_inverse_s<T, 4>);
+    }
   } else if (plan.M > 0) {
     set_smem_limit((const void*)k_dst_inverse<T, true>, 200 * 1024);
     k_dst_inverse<T, true><<<blocks, kThreads, smem, st>>>(y, out, mode, omega, S, cg, plan, C, done);

@@ -172,7 +172,7 @@ __host__ __device__ __forceinline__ int cols_stride(int W) {
 }
 
 template <typename T, int LOGMC>
-__global__ void __launch_bounds__(kWarpsMax * 32, (sizeof(T) == 4 && LOGMC > 0 && LOGMC <= 8) ? 4 : 1) k_dsti_cols(T* __restrict__ x, int logM_rt, int dim, int axis,
+__global__ void __launch_bounds__(kWarpsMax * 32, (sizeof(T) == 4 && LOGMC > 0 && LOGMC <= 8) ? 5 : 1) k_dsti_cols(T* __restrict__ x, int logM_rt, int dim, int axis,
                                                               long long S, int scale, DstiTabs<T> tb) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
