@@ -736,15 +736,220 @@ __global__ void __launch_bounds__(256) k_ir_outer_3d(
 
 }  // namespace
 
+namespace {
+
+// Streamed form of the 3-D FP32 step for 32 <= P <= 128: a CTA owns a band of YB = 256 / P rows
+// (all P columns) of one slot and walks a strip of R z-planes, one thread per (x, y) of the band.
+// Stage j holds the du and dp rows y0 - 1 .. y0 + YB of plane z0 - 1 + j (the band's rows are
+// contiguous: one bulk copy per array, with a 16-byte halo before and after) and the R1, R2 and
+// previous-slot du rows of the band on plane z0 - 2 + j, so the stage that completes the 7-point
+// stencil of plane z also brings that plane's other operands.  x- and y-neighbours come from the
+// stage, z-neighbours from registers; the arithmetic is that of k_ir_inner_3d term by term.
+constexpr int kBand = 256;
+constexpr int kStages3 = 6;
+
+template <int LOGP>
+struct IrStage3 {
+  static constexpr int P = 1 << LOGP, YB = kBand / P, DU = (YB + 2) * P + 2 * kHaloF;
+  float du[DU];
+  float dp[DU];
+  float r1[kBand];
+  float r2[kBand];
+  float dt[kBand];
+};
+
+template <int LOGP>
+__global__ void __launch_bounds__(kBand + 32, 4) k_ir_inner_3d_rows(
+    const float* __restrict__ du, const float* __restrict__ dp, const float* __restrict__ R1,
+    const float* __restrict__ R2, float* __restrict__ bp, float* __restrict__ rp, double* __restrict__ partials,
+    const float* __restrict__ tabf, const float* __restrict__ cthf, float a0s, float s_h2, int n, int logR,
+    long long S, int N, Steps<float> sp, SolveState* st) {
+  using Stage = IrStage3<LOGP>;
+  constexpr int P = Stage::P, YB = Stage::YB, DU = Stage::DU;
+  static_assert(sizeof(Stage) % 16 == 0, "bulk copies need 16-byte aligned stage buffers");
+  if (*((volatile const int*)&st->done) != 0 || *((volatile const int*)&st->outer) != 0) return;
+  __shared__ __align__(128) Stage stage[kStages3];
+  __shared__ __align__(8) RowRing<kStages3> ring;
+  const int R = 1 << logR;
+  constexpr int bands = P / YB;
+  const int strips = P >> logR;
+  const long long ntasks = (long long)N * bands * strips;
+  const long long P2 = (long long)P * P;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) ring.init(kBand / 32);
+  if (blockIdx.x == 0)
+    for (int i = gridDim.x + tid; i < kReduceBlocks; i += blockDim.x) partials[i] = 0.0;
+  __syncthreads();
+  float acc = 0.f;
+  if (tid >= kBand) {
+    if (lane == 0) {
+      bool ok = true;
+      unsigned c = 0;
+      for (long long task = blockIdx.x; task < ntasks && ok; task += gridDim.x) {
+        const int y0 = (int)(task % bands) * YB;
+        const long long rest = task / bands;
+        const int z0 = (int)(rest % strips) << logR;
+        const int t = (int)(rest / strips);
+        const long long slot = (long long)t * S;
+        for (int j = 0; j < R + 2; ++j, ++c) {
+          if (!ring.acquire(c)) {
+            ok = false;
+            break;
+          }
+          const int z = z0 - 1 + j, zr = z - 1;
+          // planes up to P - 1 (the ghost plane as the last z-neighbour); the row after the band
+          // is left out when it would be row P (past the slot, past the array for the last slot)
+          const bool cp_d = z <= P - 1;
+          const unsigned dbytes = (unsigned)(y0 + YB < P ? DU : DU - P) * 4u;
+          const bool cp_r = j >= 2 && zr < n, cp_t = cp_r && t > 0;
+          const unsigned bytes = (cp_d ? 2u * dbytes : 0u) + (cp_r ? 2u * kBand * 4u : 0u) +
+                                 (cp_t ? (unsigned)kBand * 4u : 0u);
+          uint64_t* bar = ring.commit(c, bytes);
+          Stage& g = stage[c % kStages3];
+          if (cp_d) {
+            const long long o = slot + ((long long)z * P + y0 - 1) * P - kHaloF;
+            bulk_g2s(g.du, du + o, dbytes, bar);
+            bulk_g2s(g.dp, dp + o, dbytes, bar);
+          }
+          if (cp_r) {
+            const long long o = slot + ((long long)zr * P + y0) * P;
+            bulk_g2s(g.r1, R1 + o, kBand * 4u, bar);
+            bulk_g2s(g.r2, R2 + o, kBand * 4u, bar);
+            if (cp_t) bulk_g2s(g.dt, du + o - S, kBand * 4u, bar);
+          }
+        }
+      }
+      if (!ok) ring.give_up();
+      if (!ring.drain(c)) ok = false;
+      if (!ok) report_timeout(st);
+    }
+    __syncwarp();
+  } else {
+    const float* nx = tabf;
+    const float* fx = tabf + P;
+    const float* ny = tabf + 2 * P;
+    const float* fy = tabf + 3 * P;
+    const float* nz = tabf + 4 * P;
+    const float* fz = tabf + 5 * P;
+    const int x = tid & (P - 1), yl = tid >> LOGP;
+    const int sc = kHaloF + (yl + 1) * P + x;  // this thread's point in a stage's du / dp rows
+    bool ok = true;
+    unsigned c = 0;
+    for (long long task = blockIdx.x; task < ntasks && ok; task += gridDim.x) {
+      const int y0 = (int)(task % bands) * YB;
+      const long long rest = task / bands;
+      const int z0 = (int)(rest % strips) << logR;
+      const int t = (int)(rest / strips);
+      const int y = y0 + yl;
+      const bool xyin = x < n && y < n;
+      const float ct = s_h2 * cthf[t];
+      const float sg = sp.sig[t], rh = sp.rho[t];
+      const float gx = nx[x], gy = ny[y];
+      const float fxl = fx[x], fxr = fx[x + 1 < P ? x + 1 : x];
+      const float fyl = fy[y], fyu = fy[y + 1 < P ? y + 1 : y];
+      const float gxy = ct * gx * gy;
+      float* bpt = bp + (long long)t * S + (long long)y * P + x;
+      float* rpt = rp + (long long)t * S + (long long)y * P + x;
+      float d_m = 0.f, d_c = 0.f, dW = 0.f, dE = 0.f, dS = 0.f, dN = 0.f;
+      float q_m = 0.f, q_c = 0.f, qW = 0.f, qE = 0.f, qS = 0.f, qN = 0.f;
+      float azl = fmaf(gxy, fz[z0], a0s);
+      for (int j = 0; j < R + 2; ++j, ++c) {
+        if (!ring.wait(c)) {
+          ok = false;
+          break;
+        }
+        const Stage& g = stage[c % kStages3];
+        const float d_p = g.du[sc], d_pW = g.du[sc - 1], d_pE = g.du[sc + 1], d_pS = g.du[sc - P],
+                    d_pN = g.du[sc + P];
+        const float q_p = g.dp[sc], q_pW = g.dp[sc - 1], q_pE = g.dp[sc + 1], q_pS = g.dp[sc - P],
+                    q_pN = g.dp[sc + P];
+        const float r1 = g.r1[tid], r2 = g.r2[tid];
+        const float dtm = t > 0 ? g.dt[tid] : 0.f;
+        ring.release(c);
+        if (j >= 2) {
+          const int z = z0 + j - 2;
+          const bool in = xyin && z < n;
+          const float azu = fmaf(gxy, fz[z + 1 < P ? z + 1 : z], a0s);
+          float b = 0.f, r = 0.f;
+          if (in) {
+            const float gz = ct * nz[z];
+            const float gyz = gz * gy, gxz = gz * gx;
+            const float axl = fmaf(gyz, fxl, a0s), axr = fmaf(gyz, fxr, a0s);
+            const float ayl = fmaf(gxz, fyl, a0s), ayu = fmaf(gxz, fyu, a0s);
+            const float Kd = d_c - dtm;
+            const float sd = axl * (d_c - dW) + axr * (d_c - dE) + ayl * (d_c - dS) + ayu * (d_c - dN) +
+                             azl * (d_c - d_m) + azu * (d_c - d_p);
+            const float sq = axl * (q_c - qW) + axr * (q_c - qE) + ayl * (q_c - qS) + ayu * (q_c - qN) +
+                             azl * (q_c - q_m) + azu * (q_c - q_p);
+            b = fmaf(-sg, sd, r2 - Kd);
+            r = (fmaf(-sg, sq, Kd) - r1) * rh;
+            acc = fmaf(b, b, acc);
+          }
+          bpt[z * P2] = b;
+          rpt[z * P2] = r;
+          azl = azu;
+        }
+        d_m = d_c;
+        d_c = d_p;
+        dW = d_pW;
+        dE = d_pE;
+        dS = d_pS;
+        dN = d_pN;
+        q_m = q_c;
+        q_c = q_p;
+        qW = q_pW;
+        qE = q_pE;
+        qS = q_pS;
+        qN = q_pN;
+      }
+    }
+    if (!ok) {
+      ring.give_up();
+      if (lane == 0) report_timeout(st);
+    }
+  }
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <int LOGP>
+void launch_ir_inner_3d_rows(const float* du, const float* dp, const float* R1, const float* R2, float* bp,
+                             float* rp, double* partials, const float* tabf, const float* cthf, float a0s,
+                             float s_h2, int n, long long S, int N, Steps<float> sp, SolveState* st, cudaStream_t s) {
+  constexpr int P = 1 << LOGP;
+  const int grid = resident_grid((const void*)k_ir_inner_3d_rows<LOGP>, kBand + 32, 0, kReduceBlocks);
+  // strips of 32 planes, shorter while there would be fewer than four tasks per CTA
+  int logR = 5;
+  while (logR > 3 && (long long)N * (P / (kBand / P)) * (P >> logR) < 4LL * grid) --logR;
+  k_ir_inner_3d_rows<LOGP><<<grid, kBand + 32, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, a0s, s_h2, n,
+                                                      logR, S, N, sp, st);
+}
+
+}  // namespace
+
+void prepare_ir_inner_3d() {
+  resident_grid((const void*)k_ir_inner_3d_rows<5>, kBand + 32, 0, kReduceBlocks);
+  resident_grid((const void*)k_ir_inner_3d_rows<6>, kBand + 32, 0, kReduceBlocks);
+  resident_grid((const void*)k_ir_inner_3d_rows<7>, kBand + 32, 0, kReduceBlocks);
+}
+
 void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s) {
+                        int n, int logP, long long S, int N, Steps<float> sp, SolveState* st, cudaStream_t s) {
   const int P = 1 << logP;
   const long long nwarps = (long long)(P / 32) * P * (P / kRows) * N;
   const double s_h2 = tau / (h * h);
   LaunchScope ls("ir_inner", s, 24.0 * (double)n * n * n * N, 0.0, kInnerStep);
-  k_ir_inner_3d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, (float)(s_h2 * a0),
-                                              (float)s_h2, n, logP, S, nwarps, sp, st);
+  const float a0s = (float)(s_h2 * a0), sh = (float)s_h2;
+  if (logP == 5)
+    launch_ir_inner_3d_rows<5>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, a0s, sh, n, S, N, sp, st, s);
+  else if (logP == 6)
+    launch_ir_inner_3d_rows<6>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, a0s, sh, n, S, N, sp, st, s);
+  else if (logP == 7)
+    launch_ir_inner_3d_rows<7>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, a0s, sh, n, S, N, sp, st, s);
+  else
+    k_ir_inner_3d<<<kReduceBlocks, 256, 0, s>>>(du, dp, R1, R2, bp, rp, partials, tabf, cthf, a0s, sh, n, logP, S,
+                                                nwarps, sp, st);
 }
 
 void launch_ir_outer_3d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,

@@ -210,14 +210,16 @@ void launch_ir_outer_2d(const double* u, const double* p, const double* F, float
                         double* partials, const double* tab, const float* tabf, const double* cth, double a0,
                         double tau, double h, int n, int logP, long long S, int N, Steps<double> sp,
                         const SolveState* st, cudaStream_t s);
-// Occupancy query of the streamed 2-D kernel, done at problem setup (outside any stream capture).
+// Occupancy queries of the streamed 2-D and 3-D kernels, done at problem setup (outside any
+// stream capture).
 void prepare_ir_inner_2d();
+void prepare_ir_inner_3d();
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
                         int n, int logP, long long S, int N, Steps<float> sp, SolveState* st, cudaStream_t s);
 void launch_ir_inner_3d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
-                        int n, int logP, long long S, int N, Steps<float> sp, const SolveState* st, cudaStream_t s);
+                        int n, int logP, long long S, int N, Steps<float> sp, SolveState* st, cudaStream_t s);
 void launch_ir_outer_3d(const double* u, const double* p, const double* F, float* R1, float* R2, float* rp,
                         double* partials, const double* tab, const float* tabf, const double* cth, double a0,
                         double tau, double h, int n, int logP, long long S, int N, Steps<double> sp,
