@@ -10,8 +10,10 @@
 // padded points are finished by one CTA per slice in shared memory.
 //
 // Also here: the exact batched tridiagonal solve used for 1-D problems.
+#include <algorithm>
 #include <cmath>
 
+#include "bulk_pipe.cuh"
 #include "stencil_common.cuh"
 
 namespace pt {
@@ -183,6 +185,182 @@ __global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ ec, Stenc
     long long t;
     int xx, y, z;
     if (decode<DIM>(i, g.logP, g.n, t, xx, y, z)) x[i] += prolong_at<DIM, T>(ec, t * Sc, Pc, xx, y, z);
+  }
+}
+
+// ---- 3-D FP32 levels of 32 <= P <= 128: residual and post-smoothing streamed by rows ----
+// A CTA owns a band of YB = 256 / P rows (all P columns) of one slice and walks a strip of R
+// z-planes, one thread per (x, y); a producer warp bulk-copies, plane after plane, the band's x
+// rows y0 - 1 .. y0 + YB (contiguous, with a 16-byte halo each side) and its b row into a ring of
+// stages (stage j: x of plane z0 - 1 + j, b of plane z0 - 2 + j).  x- and y-neighbours come from
+// the stage, z-neighbours from registers.  The arithmetic is that of k_residual / k_post_smooth
+// (faces, diagonal and stencil formed in the same order, the exact division), so the V-cycle keeps
+// the first Jacobi step's factor.  KIND 1: r = b - L x; 2: out (mode) x + w (b - L x) / D.
+constexpr int kLvBand = 256, kLvStages = 8, kLvHalo = 4;
+
+template <int LOGP>
+struct LvStage {
+  static constexpr int P = 1 << LOGP, YB = kLvBand / P, XR = (YB + 2) * P + 2 * kLvHalo;
+  float x[XR];
+  float b[kLvBand];
+};
+
+__device__ __forceinline__ void lv_timeout(int* fault) {
+  if (fault) *(volatile int*)fault = 1;
+}
+
+template <int LOGP, int KIND>
+__global__ void __launch_bounds__(kLvBand + 32, 4) k_level3_rows(const float* __restrict__ b,
+                                                                 const float* __restrict__ x, void* out, int mode,
+                                                                 int out_fp64, StencilGeom<float> g,
+                                                                 OpBatch<float> op, int B, int logR, int* fault,
+                                                                 const int* done) {
+  using Stage = LvStage<LOGP>;
+  constexpr int P = Stage::P, YB = Stage::YB, XR = Stage::XR;
+  static_assert(sizeof(Stage) % 16 == 0, "bulk copies need 16-byte aligned stage buffers");
+  if (stop_requested(done)) return;
+  __shared__ __align__(128) Stage stage[kLvStages];
+  __shared__ __align__(8) RowRing<kLvStages> ring;
+  const int R = 1 << logR;
+  constexpr int bands = P / YB;
+  const int strips = P >> logR;
+  const long long ntasks = (long long)B * bands * strips;
+  const long long P2 = (long long)P * P;
+  const int n = g.n;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) ring.init(kLvBand / 32);
+  __syncthreads();
+  if (tid >= kLvBand) {
+    if (lane == 0) {
+      bool ok = true;
+      unsigned c = 0;
+      for (long long task = blockIdx.x; task < ntasks && ok; task += gridDim.x) {
+        const int y0 = (int)(task % bands) * YB;
+        const long long rest = task / bands;
+        const int z0 = (int)(rest % strips) << logR;
+        const int t = (int)(rest / strips);
+        const long long slot = (long long)t * g.S;
+        for (int j = 0; j < R + 2; ++j, ++c) {
+          if (!ring.acquire(c)) {
+            ok = false;
+            break;
+          }
+          const int z = z0 - 1 + j, zr = z - 1;
+          const bool cp_x = z <= P - 1;
+          const unsigned xbytes = (unsigned)(y0 + YB < P ? XR : XR - P) * 4u;
+          const bool cp_b = j >= 2 && zr < n;
+          const unsigned bytes = (cp_x ? xbytes : 0u) + (cp_b ? (unsigned)kLvBand * 4u : 0u);
+          uint64_t* bar = ring.commit(c, bytes);
+          Stage& s = stage[c % kLvStages];
+          if (cp_x) bulk_g2s(s.x, x + slot + ((long long)z * P + y0 - 1) * P - kLvHalo, xbytes, bar);
+          if (cp_b) bulk_g2s(s.b, b + slot + ((long long)zr * P + y0) * P, kLvBand * 4u, bar);
+        }
+      }
+      if (!ok) ring.give_up();
+      if (!ring.drain(c)) ok = false;
+      if (!ok) lv_timeout(fault);
+    }
+    return;
+  }
+  const float* nx = g.tab;
+  const float* fx = g.tab + P;
+  const float* ny = g.tab + 2 * P;
+  const float* fy = g.tab + 3 * P;
+  const float* nz = g.tab + 4 * P;
+  const float* fz = g.tab + 5 * P;
+  const float a0 = g.a0, sh = op.s * g.h2inv;
+  const int xx = tid & (P - 1), yl = tid >> LOGP;
+  const int sc = kLvHalo + (yl + 1) * P + xx;
+  bool ok = true;
+  unsigned c = 0;
+  for (long long task = blockIdx.x; task < ntasks && ok; task += gridDim.x) {
+    const int y0 = (int)(task % bands) * YB;
+    const long long rest = task / bands;
+    const int z0 = (int)(rest % strips) << logR;
+    const int t = (int)(rest / strips);
+    const int y = y0 + yl;
+    const bool xyin = xx < n && y < n;
+    const float cth = op.cth[t], sig = op.sig[t];
+    const float cx = cth * nx[xx], cy = ny[y];
+    const float fxl = fx[xx], fxr = fx[xx + 1 < P ? xx + 1 : xx];
+    const float fyl = fy[y], fyu = fy[y + 1 < P ? y + 1 : y];
+    const long long o0 = (long long)t * g.S + (long long)y * P + xx;
+    float x_m = 0.f, x_c = 0.f, xW = 0.f, xE = 0.f, xS = 0.f, xN = 0.f;
+    for (int j = 0; j < R + 2; ++j, ++c) {
+      if (!ring.wait(c)) {
+        ok = false;
+        break;
+      }
+      const Stage& s = stage[c % kLvStages];
+      const float x_p = s.x[sc], x_pW = s.x[sc - 1], x_pE = s.x[sc + 1], x_pS = s.x[sc - P], x_pN = s.x[sc + P];
+      const float bi = s.b[tid];
+      ring.release(c);
+      if (j >= 2) {
+        const int z = z0 + j - 2;
+        const bool in = xyin && z < n;
+        const long long o = o0 + z * P2;
+        if (in) {
+          const float cz = nz[z];
+          const float gyz = cth * cy * cz;
+          const float am0 = fmaf(gyz, fxl, a0), ap0 = fmaf(gyz, fxr, a0);
+          const float gxz = cx * cz;
+          const float am1 = fmaf(gxz, fyl, a0), ap1 = fmaf(gxz, fyu, a0);
+          const float gxy = cx * cy;
+          const float am2 = fmaf(gxy, fz[z], a0), ap2 = fmaf(gxy, fz[z + 1], a0);
+          float st = am0 * (x_c - xW) + ap0 * (x_c - xE);
+          st += am1 * (x_c - xS) + ap1 * (x_c - xN);
+          st += am2 * (x_c - x_m) + ap2 * (x_c - x_p);
+          const float Lx = sig * x_c + sh * st;
+          if (KIND == 1) {
+            ((float*)out)[o] = bi - Lx;
+          } else {
+            float fs = am0 + ap0;
+            fs += am1 + ap1;
+            fs += am2 + ap2;
+            const float D = sig + sh * fs;
+            store_out<float>(out, o, mode, out_fp64, x_c + op.omega * (bi - Lx) / D);
+          }
+        } else if (KIND == 1) {
+          ((float*)out)[o] = 0.f;
+        } else if (mode == 0) {
+          store_out<float>(out, o, 0, out_fp64, 0.f);
+        }
+      }
+      x_m = x_c;
+      x_c = x_p;
+      xW = x_pW;
+      xE = x_pE;
+      xS = x_pS;
+      xN = x_pN;
+    }
+  }
+  if (!ok) {
+    ring.give_up();
+    if (lane == 0) lv_timeout(fault);
+  }
+}
+
+// the streamed form when it applies (FP32, 3-D, 32 <= P <= 128); false otherwise
+template <typename T, int KIND>
+bool launch_level3_rows(const T* b, const T* x, void* out, int mode, int out_fp64, StencilGeom<T> g, OpBatch<T> op,
+                        int B, int* fault, const int* done, cudaStream_t st) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    if (g.dim != 3 || g.P < 32 || g.P > 128 || op.mass != 0) return false;
+    auto go = [&](auto kern, int P) {
+      const int grid = resident_grid((const void*)kern, kLvBand + 32, 0, 1 << 30);
+      int logR = 5;
+      while (logR > 3 && (long long)B * (P / (kLvBand / P)) * (P >> logR) < 4LL * grid) --logR;
+      kern<<<grid, kLvBand + 32, 0, st>>>(b, x, out, mode, out_fp64, g, op, B, logR, fault, done);
+    };
+    if (g.P == 32)
+      go(k_level3_rows<5, KIND>, 32);
+    else if (g.P == 64)
+      go(k_level3_rows<6, KIND>, 64);
+    else
+      go(k_level3_rows<7, KIND>, 128);
+    return true;
   }
 }
 
@@ -538,7 +716,8 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     }
     {
       LaunchScope ls("mg_residual", st, 3 * s * df);
-      k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, r, g, op, total, done);
+      if (!launch_level3_rows<T, 1>(bl, x, r, 0, 0, g, op, B, plan.fault, done, st))
+        k_residual<DIM, T><<<grid_for(total), kThreads, 0, st>>>(bl, x, r, g, op, total, done);
     }
     const long long total_c = C.S * B;
     {
@@ -567,11 +746,13 @@ void vcycle_dim(const MGPlan<T>& plan, OpBatch<T> op, const T* b0, void* out, in
     if (l == 0) {
       const double ob = out_fp64 ? (mode == 1 ? 16.0 : 8.0) : (mode == 1 ? 2 * s : s);
       LaunchScope ls("mg_post_smooth", st, (2 * s + ob) * df);
-      k_post_smooth<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, out, mode, out_fp64, g, op, total,
-                                                                  done);
+      if (!launch_level3_rows<T, 2>(b, x, out, mode, out_fp64, g, op, B, plan.fault, done, st))
+        k_post_smooth<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, out, mode, out_fp64, g, op, total,
+                                                                    done);
     } else {
       LaunchScope ls("mg_post_smooth", st, 3 * s * df);
-      k_post_smooth<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, 0, 0, g, op, total, done);
+      if (!launch_level3_rows<T, 2>(b, x, r, 0, 0, g, op, B, plan.fault, done, st))
+        k_post_smooth<DIM, T><<<grid_for(total), kThreads, 0, st>>>(b, x, r, 0, 0, g, op, total, done);
     }
   }
 }
