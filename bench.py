@@ -789,7 +789,7 @@ def main():
 
     tail = {}
     if not args.no_extras and rank == 0:
-        # the benchmark spec's GMG-only form: two V-cycles per H_k solve instead of the transform solves
+        # the multigrid-only form: two V-cycles per H_k solve instead of the transform solves
         Pv = ptu.Problem(prob.dim, prob.n, prob.N, prob.T, prob.coeff, f, u0, precision="fp64", omega=args.omega,
                          h_solver="vcycle")
         Pv.solve(args.tol, args.max_it)

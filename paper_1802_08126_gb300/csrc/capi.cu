@@ -1788,7 +1788,7 @@ pt_status pt_solve_batch(pt_problem** ps, int count, const double* tol, const in
   // and the control kernel, so a whole run of rounds is a single graph launch; the loop ends on
   // the device once a quarter of the active set has finished (all of it when one is left), or
   // after the round limit.  Then the host drops the finished problems and launches again.  If
-  // the driver cannot build conditional nodes, one plain graph launch per round is used instead.
+  // the CUDA driver cannot build conditional nodes, one plain graph launch per round is used instead.
   const int limit = max_rounds + 2;
   bool device_loop = graphs;
   auto rebuild = [&]() -> cudaError_t {
