@@ -158,7 +158,9 @@ pt_status pt_problem_set_rhs_uniform(pt_problem* p, unsigned long long seed, con
  *   res_hist: host array of max_it + 1 doubles receiving ||F - B u_j||/||F||, j = 0..iters
  *             (res_hist[0] = 1); or NULL.
  *   iters   : host int receiving the number of updates performed; or NULL.
- * Returns PT_OK, PT_ENOTCONV (u_out still written) or PT_EDIVERGED, or an error. */
+ * Returns PT_OK, PT_ENOTCONV (u_out still written) or PT_EDIVERGED, or an error.  PT_ETIMEOUT
+ * means a bounded wait inside one of the row-streamed kernels (mixed precision) ran out: the
+ * solve stopped at the next residual check and its iterate is not meaningful. */
 pt_status pt_solve(pt_problem* p, double tol, int max_it, double* u_out, int u_out_on_device,
                    double* res_hist, int* iters);
 
@@ -246,11 +248,14 @@ pt_status pt_dst_forward(pt_problem* p, const double* r_dev, double* out_dev);
 pt_status pt_dst_inverse(pt_problem* p, const double* y_dev, double* out_dev);
 
 /* out = A~^-1 r: slice n gets the spatial solver of tau_n A_n (one V-cycle, or the exact
- * tridiagonal solve in 1-D) applied to r_n (§3, eq. 3.2). */
+ * tridiagonal solve in 1-D) applied to r_n (§3, eq. 3.2).  Returns after the work has finished
+ * on the stream (it reads back whether a bounded wait of a row-streamed kernel ran out:
+ * PT_ETIMEOUT, out not meaningful). */
 pt_status pt_precond_A(pt_problem* p, const double* r_dev, double* out_dev);
 
 /* out = H~^-1 r = Phi^-1 Hhat~^-1 Phi^-T r with Hhat~_k^-1 = (2 tau/N) H~_k^-1 Abar H~_k^-1,
- * H_k = mu_k M + tau Abar, mu_k = 2 sin((2k-1) pi/(4N))  (§4, eq. 4.4-4.6). */
+ * H_k = mu_k M + tau Abar, mu_k = 2 sin((2k-1) pi/(4N))  (§4, eq. 4.4-4.6).  Returns after the
+ * work has finished, as pt_precond_A. */
 pt_status pt_precond_H(pt_problem* p, const double* r_dev, double* out_dev);
 
 /* ---- Allocation-free transform ------------------------------------------------------------
