@@ -1458,7 +1458,10 @@ pt_status create_impl(const pt_grid* grid, int N_t, double T, const pt_coeff* co
     for (float** b : ir)
       if (!(*b = alloc_padded<float>(p, L0, p->N, &st))) return st;
     if (p->dim == 2) prepare_ir_inner_2d();
-    if (p->dim == 3) prepare_ir_inner_3d();
+    if (p->dim == 3) {
+      prepare_ir_inner_3d();
+      prepare_level3_rows();
+    }
   }
   st = p->mixed ? setup_precision<float>(p) : setup_precision<double>(p);
   if (st != PT_OK) return st;

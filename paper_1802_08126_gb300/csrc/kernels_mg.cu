@@ -340,6 +340,17 @@ __global__ void __launch_bounds__(kLvBand + 32, 4) k_level3_rows(const float* __
   }
 }
 
+}  // namespace
+
+void prepare_level3_rows() {
+  const void* kernels[] = {(const void*)k_level3_rows<5, 1>, (const void*)k_level3_rows<5, 2>,
+                           (const void*)k_level3_rows<6, 1>, (const void*)k_level3_rows<6, 2>,
+                           (const void*)k_level3_rows<7, 1>, (const void*)k_level3_rows<7, 2>};
+  for (const void* k : kernels) resident_grid(k, kLvBand + 32, 0, 1 << 30);
+}
+
+namespace {
+
 // the streamed form when it applies (FP32, 3-D, 32 <= P <= 128); false otherwise
 template <typename T, int KIND>
 bool launch_level3_rows(const T* b, const T* x, void* out, int mode, int out_fp64, StencilGeom<T> g, OpBatch<T> op,

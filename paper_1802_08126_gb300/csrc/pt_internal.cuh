@@ -214,6 +214,7 @@ void launch_ir_outer_2d(const double* u, const double* p, const double* F, float
 // stream capture).
 void prepare_ir_inner_2d();
 void prepare_ir_inner_3d();
+void prepare_level3_rows();  // the row-streamed 3-D FP32 V-cycle levels (kernels_mg.cu)
 void launch_ir_inner_2d(const float* du, const float* dp, const float* R1, const float* R2, float* bp, float* rp,
                         double* partials, const float* tabf, const float* cthf, double a0, double tau, double h,
                         int n, int logP, long long S, int N, Steps<float> sp, SolveState* st, cudaStream_t s);
